@@ -1,0 +1,1137 @@
+// C ABI and host orchestration of CoNCPD-APG (Algorithm 1) and
+// lraCoNCPD-APG (Algorithm 2) on one GPU.
+//
+// One iteration = one sweep (cores, then modes 1..N for all blocks) + the
+// objective, replayed as a CUDA graph; the host reads F(k) and, if it did not
+// decrease, replays the re-update graph (Algorithm 1 safeguard: restore the
+// iterate of the start of the iteration and sweep again with every
+// extrapolation weight 0).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/cncpd.h"
+#include "cncpd_internal.cuh"
+
+using namespace cncpd;
+
+namespace {
+
+thread_local std::string g_err;
+
+int set_err(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CU(expr)                                                                         \
+  do {                                                                                   \
+    cudaError_t _e = (expr);                                                             \
+    if (_e != cudaSuccess)                                                               \
+      return set_err(_e == cudaErrorMemoryAllocation ? CNCPD_ENOMEM : CNCPD_ECUDA,       \
+                     "%s: %s (%s:%d)", #expr, cudaGetErrorString(_e), __FILE__, __LINE__); \
+  } while (0)
+
+#define TRY(expr)           \
+  do {                      \
+    int _r = (expr);        \
+    if (_r != CNCPD_OK) return _r; \
+  } while (0)
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct HostScalars {  // mirror of the head of DevScalars read back each iteration
+  double t, w_hat;
+  int have_prev, have_cur, nonfinite, pad0;
+  double F, relerr;
+};
+
+}  // namespace
+
+struct cncpd_ctx {
+  int device = 0, num_sms = 0;
+  int K = 0, N = 0, h = 0;
+  std::vector<int64_t> dims;  // K*N
+  std::vector<int> R, L, nonneg;
+  int Rmax = 0, RP = 0;
+  cncpd_opts opts{};
+  int st = ST_F32, fp64 = 0;
+  size_t fsz = 4;
+  cudaStream_t stream = nullptr;
+  std::vector<void*> allocs;
+
+  // factor arenas
+  size_t arena_elems = 0;
+  std::vector<size_t> foff;  // K*N element offsets
+  char *A1 = nullptr, *A2 = nullptr, *AS = nullptr;
+
+  DevDesc hd{};
+  DevDesc* dd = nullptr;
+  DevScalars* sc = nullptr;
+  std::vector<double> lam_init;  // K*RMAX
+  std::vector<double> xnorm2;    // K
+  int64_t* d_red_prefix = nullptr;
+  HostScalars* hs = nullptr;     // pinned
+
+  // solver state on the host
+  bool dirty = true;             // factors/cores changed: re-initialise history
+  double F_prev = 0.0, rel_prev = 0.0;
+  int total_iters = 0;
+
+  cudaGraphExec_t g_main = nullptr, g_redo = nullptr;
+  int main_runs = 0, redo_runs = 0;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+
+  // LRA
+  bool lra = false;
+  std::vector<int> Rt;
+  DevDesc hd_als{};
+  DevDesc* dd_als = nullptr;
+  int RPt = 0;
+  int64_t* d_red_prefix_als = nullptr;
+  int* d_active = nullptr;
+  int* d_status = nullptr;
+  double* d_relk = nullptr;
+
+  int64_t dim(int k, int n) const { return dims[(size_t)k * N + n]; }
+  void* U1p(int k, int n) const { return A1 + foff[(size_t)k * N + n] * fsz; }
+  void* U2p(int k, int n) const { return A2 + foff[(size_t)k * N + n] * fsz; }
+};
+
+namespace {
+
+int dalloc(cncpd_ctx* c, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(CNCPD_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  c->allocs.push_back(*p);
+  return CNCPD_OK;
+}
+
+// Split-K plan of the lead-mode contraction for rank bucket RP.
+void plan_lead_splits(cncpd_ctx* c, DevDesc& d, int RP, int fp64, size_t* partial_elems) {
+  const int cpt = lead_cpt(fp64, RP);
+  int64_t tot_rows = 0;
+  for (int k = 0; k < d.K; ++k) tot_rows += d.lead_rows[k];
+  // aim for ~4 CTAs per SM in total, at least 64 rows per split
+  const int64_t target_units = (int64_t)c->num_sms * 4;
+  d.tt_prefix[0] = 0;
+  size_t off = 0;
+  for (int k = 0; k < d.K; ++k) {
+    const int64_t J = d.trail_cols[k];
+    const int ctiles = (int)((J + 64 * cpt - 1) / (64 * cpt));
+    const int64_t rows = d.lead_rows[k];
+    int64_t want = std::max<int64_t>(1, (target_units * rows) / std::max<int64_t>(1, tot_rows) / ctiles);
+    int64_t split_rows = (rows + want - 1) / want;
+    split_rows = std::max<int64_t>(split_rows, 64);
+    split_rows = ((split_rows + 63) / 64) * 64;
+    const int ns = (int)((rows + split_rows - 1) / split_rows);
+    d.tt_ctiles[k] = ctiles;
+    d.nsplit[k] = ns;
+    d.split_rows[k] = split_rows;
+    d.partial_off[k] = (int64_t)off;
+    off += (size_t)ns * J * d.R[k];
+    d.tt_prefix[k + 1] = d.tt_prefix[k] + ctiles * ns;
+  }
+  d.tt_cpt = cpt;
+  *partial_elems = off;
+}
+
+void plan_trailing_tiles(DevDesc& d) {
+  d.lt_prefix[0] = 0;
+  for (int k = 0; k < d.K; ++k) d.lt_prefix[k + 1] = d.lt_prefix[k] + (int)((d.lead_rows[k] + 31) / 32);
+}
+
+int upload_desc(cncpd_ctx* c) {
+  CU(cudaMemcpyAsync(c->dd, &c->hd, sizeof(DevDesc), cudaMemcpyHostToDevice, c->stream));
+  if (c->dd_als) CU(cudaMemcpyAsync(c->dd_als, &c->hd_als, sizeof(DevDesc), cudaMemcpyHostToDevice, c->stream));
+  return CNCPD_OK;
+}
+
+int sync(cncpd_ctx* c) {
+  CU(cudaStreamSynchronize(c->stream));
+  return CNCPD_OK;
+}
+
+void destroy_graphs(cncpd_ctx* c) {
+  if (c->g_main) cudaGraphExecDestroy(c->g_main);
+  if (c->g_redo) cudaGraphExecDestroy(c->g_redo);
+  c->g_main = c->g_redo = nullptr;
+  c->main_runs = c->redo_runs = 0;
+}
+
+// Copy the shared first L_n columns of block 0 into every other block (arena A).
+int propagate_common(cncpd_ctx* c, char* arena) {
+  for (int n = 0; n < c->N; ++n) {
+    const int Ln = c->L[n];
+    if (Ln == 0) continue;
+    const char* src = arena + c->foff[n] * c->fsz;
+    for (int k = 1; k < c->K; ++k) {
+      char* dst = arena + c->foff[(size_t)k * c->N + n] * c->fsz;
+      CU(cudaMemcpy2DAsync(dst, c->R[k] * c->fsz, src, c->R[0] * c->fsz, Ln * c->fsz, c->dim(0, n),
+                           cudaMemcpyDeviceToDevice, c->stream));
+    }
+  }
+  return CNCPD_OK;
+}
+
+// ----------------------------------------------------------- the sweep -----
+
+int record(cncpd_ctx* c, int which_ev) {
+  if (!c->opts.profile) return CNCPD_OK;
+  CU(cudaEventRecordWithFlags(c->ev[which_ev], c->stream,
+                              c->opts.use_graph ? cudaEventRecordExternal : cudaEventRecordDefault));
+  return CNCPD_OK;
+}
+
+// M^(n) for every block at the current factors of the other modes, given
+// that the level-1 partial of n's group is current.
+int enqueue_mode_m(cncpd_ctx* c, int n) {
+  LaunchCfg lc{c->stream, c->num_sms};
+  if (c->lra) {
+    CU(launch_collapsed_m(lc, c->dd, c->hd, c->fp64, n));
+    return CNCPD_OK;
+  }
+  const int gsize = (n < c->h) ? c->h : c->N - c->h;
+  if (gsize > 1) CU(launch_level2(lc, c->dd, c->hd, c->fp64, c->RP, n));
+  return CNCPD_OK;
+}
+
+int enqueue_trailing(cncpd_ctx* c, const DevDesc* dd, const DevDesc& hd, int RP) {
+  LaunchCfg lc{c->stream, c->num_sms};
+  TRY(record(c, 0));
+  CU(launch_trailing_contract(lc, dd, hd, c->st, RP));
+  TRY(record(c, 1));
+  return CNCPD_OK;
+}
+
+int enqueue_lead(cncpd_ctx* c, const DevDesc* dd, const DevDesc& hd, int RP, const int64_t* red_prefix) {
+  LaunchCfg lc{c->stream, c->num_sms};
+  TRY(record(c, 2));
+  CU(launch_lead_contract(lc, dd, hd, c->st, RP, red_prefix));
+  TRY(record(c, 3));
+  return CNCPD_OK;
+}
+
+int enqueue_sweep(cncpd_ctx* c, int use_w) {
+  LaunchCfg lc{c->stream, c->num_sms};
+  const double dw = c->opts.delta_w;
+  const int core = c->opts.use_core;
+  if (core) CU(launch_core_update(lc, c->dd, c->hd, use_w, dw));
+  for (int n = 0; n < c->N; ++n) {
+    if (!c->lra) {
+      if (n == 0) TRY(enqueue_trailing(c, c->dd, c->hd, c->RP));
+      if (n == c->h) TRY(enqueue_lead(c, c->dd, c->hd, c->RP, c->d_red_prefix));
+    }
+    TRY(enqueue_mode_m(c, n));
+    CU(launch_lipschitz(lc, c->dd, c->hd, c->fp64, n, core));
+    CU(launch_update(lc, c->dd, c->hd, c->fp64, c->RP, n, use_w, dw, core));
+    CU(launch_gram(lc, c->dd, c->hd, c->fp64, n, n + 1, 0));
+    if (c->lra) CU(launch_cross_gram(lc, c->dd, c->hd, c->fp64, n, n + 1));
+  }
+  if (c->lra) CU(launch_lra_objective(lc, c->dd, c->hd, c->fp64, core));
+  else CU(launch_objective(lc, c->dd, c->hd, c->fp64, c->RP, 1));
+  return CNCPD_OK;
+}
+
+int enqueue_readback(cncpd_ctx* c) {
+  CU(cudaMemcpyAsync(c->hs, c->sc, sizeof(HostScalars), cudaMemcpyDeviceToHost, c->stream));
+  return CNCPD_OK;
+}
+
+size_t arena_bytes(cncpd_ctx* c) { return c->arena_elems * c->fsz; }
+
+int enqueue_main(cncpd_ctx* c) {
+  LaunchCfg lc{c->stream, c->num_sms};
+  CU(launch_iter_begin(lc, c->dd, c->hd));
+  CU(cudaMemcpyAsync(c->AS, c->A2, arena_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
+  TRY(enqueue_sweep(c, 1));
+  return enqueue_readback(c);
+}
+
+int enqueue_redo(cncpd_ctx* c) {
+  LaunchCfg lc{c->stream, c->num_sms};
+  CU(launch_redo_prepare(lc, c->dd, c->hd));
+  CU(cudaMemcpyAsync(c->A1, c->A2, arena_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->A2, c->AS, arena_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
+  CU(launch_gram(lc, c->dd, c->hd, c->fp64, 0, c->N, 0));
+  if (c->lra) CU(launch_cross_gram(lc, c->dd, c->hd, c->fp64, 0, c->N));
+  TRY(enqueue_sweep(c, 0));
+  return enqueue_readback(c);
+}
+
+int capture(cncpd_ctx* c, int (*fn)(cncpd_ctx*), cudaGraphExec_t* out) {
+  CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  int r = fn(c);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  if (r != CNCPD_OK) {
+    if (g) cudaGraphDestroy(g);
+    return r;
+  }
+  if (e != cudaSuccess) return set_err(CNCPD_ECUDA, "stream capture failed: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return set_err(CNCPD_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+  return CNCPD_OK;
+}
+
+// The first replay of each kind runs eagerly (so that every kernel's
+// attributes are set outside stream capture); later ones replay the graph.
+int run_main(cncpd_ctx* c) {
+  if (c->opts.use_graph && c->main_runs++ > 0) {
+    if (!c->g_main) TRY(capture(c, enqueue_main, &c->g_main));
+    CU(cudaGraphLaunch(c->g_main, c->stream));
+    return CNCPD_OK;
+  }
+  return enqueue_main(c);
+}
+
+int run_redo(cncpd_ctx* c) {
+  if (c->opts.use_graph && c->redo_runs++ > 0) {
+    if (!c->g_redo) TRY(capture(c, enqueue_redo, &c->g_redo));
+    CU(cudaGraphLaunch(c->g_redo, c->stream));
+    return CNCPD_OK;
+  }
+  return enqueue_redo(c);
+}
+
+// Reset the iteration history (first iteration of Algorithm 1) and evaluate
+// F(0) at the current factors.
+int initialise(cncpd_ctx* c) {
+  LaunchCfg lc{c->stream, c->num_sms};
+  // U_{-1} := U_0 (reading R2)
+  CU(cudaMemcpyAsync(c->A2, c->A1, arena_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
+  // scalars: t_0 = 1, no Lipschitz history, cores from lam_init
+  std::vector<char> buf(sizeof(DevScalars), 0);
+  DevScalars* s = reinterpret_cast<DevScalars*>(buf.data());
+  s->t = 1.0;
+  for (int k = 0; k < c->K; ++k) {
+    s->xnorm2_orig[k] = c->xnorm2[k];
+    s->xnorm2[k] = c->xnorm2[k];
+    for (int r = 0; r < CNCPD_RMAX; ++r) {
+      const double v = c->opts.use_core ? c->lam_init[(size_t)k * CNCPD_RMAX + r] : 1.0;
+      s->lam1[k][r] = s->lam2[k][r] = s->lamS[k][r] = v;
+    }
+  }
+  if (c->lra) {
+    // ||X~||^2 is computed on the device; keep it.
+    CU(cudaMemcpyAsync(c->hs, c->sc, sizeof(HostScalars), cudaMemcpyDeviceToHost, c->stream));
+    std::vector<double> xt(c->K);
+    CU(cudaMemcpyAsync(xt.data(), c->sc->xnorm2, sizeof(double) * c->K, cudaMemcpyDeviceToHost, c->stream));
+    TRY(sync(c));
+    for (int k = 0; k < c->K; ++k) s->xnorm2[k] = xt[k];
+  }
+  CU(cudaMemcpyAsync(c->sc, buf.data(), sizeof(DevScalars), cudaMemcpyHostToDevice, c->stream));
+  CU(launch_gram(lc, c->dd, c->hd, c->fp64, 0, c->N, 0));
+  const int n = c->N - 1;
+  if (c->lra) {
+    CU(launch_cross_gram(lc, c->dd, c->hd, c->fp64, 0, c->N));
+    CU(launch_lra_objective(lc, c->dd, c->hd, c->fp64, c->opts.use_core));
+  } else {
+    TRY(enqueue_lead(c, c->dd, c->hd, c->RP, c->d_red_prefix));
+    TRY(enqueue_mode_m(c, n));
+    CU(launch_objective(lc, c->dd, c->hd, c->fp64, c->RP, 1));
+  }
+  TRY(enqueue_readback(c));
+  TRY(sync(c));
+  if (c->hs->nonfinite || !std::isfinite(c->hs->F))
+    return set_err(CNCPD_ENONFINITE, "initial objective is not finite (F = %g)", c->hs->F);
+  c->F_prev = c->hs->F;
+  c->rel_prev = c->hs->relerr;
+  c->total_iters = 0;
+  c->dirty = false;
+  return CNCPD_OK;
+}
+
+double pass_bytes(cncpd_ctx* c) {
+  double b = 0;
+  const double es = c->st == ST_F64 ? 8 : c->st == ST_F32 ? 4 : c->st == ST_BF16 ? 2 : 4;
+  for (int k = 0; k < c->K; ++k) {
+    double n = 1;
+    for (int m = 0; m < c->N; ++m) n *= (double)c->dim(k, m);
+    b += n * es;
+  }
+  return b;
+}
+
+// Kernels launched by one main (redo = 0) or re-update (redo = 1) replay.
+long long kernels_per_replay(cncpd_ctx* c, int redo) {
+  long long n = c->opts.use_core ? 1 : 0;
+  if (!c->lra) n += 1 + 2;  // trailing contraction; lead contraction + split reduction
+  for (int m = 0; m < c->N; ++m) {
+    const int gsize = (m < c->h) ? c->h : c->N - c->h;
+    if (c->lra) n += 2;     // collapsed M, cross Gram
+    else if (gsize > 1) n += 1;
+    n += 3;                 // Lipschitz, update, Gram
+  }
+  n += 1;                   // objective
+  n += redo ? (c->lra ? 3 : 2) : 1;
+  return n;
+}
+
+int read_profile(cncpd_ctx* c, cncpd_stats* st) {
+  if (!c->opts.profile || c->lra) return CNCPD_OK;
+  float a = 0, b = 0;
+  CU(cudaEventElapsedTime(&a, c->ev[0], c->ev[1]));
+  CU(cudaEventElapsedTime(&b, c->ev[2], c->ev[3]));
+  st->stream_ms += a + b;
+  st->trail_ms += a;
+  st->lead_ms += b;
+  st->stream_launches += 2;
+  return CNCPD_OK;
+}
+
+int run_iterations(cncpd_ctx* c, int n_iters, bool use_eps, cncpd_stats* out) {
+  cncpd_stats st{};
+  const double t0 = now_s();
+  if (c->dirty) TRY(initialise(c));
+  const double pb = c->lra ? 0.0 : 2.0 * pass_bytes(c);
+  for (int it = 0; it < n_iters; ++it) {
+    TRY(run_main(c));
+    TRY(sync(c));
+    TRY(read_profile(c, &st));
+    st.x_bytes += pb;
+    st.launches += kernels_per_replay(c, 0);
+    double F = c->hs->F;
+    const bool redo = c->opts.reupdate && (F - c->F_prev) > 1e-13 * std::fabs(c->F_prev);
+    if (redo) {
+      TRY(run_redo(c));
+      TRY(sync(c));
+      TRY(read_profile(c, &st));
+      st.x_bytes += pb;
+      st.launches += kernels_per_replay(c, 1);
+      F = c->hs->F;
+      st.reupdates++;
+    }
+    if (c->hs->nonfinite || !std::isfinite(F))
+      return set_err(CNCPD_ENONFINITE, "objective or Lipschitz constant not finite at iteration %d",
+                     c->total_iters + 1);
+    const double rel = c->hs->relerr;
+    c->total_iters++;
+    st.iters++;
+    c->F_prev = F;
+    const bool stop = use_eps && std::fabs(rel - c->rel_prev) < c->opts.eps;
+    c->rel_prev = rel;
+    if (stop) {
+      st.converged = 1;
+      break;
+    }
+  }
+  st.total_iters = c->total_iters;
+  st.F = c->F_prev;
+  st.relerr = c->rel_prev;
+  st.fit = 1.0 - c->rel_prev;
+  st.seconds = now_s() - t0;
+  if (out) *out = st;
+  return CNCPD_OK;
+}
+
+// M^(n) for every mode at the current factors (no updates in between):
+// both level-1 contractions, then level 2.  Used by the gradient, the
+// MTTKRP hook and the global fit.
+int all_modes_m(cncpd_ctx* c) {
+  LaunchCfg lc{c->stream, c->num_sms};
+  TRY(enqueue_trailing(c, c->dd, c->hd, c->RP));
+  TRY(enqueue_lead(c, c->dd, c->hd, c->RP, c->d_red_prefix));
+  for (int n = 0; n < c->N; ++n) {
+    const int gsize = (n < c->h) ? c->h : c->N - c->h;
+    if (gsize > 1) CU(launch_level2(lc, c->dd, c->hd, c->fp64, c->RP, n));
+  }
+  return CNCPD_OK;
+}
+
+int check_handle(cncpd_t h) {
+  if (!h) return set_err(CNCPD_EINVAL, "null handle");
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return set_err(CNCPD_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  return CNCPD_OK;
+}
+
+int copy_matrix_out(cncpd_ctx* c, const void* src, int src_f64, int64_t n, void* dst, cncpd_dtype dt) {
+  if (dt != CNCPD_F64 && dt != CNCPD_F32) return set_err(CNCPD_EINVAL, "output dtype must be F64 or F32");
+  const int dst_f64 = dt == CNCPD_F64;
+  if (dst_f64 == src_f64) {
+    CU(cudaMemcpyAsync(dst, src, n * (src_f64 ? 8 : 4), cudaMemcpyDefault, c->stream));
+  } else {
+    void* tmp = nullptr;
+    CU(cudaMallocAsync(&tmp, n * (dst_f64 ? 8 : 4) + 16, c->stream));
+    CU(launch_convert(c->stream, src, src_f64, tmp, dst_f64, n));
+    CU(cudaMemcpyAsync(dst, tmp, n * (dst_f64 ? 8 : 4), cudaMemcpyDefault, c->stream));
+    CU(cudaFreeAsync(tmp, c->stream));
+  }
+  return sync(c);
+}
+
+}  // namespace
+
+// =============================================================== C ABI ====
+
+extern "C" {
+
+void cncpd_default_opts(cncpd_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->eps = 1e-8;
+  o->max_it = 1000;
+  o->lra_eps = 1e-4;
+  o->lra_max_it = 200;
+  o->delta_w = 0.9999;
+  o->use_core = 0;
+  o->reupdate = 1;
+  o->storage = -1;
+  o->use_graph = 1;
+  o->profile = 0;
+}
+
+const char* cncpd_last_error(void) { return g_err.c_str(); }
+
+void cncpd_destroy(cncpd_t h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  destroy_graphs(h);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->hs) cudaFreeHost(h->hs);
+  for (auto& e : h->ev)
+    if (e) cudaEventDestroy(e);
+  if (h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* const* X, cncpd_dtype x_dtype,
+                 const int* R, const int* L, const unsigned char* nonneg, const cncpd_opts* opts, void* stream) {
+  g_err.clear();
+  if (!out) return set_err(CNCPD_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (K < 1 || K > CNCPD_KMAX) return set_err(CNCPD_EINVAL, "K = %d outside 1..%d", K, CNCPD_KMAX);
+  if (N < 3 || N > CNCPD_NMAX) return set_err(CNCPD_EINVAL, "N = %d outside 3..%d", N, CNCPD_NMAX);
+  if (!dims || !X || !R || !L) return set_err(CNCPD_EINVAL, "dims, X, R and L are required");
+  if (x_dtype != CNCPD_F64 && x_dtype != CNCPD_F32) return set_err(CNCPD_EINVAL, "x_dtype must be F64 or F32");
+  int minR = 1 << 30;
+  for (int k = 0; k < K; ++k) {
+    if (R[k] < 1 || R[k] > CNCPD_RMAX) return set_err(CNCPD_EINVAL, "R[%d] = %d outside 1..%d", k, R[k], CNCPD_RMAX);
+    minR = std::min(minR, R[k]);
+    if (!X[k]) return set_err(CNCPD_EINVAL, "X[%d] is NULL", k);
+    for (int n = 0; n < N; ++n)
+      if (dims[(size_t)k * N + n] < 1) return set_err(CNCPD_EINVAL, "dims[%d][%d] < 1", k, n);
+  }
+  for (int n = 0; n < N; ++n) {
+    if (L[n] < 0 || L[n] > minR)
+      return set_err(CNCPD_EINVAL, "L[%d] = %d outside 0..min_k R_k = %d", n, L[n], minR);
+    if (L[n] > 0)
+      for (int k = 1; k < K; ++k)
+        if (dims[(size_t)k * N + n] != dims[n])
+          return set_err(CNCPD_EINVAL, "coupled mode %d has different sizes across blocks", n);
+  }
+  cncpd_opts o;
+  if (opts) o = *opts;
+  else cncpd_default_opts(&o);
+  int st = o.storage < 0 ? (x_dtype == CNCPD_F64 ? ST_F64 : ST_F32) : o.storage;
+  if (st < 0 || st > 3) return set_err(CNCPD_EINVAL, "bad storage type %d", o.storage);
+  if (o.delta_w <= 0 || o.delta_w >= 1.0) return set_err(CNCPD_EINVAL, "delta_w must be in (0, 1)");
+
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) return set_err(CNCPD_ECUDA, "no CUDA device: %s", cudaGetErrorString(ce));
+
+  cncpd_ctx* c = new cncpd_ctx();
+  c->device = dev;
+  c->K = K;
+  c->N = N;
+  c->h = (N + 1) / 2;
+  c->dims.assign(dims, dims + (size_t)K * N);
+  c->R.assign(R, R + K);
+  c->L.assign(L, L + N);
+  c->nonneg.assign(N, 1);
+  if (nonneg)
+    for (int n = 0; n < N; ++n) c->nonneg[n] = nonneg[n] ? 1 : 0;
+  c->Rmax = *std::max_element(c->R.begin(), c->R.end());
+  c->RP = rank_bucket(c->Rmax);
+  c->opts = o;
+  c->st = st;
+  c->fp64 = (st == ST_F64);
+  c->fsz = c->fp64 ? 8 : 4;
+  c->lam_init.assign((size_t)K * CNCPD_RMAX, 1.0);
+  c->xnorm2.assign(K, 0.0);
+
+  auto fail = [&](int code) {
+    std::string msg = g_err;
+    cncpd_destroy(c);
+    g_err = msg;
+    return code;
+  };
+#define CTRY(expr)                 \
+  do {                             \
+    int _r = (expr);               \
+    if (_r != CNCPD_OK) return fail(_r); \
+  } while (0)
+#define CCU(expr)                                                                                   \
+  do {                                                                                              \
+    cudaError_t _e = (expr);                                                                        \
+    if (_e != cudaSuccess) return fail(set_err(CNCPD_ECUDA, "%s: %s", #expr, cudaGetErrorString(_e))); \
+  } while (0)
+
+  CCU(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
+  CCU(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+  CCU(cudaMallocHost((void**)&c->hs, sizeof(HostScalars)));
+  for (auto& e : c->ev) CCU(cudaEventCreate(&e));
+  // order after the caller's stream
+  if (stream) {
+    cudaEvent_t ev;
+    CCU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CCU(cudaEventRecord(ev, (cudaStream_t)stream));
+    CCU(cudaStreamWaitEvent(c->stream, ev, 0));
+    cudaEventDestroy(ev);
+  } else {
+    CCU(cudaStreamSynchronize(0));
+  }
+
+  DevDesc& d = c->hd;
+  std::memset(&d, 0, sizeof d);
+  d.K = K;
+  d.N = N;
+  d.h = c->h;
+  d.Rmax = c->Rmax;
+  for (int k = 0; k < K; ++k) {
+    d.R[k] = R[k];
+    int64_t lr = 1, tc = 1;
+    for (int n = 0; n < N; ++n) {
+      d.dims[k][n] = c->dim(k, n);
+      if (n < c->h) lr *= c->dim(k, n);
+      else tc *= c->dim(k, n);
+    }
+    d.lead_rows[k] = lr;
+    d.trail_cols[k] = tc;
+  }
+  for (int n = 0; n < N; ++n) {
+    d.L[n] = c->L[n];
+    d.nonneg[n] = c->nonneg[n];
+  }
+
+  // --- X: quantise into library storage
+  const size_t xes = (st == ST_F64) ? 8 : (st == ST_F32) ? 4 : 2;
+  const int src_f64 = x_dtype == CNCPD_F64;
+  const size_t ses = src_f64 ? 8 : 4;
+  int64_t maxel = 0;
+  for (int k = 0; k < K; ++k) maxel = std::max(maxel, d.lead_rows[k] * d.trail_cols[k]);
+  void* stage = nullptr;
+  double* nscratch = nullptr;
+  double* nout = nullptr;
+  const int nblk = 1024;
+  CTRY(dalloc(c, (void**)&nscratch, nblk * sizeof(double)));
+  CTRY(dalloc(c, (void**)&nout, CNCPD_KMAX * sizeof(double)));
+  for (int k = 0; k < K; ++k) {
+    const int64_t ne = d.lead_rows[k] * d.trail_cols[k];
+    void* xb = nullptr;
+    void* xlo = nullptr;
+    CTRY(dalloc(c, &xb, ne * xes));
+    if (st == ST_BF16X2) CTRY(dalloc(c, &xlo, ne * xes));
+    const void* src = X[k];
+    cudaPointerAttributes pa;
+    bool on_dev = false;
+    if (cudaPointerGetAttributes(&pa, src) == cudaSuccess)
+      on_dev = (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
+    else
+      cudaGetLastError();
+    if (!on_dev) {
+      if (!stage) CTRY(dalloc(c, &stage, maxel * ses));
+      CCU(cudaMemcpyAsync(stage, src, ne * ses, cudaMemcpyHostToDevice, c->stream));
+      src = stage;
+    }
+    CCU(launch_quantize(c->stream, src, src_f64, xb, xlo, st, ne, nout + k, nscratch, nblk));
+    d.X[k] = xb;
+    d.Xlo[k] = xlo;
+  }
+  CCU(cudaMemcpyAsync(c->xnorm2.data(), nout, K * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+
+  // --- factor arenas
+  c->foff.resize((size_t)K * N);
+  size_t off = 0;
+  for (int k = 0; k < K; ++k)
+    for (int n = 0; n < N; ++n) {
+      c->foff[(size_t)k * N + n] = off;
+      off += ((size_t)c->dim(k, n) * R[k] + 31) / 32 * 32;
+    }
+  c->arena_elems = off;
+  CTRY(dalloc(c, (void**)&c->A1, off * c->fsz));
+  CTRY(dalloc(c, (void**)&c->A2, off * c->fsz));
+  CTRY(dalloc(c, (void**)&c->AS, off * c->fsz));
+  for (int k = 0; k < K; ++k)
+    for (int n = 0; n < N; ++n) {
+      d.U1[k][n] = c->U1p(k, n);
+      d.U2[k][n] = c->U2p(k, n);
+      void* m = nullptr;
+      CTRY(dalloc(c, &m, (size_t)c->dim(k, n) * R[k] * c->fsz));
+      d.M[k][n] = m;
+      double* g = nullptr;
+      CTRY(dalloc(c, (void**)&g, (size_t)R[k] * R[k] * sizeof(double)));
+      d.G[k][n] = g;
+    }
+  for (int k = 0; k < K; ++k) {
+    void* p = nullptr;
+    CTRY(dalloc(c, &p, (size_t)d.lead_rows[k] * R[k] * c->fsz));
+    d.Pl[k] = p;
+    if (N - c->h == 1) {
+      d.Pt[k] = d.M[k][N - 1];  // the lead contraction is the last mode's MTTKRP
+    } else {
+      CTRY(dalloc(c, &p, (size_t)d.trail_cols[k] * R[k] * c->fsz));
+      d.Pt[k] = p;
+    }
+    CTRY(dalloc(c, &p, (size_t)R[k] * R[k] * c->fsz));
+    d.H[k] = p;
+  }
+  size_t pel = 0;
+  plan_lead_splits(c, d, c->RP, c->fp64, &pel);
+  plan_trailing_tiles(d);
+  CTRY(dalloc(c, &d.partial, pel * c->fsz));
+  {
+    std::vector<int64_t> pre(K + 1, 0);
+    for (int k = 0; k < K; ++k) pre[k + 1] = pre[k] + d.trail_cols[k] * R[k];
+    CTRY(dalloc(c, (void**)&c->d_red_prefix, (K + 1) * sizeof(int64_t)));
+    CCU(cudaMemcpyAsync(c->d_red_prefix, pre.data(), (K + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+    CCU(cudaStreamSynchronize(c->stream));
+  }
+  CTRY(dalloc(c, (void**)&c->sc, sizeof(DevScalars)));
+  CTRY(dalloc(c, (void**)&d.err, sizeof(int)));
+  CCU(cudaMemsetAsync(d.err, 0, sizeof(int), c->stream));
+  d.sc = c->sc;
+  CTRY(dalloc(c, (void**)&c->dd, sizeof(DevDesc)));
+  CTRY(upload_desc(c));
+
+  // default initial factors: Uniform[0,1] (Section IV), shared columns from block 0
+  for (int k = 0; k < K; ++k)
+    for (int n = 0; n < N; ++n)
+      CCU(launch_uniform_init(c->stream, c->U1p(k, n), c->fp64, (int64_t)c->dim(k, n) * R[k],
+                              0x5eedULL * 1000003ULL + (uint64_t)(k * CNCPD_NMAX + n)));
+  CTRY(propagate_common(c, c->A1));
+  CCU(cudaStreamSynchronize(c->stream));
+  c->dirty = true;
+  *out = c;
+#undef CTRY
+#undef CCU
+  return CNCPD_OK;
+}
+
+int cncpd_set_factors(cncpd_t h, int k, int n, const void* U, cncpd_dtype dtype) {
+  TRY(check_handle(h));
+  if (k < 0 || k >= h->K || n < 0 || n >= h->N || !U) return set_err(CNCPD_EINVAL, "bad block/mode or NULL data");
+  if (dtype != CNCPD_F64 && dtype != CNCPD_F32) return set_err(CNCPD_EINVAL, "factor dtype must be F64 or F32");
+  const int64_t I = h->dim(k, n);
+  const int R = h->R[k];
+  const int src_f64 = dtype == CNCPD_F64;
+  const size_t ses = src_f64 ? 8 : 4;
+  void* tmp = nullptr;
+  CU(cudaMallocAsync(&tmp, I * R * ses + 16, h->stream));
+  CU(cudaMemcpyAsync(tmp, U, I * R * ses, cudaMemcpyDefault, h->stream));
+  void* conv = tmp;
+  void* tmp2 = nullptr;
+  if (src_f64 != h->fp64) {
+    CU(cudaMallocAsync(&tmp2, I * R * h->fsz + 16, h->stream));
+    CU(launch_convert(h->stream, tmp, src_f64, tmp2, h->fp64, I * R));
+    conv = tmp2;
+  }
+  const int Ln = h->L[n];
+  char* dst = (char*)h->U1p(k, n);
+  if (k == 0 || Ln == 0) {
+    CU(cudaMemcpyAsync(dst, conv, I * R * h->fsz, cudaMemcpyDeviceToDevice, h->stream));
+  } else if (Ln < R) {
+    CU(cudaMemcpy2DAsync(dst + Ln * h->fsz, R * h->fsz, (char*)conv + Ln * h->fsz, R * h->fsz, (R - Ln) * h->fsz, I,
+                         cudaMemcpyDeviceToDevice, h->stream));
+  }
+  if (k == 0) TRY(propagate_common(h, h->A1));
+  CU(cudaFreeAsync(tmp, h->stream));
+  if (tmp2) CU(cudaFreeAsync(tmp2, h->stream));
+  TRY(sync(h));
+  h->dirty = true;
+  return CNCPD_OK;
+}
+
+int cncpd_set_core(cncpd_t h, int k, const double* lambda) {
+  TRY(check_handle(h));
+  if (k < 0 || k >= h->K || !lambda) return set_err(CNCPD_EINVAL, "bad block or NULL lambda");
+  for (int r = 0; r < h->R[k]; ++r) {
+    if (!(lambda[r] >= 0.0)) return set_err(CNCPD_EINVAL, "core entries must be >= 0");
+    h->lam_init[(size_t)k * CNCPD_RMAX + r] = lambda[r];
+  }
+  h->dirty = true;
+  return CNCPD_OK;
+}
+
+int cncpd_step(cncpd_t h, int n_iters, cncpd_stats* out) {
+  TRY(check_handle(h));
+  if (n_iters < 0) return set_err(CNCPD_EINVAL, "n_iters < 0");
+  return run_iterations(h, n_iters, false, out);
+}
+
+int cncpd_fit(cncpd_t h, cncpd_stats* out) {
+  TRY(check_handle(h));
+  return run_iterations(h, h->opts.max_it, true, out);
+}
+
+int cncpd_factors(cncpd_t h, int k, int n, void* dst, cncpd_dtype dtype) {
+  TRY(check_handle(h));
+  if (k < 0 || k >= h->K || n < 0 || n >= h->N || !dst) return set_err(CNCPD_EINVAL, "bad block/mode or NULL dst");
+  return copy_matrix_out(h, h->U1p(k, n), h->fp64, h->dim(k, n) * h->R[k], dst, dtype);
+}
+
+int cncpd_core(cncpd_t h, int k, double* lambda) {
+  TRY(check_handle(h));
+  if (k < 0 || k >= h->K || !lambda) return set_err(CNCPD_EINVAL, "bad block or NULL lambda");
+  if (h->dirty) {
+    for (int r = 0; r < h->R[k]; ++r)
+      lambda[r] = h->opts.use_core ? h->lam_init[(size_t)k * CNCPD_RMAX + r] : 1.0;
+    return CNCPD_OK;
+  }
+  CU(cudaMemcpyAsync(lambda, h->sc->lam1[k], h->R[k] * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  return sync(h);
+}
+
+int cncpd_mttkrp(cncpd_t h, int k, int n, void* dst, cncpd_dtype dtype) {
+  TRY(check_handle(h));
+  if (k < 0 || k >= h->K || n < 0 || n >= h->N || !dst) return set_err(CNCPD_EINVAL, "bad block/mode or NULL dst");
+  if (h->lra) {
+    LaunchCfg lc{h->stream, h->num_sms};
+    CU(launch_cross_gram(lc, h->dd, h->hd, h->fp64, 0, h->N));
+    CU(launch_collapsed_m(lc, h->dd, h->hd, h->fp64, n));
+  } else {
+    TRY(all_modes_m(h));
+  }
+  return copy_matrix_out(h, h->hd.M[k][n], h->fp64, h->dim(k, n) * h->R[k], dst, dtype);
+}
+
+int cncpd_objective_grad(cncpd_t h, double* F, void* const* gradU, void* const* gradC, cncpd_dtype dtype) {
+  TRY(check_handle(h));
+  if (dtype != CNCPD_F64 && dtype != CNCPD_F32) return set_err(CNCPD_EINVAL, "dtype must be F64 or F32");
+  if (h->dirty) TRY(initialise(h));
+  LaunchCfg lc{h->stream, h->num_sms};
+  CU(launch_gram(lc, h->dd, h->hd, h->fp64, 0, h->N, 0));
+  if (h->lra) {
+    CU(launch_cross_gram(lc, h->dd, h->hd, h->fp64, 0, h->N));
+    CU(launch_lra_objective(lc, h->dd, h->hd, h->fp64, h->opts.use_core));
+    for (int n = 0; n < h->N; ++n) CU(launch_collapsed_m(lc, h->dd, h->hd, h->fp64, n));
+  } else {
+    TRY(all_modes_m(h));
+    CU(launch_objective(lc, h->dd, h->hd, h->fp64, h->RP, 1));
+  }
+  TRY(enqueue_readback(h));
+  TRY(sync(h));
+  if (F) *F = h->hs->F;
+  const int dst_f64 = dtype == CNCPD_F64;
+  for (int n = 0; n < h->N; ++n) {
+    CU(launch_grad(lc, h->dd, h->hd, h->fp64, h->RP, n, h->opts.use_core));
+    TRY(sync(h));
+    if (gradU)
+      for (int k = 0; k < h->K; ++k)
+        if (gradU[(size_t)k * h->N + n])
+          TRY(copy_matrix_out(h, h->hd.M[k][n], h->fp64, h->dim(k, n) * h->R[k], gradU[(size_t)k * h->N + n], dtype));
+    if (gradC && gradC[n] && h->L[n] > 0) {
+      const int Ln = h->L[n];
+      const int64_t I = h->dim(0, n);
+      std::vector<double> acc((size_t)I * Ln, 0.0);
+      for (int k = 0; k < h->K; ++k) {
+        std::vector<double> g((size_t)I * h->R[k]);
+        TRY(copy_matrix_out(h, h->hd.M[k][n], h->fp64, I * h->R[k], g.data(), CNCPD_F64));
+        for (int64_t i = 0; i < I; ++i)
+          for (int r = 0; r < Ln; ++r) acc[(size_t)i * Ln + r] += g[(size_t)i * h->R[k] + r];
+      }
+      if (dst_f64) {
+        CU(cudaMemcpyAsync(gradC[n], acc.data(), acc.size() * 8, cudaMemcpyDefault, h->stream));
+      } else {
+        std::vector<float> f(acc.begin(), acc.end());
+        CU(cudaMemcpyAsync(gradC[n], f.data(), f.size() * 4, cudaMemcpyDefault, h->stream));
+        TRY(sync(h));
+        continue;
+      }
+      TRY(sync(h));
+    }
+  }
+  return CNCPD_OK;
+}
+
+int cncpd_global_fit(cncpd_t h, double* fit) {
+  TRY(check_handle(h));
+  if (!fit) return set_err(CNCPD_EINVAL, "fit is NULL");
+  if (h->dirty) TRY(initialise(h));
+  LaunchCfg lc{h->stream, h->num_sms};
+  const bool was_lra = h->lra;
+  h->lra = false;
+  CU(launch_gram(lc, h->dd, h->hd, h->fp64, 0, h->N, 0));
+  int r = enqueue_lead(h, h->dd, h->hd, h->RP, h->d_red_prefix);
+  if (r == CNCPD_OK) r = enqueue_mode_m(h, h->N - 1);
+  h->lra = was_lra;
+  TRY(r);
+  CU(launch_objective(lc, h->dd, h->hd, h->fp64, h->RP, 0));
+  std::vector<double> rel(h->K);
+  CU(cudaMemcpyAsync(rel.data(), h->sc->out_relk, h->K * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  TRY(sync(h));
+  double s = 0;
+  for (double v : rel) s += v;
+  *fit = 1.0 - s / h->K;
+  return CNCPD_OK;
+}
+
+int cncpd_lipschitz(const double* H, int R, double* lmax) {
+  g_err.clear();
+  if (!H || !lmax || R < 1 || R > CNCPD_RMAX) return set_err(CNCPD_EINVAL, "bad arguments");
+  double* d = nullptr;
+  CU(cudaMalloc(&d, (size_t)(R * R + 1) * sizeof(double)));
+  cudaError_t e = cudaMemcpy(d, H, (size_t)R * R * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_lmax_host(d, R, d + R * R, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(lmax, d + R * R, sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return set_err(CNCPD_ECUDA, "lipschitz: %s", cudaGetErrorString(e));
+  return CNCPD_OK;
+}
+
+// ------------------------------------------------------------- LRA -------
+
+int cncpd_lra(cncpd_t h, const int* R_tilde, const void* const* Ut0, cncpd_dtype dtype, cncpd_stats* out) {
+  TRY(check_handle(h));
+  if (h->lra) return set_err(CNCPD_ESTATE, "cncpd_lra already ran on this handle");
+  if (!R_tilde) return set_err(CNCPD_EINVAL, "R_tilde is NULL");
+  if (Ut0 && dtype != CNCPD_F64 && dtype != CNCPD_F32) return set_err(CNCPD_EINVAL, "Ut0 dtype must be F64 or F32");
+  const double t0 = now_s();
+  const int K = h->K, N = h->N;
+  h->Rt.assign(R_tilde, R_tilde + K);
+  int rtmax = 0;
+  for (int k = 0; k < K; ++k) {
+    if (R_tilde[k] < 1 || R_tilde[k] > CNCPD_RMAX) return set_err(CNCPD_EINVAL, "R_tilde[%d] outside 1..64", k);
+    rtmax = std::max(rtmax, R_tilde[k]);
+    h->hd.Rt[k] = R_tilde[k];
+  }
+  h->RPt = rank_bucket(rtmax);
+  DevDesc& a = h->hd_als;
+  a = h->hd;
+  a.Rmax = rtmax;
+  for (int k = 0; k < K; ++k) {
+    a.R[k] = a.Rt[k] = R_tilde[k];
+    for (int n = 0; n < N; ++n) {
+      void* u = nullptr;
+      TRY(dalloc(h, &u, (size_t)h->dim(k, n) * R_tilde[k] * h->fsz + 16));
+      h->hd.Ut[k][n] = a.Ut[k][n] = a.U1[k][n] = u;
+      a.U2[k][n] = nullptr;
+      double* g = nullptr;
+      TRY(dalloc(h, (void**)&g, (size_t)R_tilde[k] * R_tilde[k] * sizeof(double)));
+      h->hd.Gt[k][n] = a.Gt[k][n] = a.G[k][n] = g;
+      TRY(dalloc(h, (void**)&g, (size_t)R_tilde[k] * h->R[k] * sizeof(double)));
+      h->hd.C[k][n] = a.C[k][n] = g;
+      void* m = nullptr;
+      TRY(dalloc(h, &m, (size_t)h->dim(k, n) * R_tilde[k] * h->fsz));
+      a.M[k][n] = m;
+    }
+    void* p = nullptr;
+    TRY(dalloc(h, &p, (size_t)a.lead_rows[k] * R_tilde[k] * h->fsz));
+    a.Pl[k] = p;
+    if (N - h->h == 1) {
+      a.Pt[k] = a.M[k][N - 1];
+    } else {
+      TRY(dalloc(h, &p, (size_t)a.trail_cols[k] * R_tilde[k] * h->fsz));
+      a.Pt[k] = p;
+    }
+    TRY(dalloc(h, &p, (size_t)R_tilde[k] * R_tilde[k] * h->fsz));
+    h->hd.Vinv[k] = a.Vinv[k] = p;
+  }
+  size_t pel = 0;
+  plan_lead_splits(h, a, h->RPt, h->fp64, &pel);
+  plan_trailing_tiles(a);
+  TRY(dalloc(h, &a.partial, pel * h->fsz));
+  std::vector<int64_t> pre(K + 1, 0);
+  for (int k = 0; k < K; ++k) pre[k + 1] = pre[k] + a.trail_cols[k] * R_tilde[k];
+  TRY(dalloc(h, (void**)&h->d_red_prefix_als, (K + 1) * sizeof(int64_t)));
+  TRY(dalloc(h, (void**)&h->d_active, CNCPD_KMAX * sizeof(int)));
+  TRY(dalloc(h, (void**)&h->d_status, CNCPD_KMAX * sizeof(int)));
+  TRY(dalloc(h, (void**)&h->d_relk, CNCPD_KMAX * sizeof(double)));
+  TRY(dalloc(h, (void**)&h->dd_als, sizeof(DevDesc)));
+  CU(cudaMemcpyAsync(h->d_red_prefix_als, pre.data(), (K + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
+  // initial ALS factors
+  for (int k = 0; k < K; ++k)
+    for (int n = 0; n < N; ++n) {
+      const int64_t ne = h->dim(k, n) * R_tilde[k];
+      if (Ut0 && Ut0[(size_t)k * N + n]) {
+        void* tmp = nullptr;
+        const int src_f64 = dtype == CNCPD_F64;
+        CU(cudaMallocAsync(&tmp, ne * (src_f64 ? 8 : 4) + 16, h->stream));
+        CU(cudaMemcpyAsync(tmp, Ut0[(size_t)k * N + n], ne * (src_f64 ? 8 : 4), cudaMemcpyDefault, h->stream));
+        CU(launch_convert(h->stream, tmp, src_f64, a.Ut[k][n], h->fp64, ne));
+        CU(cudaFreeAsync(tmp, h->stream));
+      } else {
+        CU(launch_uniform_init(h->stream, a.Ut[k][n], h->fp64, ne, 0x1a5eedULL * 7919ULL + (uint64_t)(k * CNCPD_NMAX + n)));
+      }
+    }
+  // ||X||^2 of the stored tensors for the ALS relative error
+  {
+    std::vector<char> buf(sizeof(DevScalars), 0);
+    DevScalars* s = reinterpret_cast<DevScalars*>(buf.data());
+    for (int k = 0; k < K; ++k) s->xnorm2_orig[k] = s->xnorm2[k] = h->xnorm2[k];
+    CU(cudaMemcpyAsync(h->sc->xnorm2_orig, s->xnorm2_orig, sizeof(double) * CNCPD_KMAX, cudaMemcpyHostToDevice,
+                       h->stream));
+  }
+  TRY(upload_desc(h));
+  LaunchCfg lc{h->stream, h->num_sms};
+  CU(launch_gram(lc, h->dd_als, h->hd_als, h->fp64, 0, N, 0));
+  std::vector<int> active(CNCPD_KMAX, 0), sweeps(K, 0);
+  for (int k = 0; k < K; ++k) active[k] = 1;
+  std::vector<double> rel_prev(K, -1.0), rel(K, 0.0);
+  // relative error of the initial factors
+  {
+    // M^(N-1) at the initial factors for the ALS relative error
+    TRY(enqueue_lead(h, h->dd_als, h->hd_als, h->RPt, h->d_red_prefix_als));
+    if (N - h->h > 1) CU(launch_level2(lc, h->dd_als, h->hd_als, h->fp64, h->RPt, N - 1));
+    CU(launch_als_relerr(lc, h->dd_als, h->hd_als, h->fp64, h->d_relk));
+    CU(cudaMemcpyAsync(rel_prev.data(), h->d_relk, K * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    TRY(sync(h));
+  }
+  const DevDesc full = h->hd_als;
+  for (int s = 1; s <= h->opts.lra_max_it; ++s) {
+    int nact = 0;
+    for (int k = 0; k < K; ++k) nact += active[k];
+    if (nact == 0) break;
+    // only active blocks stream X
+    DevDesc& aa = h->hd_als;
+    aa.lt_prefix[0] = aa.tt_prefix[0] = 0;
+    for (int k = 0; k < K; ++k) {
+      aa.lt_prefix[k + 1] = aa.lt_prefix[k] + (active[k] ? full.lt_prefix[k + 1] - full.lt_prefix[k] : 0);
+      aa.tt_prefix[k + 1] = aa.tt_prefix[k] + (active[k] ? full.tt_prefix[k + 1] - full.tt_prefix[k] : 0);
+    }
+    CU(cudaMemcpyAsync(h->dd_als, &aa, sizeof(DevDesc), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(h->d_active, active.data(), CNCPD_KMAX * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemsetAsync(h->d_status, 0, CNCPD_KMAX * sizeof(int), h->stream));
+    for (int n = 0; n < N; ++n) {
+      if (n == 0) TRY(enqueue_trailing(h, h->dd_als, h->hd_als, h->RPt));
+      if (n == h->h) TRY(enqueue_lead(h, h->dd_als, h->hd_als, h->RPt, h->d_red_prefix_als));
+      const int gsize = (n < h->h) ? h->h : N - h->h;
+      if (gsize > 1) CU(launch_level2(lc, h->dd_als, h->hd_als, h->fp64, h->RPt, n));
+      CU(launch_als_solve(lc, h->dd_als, h->hd_als, h->fp64, n, h->d_active, h->d_status));
+      CU(launch_als_apply(lc, h->dd_als, h->hd_als, h->fp64, n, h->d_active));
+      CU(launch_gram(lc, h->dd_als, h->hd_als, h->fp64, n, n + 1, 0));
+    }
+    CU(launch_als_relerr(lc, h->dd_als, h->hd_als, h->fp64, h->d_relk));
+    std::vector<int> status(K, 0);
+    CU(cudaMemcpyAsync(rel.data(), h->d_relk, K * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(status.data(), h->d_status, K * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    TRY(sync(h));
+    for (int k = 0; k < K; ++k) {
+      if (!active[k]) continue;
+      if (status[k]) return set_err(CNCPD_ESINGULAR, "ALS normal matrix of block %d not positive definite", k);
+      sweeps[k] = s;
+      if (std::fabs(rel[k] - rel_prev[k]) < h->opts.lra_eps) active[k] = 0;
+      rel_prev[k] = rel[k];
+    }
+  }
+  h->hd_als = full;
+  // switch to the collapsed products; ||X~||^2 for the objective of Eq. cosfunclra
+  h->hd.lra = 1;
+  h->lra = true;
+  destroy_graphs(h);
+  TRY(upload_desc(h));
+  CU(launch_gram(lc, h->dd, h->hd, h->fp64, 0, N, 1));
+  CU(launch_lra_xnorm(lc, h->dd, h->hd));
+  TRY(sync(h));
+  h->dirty = true;
+  if (out) {
+    cncpd_stats st{};
+    st.lra_sweeps = *std::max_element(sweeps.begin(), sweeps.end());
+    double m = 0;
+    for (double v : rel_prev) m += v;
+    st.lra_relerr = m / K;
+    st.seconds = now_s() - t0;
+    *out = st;
+  }
+  return CNCPD_OK;
+}
+
+int cncpd_lra_factors(cncpd_t h, int k, int n, void* dst, cncpd_dtype dtype) {
+  TRY(check_handle(h));
+  if (!h->lra) return set_err(CNCPD_ESTATE, "cncpd_lra has not run");
+  if (k < 0 || k >= h->K || n < 0 || n >= h->N || !dst) return set_err(CNCPD_EINVAL, "bad block/mode or NULL dst");
+  return copy_matrix_out(h, h->hd.Ut[k][n], h->fp64, h->dim(k, n) * h->Rt[k], dst, dtype);
+}
+
+// ------------------------------------------------------- checkpoint -------
+
+struct BlobHeader {
+  char magic[8];
+  int K, N, fp64, lra;
+  int total_iters, pad;
+  double F_prev, rel_prev;
+  uint64_t arena_bytes, scalars_bytes;
+};
+
+int cncpd_save_state(cncpd_t h, void** blob, size_t* nbytes) {
+  TRY(check_handle(h));
+  if (!blob || !nbytes) return set_err(CNCPD_EINVAL, "NULL output");
+  if (h->dirty) TRY(initialise(h));
+  const size_t ab = arena_bytes(h);
+  const size_t total = sizeof(BlobHeader) + 2 * ab + sizeof(DevScalars);
+  char* p = (char*)std::malloc(total);
+  if (!p) return set_err(CNCPD_ENOMEM, "host malloc failed");
+  BlobHeader hdr{};
+  std::memcpy(hdr.magic, "CNCPDst1", 8);
+  hdr.K = h->K;
+  hdr.N = h->N;
+  hdr.fp64 = h->fp64;
+  hdr.lra = h->lra;
+  hdr.total_iters = h->total_iters;
+  hdr.F_prev = h->F_prev;
+  hdr.rel_prev = h->rel_prev;
+  hdr.arena_bytes = ab;
+  hdr.scalars_bytes = sizeof(DevScalars);
+  std::memcpy(p, &hdr, sizeof hdr);
+  cudaError_t e = cudaMemcpyAsync(p + sizeof hdr, h->A1, ab, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p + sizeof hdr + ab, h->A2, ab, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p + sizeof hdr + 2 * ab, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    std::free(p);
+    return set_err(CNCPD_ECUDA, "save_state: %s", cudaGetErrorString(e));
+  }
+  *blob = p;
+  *nbytes = total;
+  return CNCPD_OK;
+}
+
+int cncpd_load_state(cncpd_t h, const void* blob, size_t nbytes) {
+  TRY(check_handle(h));
+  if (!blob || nbytes < sizeof(BlobHeader)) return set_err(CNCPD_EINVAL, "blob too small");
+  BlobHeader hdr;
+  std::memcpy(&hdr, blob, sizeof hdr);
+  const size_t ab = arena_bytes(h);
+  if (std::memcmp(hdr.magic, "CNCPDst1", 8) != 0 || hdr.K != h->K || hdr.N != h->N || hdr.fp64 != h->fp64 ||
+      hdr.lra != (int)h->lra || hdr.arena_bytes != ab || hdr.scalars_bytes != sizeof(DevScalars) ||
+      nbytes != sizeof(BlobHeader) + 2 * ab + sizeof(DevScalars))
+    return set_err(CNCPD_EINVAL, "blob does not match this problem");
+  const char* p = (const char*)blob + sizeof hdr;
+  CU(cudaMemcpyAsync(h->A1, p, ab, cudaMemcpyHostToDevice, h->stream));
+  CU(cudaMemcpyAsync(h->A2, p + ab, ab, cudaMemcpyHostToDevice, h->stream));
+  CU(cudaMemcpyAsync(h->sc, p + 2 * ab, sizeof(DevScalars), cudaMemcpyHostToDevice, h->stream));
+  LaunchCfg lc{h->stream, h->num_sms};
+  CU(launch_gram(lc, h->dd, h->hd, h->fp64, 0, h->N, 0));
+  if (h->lra) CU(launch_cross_gram(lc, h->dd, h->hd, h->fp64, 0, h->N));
+  TRY(sync(h));
+  h->total_iters = hdr.total_iters;
+  h->F_prev = hdr.F_prev;
+  h->rel_prev = hdr.rel_prev;
+  h->dirty = false;
+  return CNCPD_OK;
+}
+
+void cncpd_free_blob(void* blob) { std::free(blob); }
+
+}  // extern "C"

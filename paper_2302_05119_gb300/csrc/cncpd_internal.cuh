@@ -1,0 +1,178 @@
+// Internal definitions shared by the translation units of libcncpd.
+//
+// Device data layout (all in HBM, allocated once per handle):
+//  - X^(k): dense C-order tensor in the storage type (f64, f32, bf16, or two
+//    bf16 planes hi/lo).  The tensor is viewed as a matrix with
+//    lead_rows = prod_{m<h} I_m rows and trail_cols = prod_{m>=h} I_m
+//    columns (h = number of "lead" modes of the two-level dimension tree).
+//  - factors U1 (current iterate), U2 (previous iterate), S (snapshot of U2
+//    at the start of an iteration) live in three arenas of identical layout;
+//    U^(n,k) is row-major I_n x R_k.
+//  - Grams G^(n,k) = U^T U are R_k x R_k in FP64.
+//  - Pl^(k) (lead_rows x R) and Pt^(k) (trail_cols x R) hold the level-1
+//    partial contractions of the dimension tree; M^(n,k) (I_n x R_k) the
+//    MTTKRP of the mode being updated.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#define CNCPD_KMAX 64
+#define CNCPD_NMAX 8
+#define CNCPD_RMAX 64
+
+namespace cncpd {
+
+enum Storage { ST_F64 = 0, ST_F32 = 1, ST_BF16 = 2, ST_BF16X2 = 3 };
+
+// Scalars that live on the device so that a whole sweep can be replayed as a
+// CUDA graph without host round trips.
+struct DevScalars {
+  double t;          // momentum sequence t_{k} (Appendix A)
+  double w_hat;      // hat w of the current iteration
+  int have_prev;     // L_prev valid (false in the first iteration)
+  int have_cur;      // L_cur written by a sweep
+  int nonfinite;     // set when F or a Lipschitz constant is NaN/Inf
+  int pad0;
+  double F;          // objective of the last evaluated iterate
+  double relerr;     // mean relative error of the same
+  double Fk[CNCPD_KMAX];
+  double relk[CNCPD_KMAX];
+  double xnorm2[CNCPD_KMAX];               // ||X^(k)||^2 (or ||X~^(k)||^2 on the LRA path)
+  double Lprev_u[CNCPD_NMAX][CNCPD_KMAX];  // L_u^(n,k) of the previous accepted sweep
+  double Lcur_u[CNCPD_NMAX][CNCPD_KMAX];
+  double LCprev[CNCPD_NMAX], LCcur[CNCPD_NMAX];
+  double Ldprev[CNCPD_KMAX], Ldcur[CNCPD_KMAX];
+  double cterm[CNCPD_KMAX][CNCPD_RMAX];    // (U^{odot})^T vec(X^(k)) at the current factors
+  double cterm_save[CNCPD_KMAX][CNCPD_RMAX];
+  double ip[CNCPD_KMAX];                   // <X^(k), X_hat^(k)>
+  double xhat2[CNCPD_KMAX];                // ||X_hat^(k)||^2
+  double lam1[CNCPD_KMAX][CNCPD_RMAX];     // cores: current, previous, snapshot
+  double lam2[CNCPD_KMAX][CNCPD_RMAX];
+  double lamS[CNCPD_KMAX][CNCPD_RMAX];
+  double xnorm2_orig[CNCPD_KMAX];          // ||X^(k)||^2 of the stored tensors (global fit)
+  double out_relk[CNCPD_KMAX];             // per-block relative error of an uncommitted evaluation
+};
+
+struct DevDesc {
+  int K, N, h;        // blocks, order, number of lead modes
+  int Rmax;
+  int lra;            // 1: collapsed (LRA) products replace the tensor passes
+  int pad0;
+  int R[CNCPD_KMAX];
+  int Rt[CNCPD_KMAX];  // LRA ranks
+  int L[CNCPD_NMAX];
+  int nonneg[CNCPD_NMAX];
+  int64_t dims[CNCPD_KMAX][CNCPD_NMAX];
+  int64_t lead_rows[CNCPD_KMAX];
+  int64_t trail_cols[CNCPD_KMAX];
+  const void* X[CNCPD_KMAX];
+  const void* Xlo[CNCPD_KMAX];
+  void* U1[CNCPD_KMAX][CNCPD_NMAX];
+  void* U2[CNCPD_KMAX][CNCPD_NMAX];
+  void* M[CNCPD_KMAX][CNCPD_NMAX];
+  double* G[CNCPD_KMAX][CNCPD_NMAX];
+  void* Pl[CNCPD_KMAX];
+  void* Pt[CNCPD_KMAX];
+  void* H[CNCPD_KMAX];          // D (*_{m!=n} G) D of the mode being updated, in the factor type
+  // LRA step
+  void* Ut[CNCPD_KMAX][CNCPD_NMAX];    // U~^(n,k), I_n x Rt_k
+  double* Gt[CNCPD_KMAX][CNCPD_NMAX];  // U~^T U~ (Rt x Rt)
+  double* C[CNCPD_KMAX][CNCPD_NMAX];   // U~^T U (Rt x R)
+  void* Vinv[CNCPD_KMAX];              // ALS: V^{-1} in the factor type (Rt x Rt)
+  // split-K partials of the lead-mode contraction
+  void* partial;
+  int64_t partial_off[CNCPD_KMAX];     // element offset of block k's partials
+  int nsplit[CNCPD_KMAX];
+  int64_t split_rows[CNCPD_KMAX];
+  int lt_prefix[CNCPD_KMAX + 1];       // cumulative 32-row tiles of the trailing-mode contraction
+  int tt_prefix[CNCPD_KMAX + 1];       // cumulative (column tile x split) units of the lead-mode contraction
+  int tt_ctiles[CNCPD_KMAX];           // column tiles per block
+  int tt_cpt;                          // columns per thread of that kernel
+  int pad1;
+  DevScalars* sc;
+  int* err;                            // device error word (bounded waits, bad state)
+};
+
+// -------------------------------------------------------------- helpers ----
+
+template <typename T> struct Acc;  // wide accumulator type for reductions
+template <> struct Acc<float> { typedef double type; };
+template <> struct Acc<double> { typedef double type; };
+
+template <int ST, typename T>
+__device__ __forceinline__ T load_x(const void* __restrict__ x, const void* __restrict__ xlo, int64_t i) {
+  if constexpr (ST == ST_F64) {
+    return (T)__ldg(reinterpret_cast<const double*>(x) + i);
+  } else if constexpr (ST == ST_F32) {
+    return (T)__ldg(reinterpret_cast<const float*>(x) + i);
+  } else if constexpr (ST == ST_BF16) {
+    return (T)__bfloat162float(reinterpret_cast<const __nv_bfloat16*>(x)[i]);
+  } else {
+    return (T)(__bfloat162float(reinterpret_cast<const __nv_bfloat16*>(x)[i]) +
+               __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(xlo)[i]));
+  }
+}
+
+// Mixed-radix decode of a flat C-order index over modes [m0, m1) of block k.
+__device__ __forceinline__ void decode(const DevDesc* d, int k, int m0, int m1, int64_t flat, int* idx) {
+  for (int m = m1 - 1; m >= m0; --m) {
+    int64_t I = d->dims[k][m];
+    idx[m] = (int)(flat % I);
+    flat /= I;
+  }
+}
+
+__device__ __forceinline__ int ceil_div_i(int a, int b) { return (a + b - 1) / b; }
+
+// Bucketed padded rank used as a compile-time register count.
+#define CNCPD_FOR_EACH_RP(X) X(4) X(8) X(12) X(16) X(20) X(24) X(32) X(40) X(48) X(64)
+
+inline int rank_bucket(int R) {
+  const int b[] = {4, 8, 12, 16, 20, 24, 32, 40, 48, 64};
+  for (int v : b) if (R <= v) return v;
+  return -1;
+}
+
+// ----------------------------------------------------- launch wrappers ----
+// Implemented in mttkrp.cu / update.cu / lra.cu.  `fp64` selects the FP64
+// factor path (storage ST_F64); otherwise factors are FP32.
+
+struct LaunchCfg {
+  cudaStream_t stream;
+  int num_sms;
+};
+
+// trailing-mode contraction -> Pl ; lead-mode contraction (split-K + fixed-order reduction) -> Pt
+cudaError_t launch_trailing_contract(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int st, int RP);
+cudaError_t launch_lead_contract(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int st, int RP,
+                                 const int64_t* d_red_prefix);
+int lead_cpt(int fp64, int RP);
+cudaError_t launch_level2(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int RP, int n);
+cudaError_t launch_gram(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int n_begin, int n_end, int which);
+cudaError_t launch_lipschitz(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int n, int use_core);
+cudaError_t launch_update(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int RP, int n,
+                          int use_w, double delta_w, int use_core);
+// commit = 1: write F/relerr/core term of the solver state; 0: only out_relk against xnorm2_orig
+cudaError_t launch_objective(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int RP, int commit);
+cudaError_t launch_core_update(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int use_w, double delta_w);
+cudaError_t launch_iter_begin(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc);
+cudaError_t launch_redo_prepare(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc);
+cudaError_t launch_quantize(cudaStream_t s, const void* src, int src_f64, void* dst, void* dst_lo, int st,
+                            int64_t n, double* norm2_out, double* norm2_scratch, int nblk);
+cudaError_t launch_convert(cudaStream_t s, const void* src, int src_f64, void* dst, int dst_f64, int64_t n);
+cudaError_t launch_uniform_init(cudaStream_t s, void* dst, int fp64, int64_t n, uint64_t seed);
+cudaError_t launch_lmax_host(const double* d_H, int R, double* d_out, cudaStream_t s);
+cudaError_t launch_grad(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int RP, int n, int use_core);
+// LRA
+cudaError_t launch_cross_gram(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int n_begin, int n_end);
+cudaError_t launch_collapsed_m(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int n);
+cudaError_t launch_lra_objective(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int use_core);
+cudaError_t launch_als_solve(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int n,
+                             const int* active, int* status);
+cudaError_t launch_als_apply(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int n, const int* active);
+cudaError_t launch_als_relerr(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, double* relk);
+cudaError_t launch_lra_xnorm(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc);
+
+}  // namespace cncpd

@@ -1,0 +1,694 @@
+// Small per-mode kernels of the APG sweep: Grams, Hadamard products and
+// Lipschitz constants, the fused extrapolate / gradient / step / projection
+// update with the coupled common-column sum, the objective, the core update,
+// and the bookkeeping of iterations and re-updates.
+#include "cncpd_internal.cuh"
+
+namespace cncpd {
+
+// ---------------------------------------------------------------------------
+// Largest eigenvalue of a symmetric PSD R x R matrix (R <= 64), called by a
+// whole CTA.  ||H||_2 of Eqs. eqLipsLd / eqLipsLu.  Normalised repeated
+// squaring A <- A^2 / tr(A^2) in FP32 converges to the projector on the
+// leading eigenvector (ratios of eigenvalues are raised to the power 2^s);
+// a column of the limit, refined by four FP64 power iterations, gives the
+// Rayleigh quotient v^T H v / v^T v in FP64.  Returns 0 for a zero matrix and
+// propagates NaN/Inf.
+// ---------------------------------------------------------------------------
+// Shared-memory layout of lmax_psd for an R x R problem (dynamic smem):
+// Hs (R*R doubles), v, w (R doubles each), A, B (R*R floats each), red (32 floats).
+__host__ __device__ inline size_t lmax_smem_bytes(int R) {
+  return (size_t)R * R * 8 + 2 * (size_t)R * 8 + 2 * (size_t)R * R * 4 + 32 * 4 + 16;
+}
+
+struct LmaxScratch {
+  double* Hs;
+  double* v;
+  double* w;
+  float* A;
+  float* B;
+  float* red;
+  __device__ void carve(unsigned char* base, int R) {
+    Hs = reinterpret_cast<double*>(base);
+    v = Hs + R * R;
+    w = v + R;
+    A = reinterpret_cast<float*>(w + R);
+    B = A + R * R;
+    red = B + R * R;
+  }
+};
+
+__device__ double lmax_psd(const double* Hs, int R, LmaxScratch* s) {
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int nt = blockDim.x * blockDim.y;
+  __syncthreads();
+  double tr = 0.0;
+  for (int i = 0; i < R; ++i) tr += Hs[i * R + i];
+  if (!isfinite(tr)) return tr;
+  if (!(tr > 0.0)) return 0.0;
+  const int RR = R * R;
+  for (int e = tid; e < RR; e += nt) s->A[e] = (float)(Hs[e] / tr);
+  __syncthreads();
+  for (int it = 0; it < 64; ++it) {
+    for (int e = tid; e < RR; e += nt) {
+      const int i = e / R, j = e % R;
+      float acc = 0.f;
+      for (int l = 0; l < R; ++l) acc = fmaf(s->A[i * R + l], s->A[l * R + j], acc);
+      s->B[e] = acc;
+    }
+    __syncthreads();
+    float trb = 0.f;
+    for (int i = 0; i < R; ++i) trb += s->B[i * R + i];
+    float dmax = 0.f;
+    if (trb > 0.f) {
+      for (int e = tid; e < RR; e += nt) {
+        const float nv = s->B[e] / trb;
+        dmax = fmaxf(dmax, fabsf(nv - s->A[e]));
+        s->A[e] = nv;
+      }
+    }
+    // CTA max of dmax
+    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    if ((tid & 31) == 0) s->red[tid >> 5] = dmax;
+    __syncthreads();
+    float m = 0.f;
+    for (int i = 0; i < (nt + 31) / 32; ++i) m = fmaxf(m, s->red[i]);
+    __syncthreads();
+    if (!(trb > 0.f) || m < 2e-7f) break;
+  }
+  // column of the limit with the largest diagonal entry
+  int jm = 0;
+  float dm = -1.f;
+  for (int i = 0; i < R; ++i)
+    if (s->A[i * R + i] > dm) { dm = s->A[i * R + i]; jm = i; }
+  for (int i = tid; i < R; i += nt) s->v[i] = (double)s->A[i * R + jm] + 1e-30;
+  __syncthreads();
+  for (int p = 0; p < 4; ++p) {
+    for (int i = tid; i < R; i += nt) {
+      double a = 0.0;
+      for (int l = 0; l < R; ++l) a = fma(Hs[i * R + l], s->v[l], a);
+      s->w[i] = a;
+    }
+    __syncthreads();
+    double nrm = 0.0;
+    for (int i = 0; i < R; ++i) nrm += s->w[i] * s->w[i];
+    nrm = sqrt(nrm);
+    __syncthreads();
+    if (nrm > 0.0)
+      for (int i = tid; i < R; i += nt) s->v[i] = s->w[i] / nrm;
+    __syncthreads();
+  }
+  double num = 0.0, den = 0.0;
+  for (int i = 0; i < R; ++i) {
+    double a = 0.0;
+    for (int l = 0; l < R; ++l) a = fma(Hs[i * R + l], s->v[l], a);
+    num = fma(s->v[i], a, num);
+    den = fma(s->v[i], s->v[i], den);
+  }
+  __syncthreads();
+  return den > 0.0 ? num / den : 0.0;
+}
+
+template <typename KernelT>
+static cudaError_t allow_smem(KernelT kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+__device__ __forceinline__ double extrap_weight(double w_hat, int have_prev, double Lprev, double Lcur,
+                                                double delta_w) {
+  // Eqs. eqextrawd / eqextrawu; first iteration reads the ratio as 1.
+  if (!(Lcur > 0.0)) return 0.0;
+  const double ratio = have_prev ? Lprev / Lcur : 1.0;
+  return fmin(w_hat, delta_w * sqrt(ratio));
+}
+
+// ---------------------------------------------------------------------------
+// Grams G = U^T U (Table II operation 1) of modes [n_begin, n_end) of every
+// block; which = 0: the factors U1, which = 1: the LRA factors U~.  FP32
+// partial sums over 64 rows are folded into FP64.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_gram(const DevDesc* __restrict__ d, int n_begin, int n_end, int which) {
+  const int nm = n_end - n_begin;
+  const int k = blockIdx.x / nm;
+  const int n = n_begin + blockIdx.x % nm;
+  const T* U = reinterpret_cast<const T*>(which ? d->Ut[k][n] : d->U1[k][n]);
+  const int R = which ? d->Rt[k] : d->R[k];
+  double* G = which ? d->Gt[k][n] : d->G[k][n];
+  const int64_t I = d->dims[k][n];
+  const int P = R * R;
+  __shared__ double red[256];
+  const int tid = threadIdx.x;
+  for (int p0 = 0; p0 < P; p0 += 256) {
+    const int np = min(256, P - p0);
+    const int Y = max(1, 256 / np);
+    const int p = p0 + tid % np;
+    const int y = tid / np;
+    double acc = 0.0;
+    if (y < Y && tid < np * Y) {
+      const int a = p / R, b = p % R;
+      T part = T(0);
+      int cnt = 0;
+      for (int64_t i = y; i < I; i += Y) {
+        part = fma(U[i * R + a], U[i * R + b], part);
+        if (++cnt == 64) { acc += (double)part; part = T(0); cnt = 0; }
+      }
+      acc += (double)part;
+    }
+    red[tid] = acc;
+    __syncthreads();
+    if (tid < np) {
+      double s = 0.0;
+      for (int yy = 0; yy < Y; ++yy) s += red[yy * np + tid];
+      G[p0 + tid] = s;
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_gram(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int n_begin, int n_end,
+                        int which) {
+  if (n_end <= n_begin) return cudaSuccess;
+  const int grid = hd.K * (n_end - n_begin);
+  if (fp64) k_gram<double><<<grid, 256, 0, c.stream>>>(dd, n_begin, n_end, which);
+  else k_gram<float><<<grid, 256, 0, c.stream>>>(dd, n_begin, n_end, which);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// H^(n,k) = D (*_{m != n} G^(m,k)) D (Eq. solapgU first term; Table II
+// operation 4) and L_u^(n,k) = ||H||_2 (Eq. eqLipsLu).  One CTA per block.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_lipschitz(const DevDesc* __restrict__ d, int n, int use_core, int want_L) {
+  const int k = blockIdx.x;
+  const int R = d->R[k], N = d->N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  LmaxScratch scr;
+  scr.carve(smem_raw, R);
+  double* Hs = scr.Hs;
+  DevScalars* sc = d->sc;
+  T* Hout = reinterpret_cast<T*>(d->H[k]);
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+    double h = 1.0;
+    for (int m = 0; m < N; ++m)
+      if (m != n) h *= d->G[k][m][e];
+    if (use_core) h *= sc->lam1[k][e / R] * sc->lam1[k][e % R];
+    Hs[e] = h;
+    Hout[e] = (T)h;
+  }
+  if (!want_L) return;
+  const double L = lmax_psd(Hs, R, &scr);
+  if (threadIdx.x == 0) {
+    sc->Lcur_u[n][k] = L;
+    if (!isfinite(L)) atomicExch(&sc->nonfinite, 1);
+  }
+}
+
+cudaError_t launch_lipschitz(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int n, int use_core) {
+  const size_t sm = lmax_smem_bytes(hd.Rmax);
+  cudaError_t e = fp64 ? allow_smem(k_lipschitz<double>, sm) : allow_smem(k_lipschitz<float>, sm);
+  if (e != cudaSuccess) return e;
+  if (fp64) k_lipschitz<double><<<hd.K, 256, sm, c.stream>>>(dd, n, use_core, 1);
+  else k_lipschitz<float><<<hd.K, 256, sm, c.stream>>>(dd, n, use_core, 1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Fused update of mode n for every block (Eqs. eqextraPU, solapgU, solUns,
+// solUnC, solUnsI):
+//   U_hat = U1 + w (U1 - U2)            (shared columns: one weight w_C)
+//   G_hat = U_hat H - M D
+//   individual columns: U1 <- P(U_hat - G_hat / L_u^(n,k))
+//   shared columns:     U1 <- P(U_hat_C - sum_k G_hat_C / sum_k L_u^(n,k)),
+//                       the same value written to every block
+//   U2 <- old U1.
+// Thread (c, y) owns column c of row blockIdx.x * ROWS + y, loops over the
+// blocks, and keeps the shared-column gradient sum in a register, so the
+// coupled sum needs no cross-CTA communication.  Rows are owned by exactly
+// one CTA, so the in-place write is race free.
+// ---------------------------------------------------------------------------
+template <typename T, int RP>
+__global__ void k_update(const DevDesc* __restrict__ d, int n, int use_w, double delta_w, int use_core) {
+  constexpr int ROWS = 256 / RP;
+  __shared__ T Hs[RP * RP];
+  __shared__ T uh[ROWS][RP];
+  const int c = threadIdx.x;
+  const int y = threadIdx.y;
+  const int64_t i = (int64_t)blockIdx.x * ROWS + y;
+  const int K = d->K;
+  const int Ln = d->L[n];
+  const int nonneg = d->nonneg[n];
+  DevScalars* sc = d->sc;
+  const double w_hat = use_w ? sc->w_hat : 0.0;
+  const int have_prev = sc->have_prev;
+  double LC = 0.0;
+  for (int k = 0; k < K; ++k) LC += sc->Lcur_u[n][k];
+  const T wC = (T)extrap_weight(w_hat, have_prev, sc->LCprev[n], LC, delta_w);
+  if (blockIdx.x == 0 && c == 0 && y == 0) {
+    sc->LCcur[n] = LC;
+    sc->have_cur = 1;
+  }
+
+  T sumC = T(0), uhC = T(0), u1C = T(0);
+  for (int k = 0; k < K; ++k) {
+    const int R = d->R[k];
+    const int64_t In = d->dims[k][n];
+    const double Lk = sc->Lcur_u[n][k];
+    const T wk = (T)extrap_weight(w_hat, have_prev, sc->Lprev_u[n][k], Lk, delta_w);
+    __syncthreads();
+    const T* Hk = reinterpret_cast<const T*>(d->H[k]);
+    for (int e = threadIdx.x + threadIdx.y * RP; e < RP * RP; e += RP * ROWS) {
+      const int a = e / RP, b = e % RP;
+      Hs[e] = (a < R && b < R) ? Hk[a * R + b] : T(0);
+    }
+    const bool valid = (i < In) && (c < R);
+    T* U1 = reinterpret_cast<T*>(d->U1[k][n]);
+    T* U2 = reinterpret_cast<T*>(d->U2[k][n]);
+    T u1 = T(0), u2 = T(0);
+    if (valid) {
+      u1 = U1[i * R + c];
+      u2 = U2[i * R + c];
+    }
+    const T w = (c < Ln) ? wC : wk;
+    const T uhat = u1 + w * (u1 - u2);
+    uh[y][c] = valid ? uhat : T(0);
+    __syncthreads();
+    if (valid) {
+      const T lam = use_core ? (T)sc->lam1[k][c] : T(1);
+      T g = -reinterpret_cast<const T*>(d->M[k][n])[i * R + c] * lam;
+#pragma unroll
+      for (int a = 0; a < RP; ++a) g = fma(uh[y][a], Hs[a * RP + c], g);
+      if (c >= Ln) {
+        T nv = u1;
+        if (Lk > 0.0) {
+          nv = uhat - g / (T)Lk;
+          if (nonneg) nv = nv > T(0) ? nv : T(0);
+        }
+        U2[i * R + c] = u1;
+        U1[i * R + c] = nv;
+      } else {
+        sumC += g;
+        uhC = uhat;
+        u1C = u1;
+      }
+    }
+  }
+  if (c < Ln && i < d->dims[0][n]) {
+    T nv = u1C;
+    if (LC > 0.0) {
+      nv = uhC - sumC / (T)LC;
+      if (nonneg) nv = nv > T(0) ? nv : T(0);
+    }
+    for (int k = 0; k < K; ++k) {
+      const int R = d->R[k];
+      reinterpret_cast<T*>(d->U2[k][n])[i * R + c] = u1C;
+      reinterpret_cast<T*>(d->U1[k][n])[i * R + c] = nv;
+    }
+  }
+}
+
+template <typename T, int RP>
+static cudaError_t update_impl(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int n, int use_w,
+                               double delta_w, int use_core) {
+  constexpr int ROWS = 256 / RP;
+  int64_t imax = 0;
+  for (int k = 0; k < hd.K; ++k) imax = hd.dims[k][n] > imax ? hd.dims[k][n] : imax;
+  const unsigned grid = (unsigned)((imax + ROWS - 1) / ROWS);
+  k_update<T, RP><<<grid, dim3(RP, ROWS), 0, c.stream>>>(dd, n, use_w, delta_w, use_core);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int RP, int n,
+                          int use_w, double delta_w, int use_core) {
+#define UCASE(V)                                                                       \
+  case V:                                                                              \
+    return fp64 ? update_impl<double, V>(c, dd, hd, n, use_w, delta_w, use_core)       \
+                : update_impl<float, V>(c, dd, hd, n, use_w, delta_w, use_core);
+  switch (RP) { CNCPD_FOR_EACH_RP(UCASE) }
+#undef UCASE
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Objective (Eq. costfunc) by the Gram expansion
+//   F_k = 1/2 (||X||^2 - 2 <X, X_hat> + ||X_hat||^2),
+//   <X, X_hat> = sum_r lambda_r sum_i M^(N-1)[i, r] U^(N-1)[i, r],
+//   ||X_hat||^2 = lambda^T (*_m G^(m)) lambda,
+// with M^(N-1) the MTTKRP of the last mode (computed before its update) and
+// U^(N-1) the updated factor: together they give <X, [[U]]> at the new point.
+// The per-r sums are the core term (U^{odot})^T vec(X) of Eq. solapgG for the
+// next core update.  RelErr per Section III-C.  One CTA, threads (r, y).
+// ---------------------------------------------------------------------------
+template <typename T, int RP>
+__global__ void k_objective(const DevDesc* __restrict__ d, int commit) {
+  const int r = threadIdx.x, y = threadIdx.y, Y = blockDim.y;
+  const int K = d->K, N = d->N, n = N - 1;
+  DevScalars* sc = d->sc;
+  __shared__ double red[256];
+  __shared__ double cr[RP];
+  double Fsum = 0.0, relsum = 0.0;
+  for (int k = 0; k < K; ++k) {
+    const int R = d->R[k];
+    const int64_t I = d->dims[k][n];
+    const T* M = reinterpret_cast<const T*>(d->M[k][n]);
+    const T* U = reinterpret_cast<const T*>(d->U1[k][n]);
+    double acc = 0.0;
+    if (r < R)
+      for (int64_t i = y; i < I; i += Y) acc = fma((double)M[i * R + r], (double)U[i * R + r], acc);
+    red[y * RP + r] = acc;
+    __syncthreads();
+    if (y == 0) {
+      double s = 0.0;
+      for (int yy = 0; yy < Y; ++yy) s += red[yy * RP + r];
+      cr[r] = s;
+      if (r < R && commit) sc->cterm[k][r] = s;
+    }
+    __syncthreads();
+    if (r == 0 && y == 0) {
+      double ip = 0.0, xx = 0.0;
+      for (int a = 0; a < R; ++a) {
+        const double la = sc->lam1[k][a];
+        ip += la * cr[a];
+        for (int b = 0; b < R; ++b) {
+          double g = 1.0;
+          for (int m = 0; m < N; ++m) g *= d->G[k][m][a * R + b];
+          xx += la * sc->lam1[k][b] * g;
+        }
+      }
+      const double x2 = commit ? sc->xnorm2[k] : sc->xnorm2_orig[k];
+      const double Fk = 0.5 * (x2 - 2.0 * ip + xx);
+      const double rel = x2 > 0.0 ? sqrt(fmax(2.0 * Fk, 0.0) / x2) : 0.0;
+      if (commit) {
+        sc->Fk[k] = Fk;
+        sc->relk[k] = rel;
+        sc->ip[k] = ip;
+        sc->xhat2[k] = xx;
+      } else {
+        sc->out_relk[k] = rel;
+      }
+      Fsum += Fk;
+      relsum += rel;
+    }
+    __syncthreads();
+  }
+  if (r == 0 && y == 0 && commit) {
+    sc->F = Fsum;
+    sc->relerr = relsum / K;
+    if (!isfinite(Fsum)) sc->nonfinite = 1;
+  }
+}
+
+cudaError_t launch_objective(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int RP, int commit) {
+#define OCASE(V)                                                                                \
+  case V:                                                                                       \
+    if (fp64) k_objective<double, V><<<1, dim3(V, 256 / V), 0, c.stream>>>(dd, commit);         \
+    else k_objective<float, V><<<1, dim3(V, 256 / V), 0, c.stream>>>(dd, commit);               \
+    return cudaGetLastError();
+  switch (RP) { CNCPD_FOR_EACH_RP(OCASE) }
+#undef OCASE
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Core update of Eqs. solD / solapgG / eqextraPG with L_d = ||(U^T U)^*||_2
+// (Eq. eqLipsLd) and the weight of Eq. eqextrawd.  One CTA per block, FP64.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_core_update(const DevDesc* __restrict__ d, int use_w, double delta_w) {
+  const int k = blockIdx.x;
+  const int R = d->R[k], N = d->N;
+  DevScalars* sc = d->sc;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  LmaxScratch scr;
+  scr.carve(smem_raw, R);
+  double* Hs = scr.Hs;
+  __shared__ double lh[CNCPD_RMAX];
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+    double h = 1.0;
+    for (int m = 0; m < N; ++m) h *= d->G[k][m][e];
+    Hs[e] = h;
+  }
+  const double Ld = lmax_psd(Hs, R, &scr);
+  const double w = extrap_weight(use_w ? sc->w_hat : 0.0, sc->have_prev, sc->Ldprev[k], Ld, delta_w);
+  for (int a = threadIdx.x; a < R; a += blockDim.x) lh[a] = sc->lam1[k][a] + w * (sc->lam1[k][a] - sc->lam2[k][a]);
+  __syncthreads();
+  if (Ld > 0.0) {
+    for (int a = threadIdx.x; a < R; a += blockDim.x) {
+      double g = -sc->cterm[k][a];
+      for (int b = 0; b < R; ++b) g = fma(Hs[a * R + b], lh[b], g);
+      const double nv = fmax(0.0, lh[a] - g / Ld);
+      sc->lam2[k][a] = sc->lam1[k][a];
+      sc->lam1[k][a] = nv;
+    }
+  } else {
+    for (int a = threadIdx.x; a < R; a += blockDim.x) sc->lam2[k][a] = sc->lam1[k][a];
+  }
+  if (threadIdx.x == 0) {
+    sc->Ldcur[k] = Ld;
+    if (!isfinite(Ld)) sc->nonfinite = 1;
+  }
+}
+
+cudaError_t launch_core_update(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int use_w, double delta_w) {
+  const size_t sm = lmax_smem_bytes(hd.Rmax);
+  cudaError_t e = allow_smem(k_core_update, sm);
+  if (e != cudaSuccess) return e;
+  k_core_update<<<hd.K, 256, sm, c.stream>>>(dd, use_w, delta_w);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Iteration bookkeeping.  Begin: t_k and hat w (Appendix A), commit the
+// Lipschitz constants of the last accepted sweep as L_{k-2}, snapshot the
+// core term and lambda_2 (the factor snapshot is a device memcpy).
+// Redo: restore lambda and the core term for the w = 0 re-update.
+// ---------------------------------------------------------------------------
+__global__ void k_iter_begin(const DevDesc* __restrict__ d) {
+  DevScalars* sc = d->sc;
+  const int K = d->K, N = d->N;
+  const int tid = threadIdx.x;
+  const int have_cur = sc->have_cur;
+  __syncthreads();
+  if (tid == 0) {
+    const double t = sc->t;
+    const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+    sc->w_hat = (t - 1.0) / tn;
+    sc->t = tn;
+  }
+  if (have_cur) {
+    for (int e = tid; e < N * CNCPD_KMAX; e += blockDim.x) {
+      const int n = e / CNCPD_KMAX, k = e % CNCPD_KMAX;
+      sc->Lprev_u[n][k] = sc->Lcur_u[n][k];
+    }
+    for (int n = tid; n < N; n += blockDim.x) sc->LCprev[n] = sc->LCcur[n];
+    for (int k = tid; k < K; k += blockDim.x) sc->Ldprev[k] = sc->Ldcur[k];
+  }
+  for (int e = tid; e < K * CNCPD_RMAX; e += blockDim.x) {
+    const int k = e / CNCPD_RMAX, r = e % CNCPD_RMAX;
+    sc->cterm_save[k][r] = sc->cterm[k][r];
+    sc->lamS[k][r] = sc->lam2[k][r];
+  }
+  __syncthreads();
+  if (tid == 0 && have_cur) sc->have_prev = 1;
+}
+
+__global__ void k_redo_prepare(const DevDesc* __restrict__ d) {
+  DevScalars* sc = d->sc;
+  const int K = d->K;
+  for (int e = threadIdx.x; e < K * CNCPD_RMAX; e += blockDim.x) {
+    const int k = e / CNCPD_RMAX, r = e % CNCPD_RMAX;
+    sc->lam1[k][r] = sc->lam2[k][r];
+    sc->lam2[k][r] = sc->lamS[k][r];
+    sc->cterm[k][r] = sc->cterm_save[k][r];
+  }
+}
+
+cudaError_t launch_iter_begin(const LaunchCfg& c, const DevDesc* dd, const DevDesc&) {
+  k_iter_begin<<<1, 256, 0, c.stream>>>(dd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_redo_prepare(const LaunchCfg& c, const DevDesc* dd, const DevDesc&) {
+  k_redo_prepare<<<1, 256, 0, c.stream>>>(dd);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Gradient at the current factors (no extrapolation), Eq. solbpgU:
+//   dF/dU^(n,k) = U D (U^T U)^{*-n} D - X_(n) U^{odot-n} D,
+// written over the M buffer of (n, k).  Threads (c, y) like the update.
+// ---------------------------------------------------------------------------
+template <typename T, int RP>
+__global__ void k_grad(const DevDesc* __restrict__ d, int n, int use_core) {
+  constexpr int ROWS = 256 / RP;
+  __shared__ T Hs[RP * RP];
+  __shared__ T us[ROWS][RP];
+  const int c = threadIdx.x, y = threadIdx.y;
+  const int64_t i = (int64_t)blockIdx.x * ROWS + y;
+  const int k = blockIdx.y;
+  const int R = d->R[k];
+  const int64_t In = d->dims[k][n];
+  DevScalars* sc = d->sc;
+  const T* Hk = reinterpret_cast<const T*>(d->H[k]);
+  for (int e = threadIdx.x + threadIdx.y * RP; e < RP * RP; e += RP * ROWS) {
+    const int a = e / RP, b = e % RP;
+    Hs[e] = (a < R && b < R) ? Hk[a * R + b] : T(0);
+  }
+  const bool valid = (i < In) && (c < R);
+  const T* U1 = reinterpret_cast<const T*>(d->U1[k][n]);
+  us[y][c] = valid ? U1[i * R + c] : T(0);
+  __syncthreads();
+  if (valid) {
+    T* M = reinterpret_cast<T*>(d->M[k][n]);
+    const T lam = use_core ? (T)sc->lam1[k][c] : T(1);
+    T g = -M[i * R + c] * lam;
+#pragma unroll
+    for (int a = 0; a < RP; ++a) g = fma(us[y][a], Hs[a * RP + c], g);
+    M[i * R + c] = g;
+  }
+}
+
+cudaError_t launch_grad(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int RP, int n,
+                        int use_core) {
+  int64_t imax = 0;
+  for (int k = 0; k < hd.K; ++k) imax = hd.dims[k][n] > imax ? hd.dims[k][n] : imax;
+  {
+    const size_t sm = lmax_smem_bytes(hd.Rmax);
+    cudaError_t e = fp64 ? allow_smem(k_lipschitz<double>, sm) : allow_smem(k_lipschitz<float>, sm);
+    if (e != cudaSuccess) return e;
+    if (fp64) k_lipschitz<double><<<hd.K, 256, sm, c.stream>>>(dd, n, use_core, 0);
+    else k_lipschitz<float><<<hd.K, 256, sm, c.stream>>>(dd, n, use_core, 0);
+  }
+#define GCASE(V)                                                                        \
+  case V: {                                                                             \
+    dim3 grid((unsigned)((imax + 256 / V - 1) / (256 / V)), hd.K);                      \
+    if (fp64) k_grad<double, V><<<grid, dim3(V, 256 / V), 0, c.stream>>>(dd, n, use_core); \
+    else k_grad<float, V><<<grid, dim3(V, 256 / V), 0, c.stream>>>(dd, n, use_core);    \
+    return cudaGetLastError();                                                          \
+  }
+  switch (RP) { CNCPD_FOR_EACH_RP(GCASE) }
+#undef GCASE
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Data preparation: quantise X into the storage type and take ||X_stored||^2
+// in FP64 (per-CTA partial sums, then a fixed-order sum).
+// ---------------------------------------------------------------------------
+template <typename S>
+__global__ void k_quantize(const S* __restrict__ src, void* dst, void* dst_lo, int st, int64_t n, double* part) {
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = (double)src[i];
+    double q;
+    if (st == ST_F64) {
+      reinterpret_cast<double*>(dst)[i] = x;
+      q = x;
+    } else if (st == ST_F32) {
+      const float f = (float)x;
+      reinterpret_cast<float*>(dst)[i] = f;
+      q = f;
+    } else if (st == ST_BF16) {
+      const __nv_bfloat16 b = __double2bfloat16(x);
+      reinterpret_cast<__nv_bfloat16*>(dst)[i] = b;
+      q = (double)__bfloat162float(b);
+    } else {
+      const float f = (float)x;
+      const __nv_bfloat16 hi = __float2bfloat16_rn(f);
+      const __nv_bfloat16 lo = __float2bfloat16_rn(f - __bfloat162float(hi));
+      reinterpret_cast<__nv_bfloat16*>(dst)[i] = hi;
+      reinterpret_cast<__nv_bfloat16*>(dst_lo)[i] = lo;
+      q = (double)(__bfloat162float(hi) + __bfloat162float(lo));
+    }
+    acc = fma(q, q, acc);
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_sum_partials(const double* part, int n, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += part[i];
+    *out = s;
+  }
+}
+
+cudaError_t launch_quantize(cudaStream_t s, const void* src, int src_f64, void* dst, void* dst_lo, int st, int64_t n,
+                            double* norm2_out, double* scratch, int nblk) {
+  if (src_f64) k_quantize<double><<<nblk, 256, 0, s>>>(reinterpret_cast<const double*>(src), dst, dst_lo, st, n, scratch);
+  else k_quantize<float><<<nblk, 256, 0, s>>>(reinterpret_cast<const float*>(src), dst, dst_lo, st, n, scratch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_sum_partials<<<1, 32, 0, s>>>(scratch, nblk, norm2_out);
+  return cudaGetLastError();
+}
+
+__global__ void k_convert(const void* src, int src_f64, void* dst, int dst_f64, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = src_f64 ? reinterpret_cast<const double*>(src)[i] : (double)reinterpret_cast<const float*>(src)[i];
+    if (dst_f64) reinterpret_cast<double*>(dst)[i] = v;
+    else reinterpret_cast<float*>(dst)[i] = (float)v;
+  }
+}
+
+cudaError_t launch_convert(cudaStream_t s, const void* src, int src_f64, void* dst, int dst_f64, int64_t n) {
+  if (n <= 0) return cudaSuccess;
+  int grid = (int)((n + 255) / 256);
+  if (grid > 4096) grid = 4096;
+  k_convert<<<grid, 256, 0, s>>>(src, src_f64, dst, dst_f64, n);
+  return cudaGetLastError();
+}
+
+// Uniform[0,1) from the SplitMix64 finaliser of (seed, index) (Steele,
+// Lea and Flood, OOPSLA 2014) -- the library's default initialisation.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_uniform(void* dst, int fp64, int64_t n, uint64_t seed) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t z = splitmix64(seed ^ splitmix64((uint64_t)i));
+    const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    if (fp64) reinterpret_cast<double*>(dst)[i] = u;
+    else reinterpret_cast<float*>(dst)[i] = (float)u;
+  }
+}
+
+cudaError_t launch_uniform_init(cudaStream_t s, void* dst, int fp64, int64_t n, uint64_t seed) {
+  if (n <= 0) return cudaSuccess;
+  int grid = (int)((n + 255) / 256);
+  if (grid > 1024) grid = 1024;
+  k_uniform<<<grid, 256, 0, s>>>(dst, fp64, n, seed);
+  return cudaGetLastError();
+}
+
+__global__ void k_lmax_one(const double* H, int R, double* out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  LmaxScratch scr;
+  scr.carve(smem_raw, R);
+  double* Hs = scr.Hs;
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) Hs[e] = H[e];
+  const double L = lmax_psd(Hs, R, &scr);
+  if (threadIdx.x == 0) *out = L;
+}
+
+cudaError_t launch_lmax_host(const double* d_H, int R, double* d_out, cudaStream_t s) {
+  const size_t sm = lmax_smem_bytes(R);
+  cudaError_t e = allow_smem(k_lmax_one, sm);
+  if (e != cudaSuccess) return e;
+  k_lmax_one<<<1, 256, sm, s>>>(d_H, R, d_out);
+  return cudaGetLastError();
+}
+
+}  // namespace cncpd
