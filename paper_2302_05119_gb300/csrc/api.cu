@@ -129,8 +129,8 @@ void plan_lead_splits(cncpd_ctx* c, DevDesc& d, int RP, int fp64, size_t* partia
   const int cpt = lead_cpt(fp64, RP);
   int64_t tot_rows = 0;
   for (int k = 0; k < d.K; ++k) tot_rows += d.lead_rows[k];
-  // aim for ~4 CTAs per SM in total, at least 64 rows per split
-  const int64_t target_units = (int64_t)c->num_sms * 4;
+  // aim for ~2 CTAs (of 256 threads) per SM in total, at least 64 rows per split
+  const int64_t target_units = (int64_t)c->num_sms * 2;
   d.tt_prefix[0] = 0;
   size_t off = 0;
   for (int k = 0; k < d.K; ++k) {
@@ -155,7 +155,7 @@ void plan_lead_splits(cncpd_ctx* c, DevDesc& d, int RP, int fp64, size_t* partia
 
 void plan_trailing_tiles(DevDesc& d) {
   d.lt_prefix[0] = 0;
-  for (int k = 0; k < d.K; ++k) d.lt_prefix[k + 1] = d.lt_prefix[k] + (int)((d.lead_rows[k] + 31) / 32);
+  for (int k = 0; k < d.K; ++k) d.lt_prefix[k + 1] = d.lt_prefix[k] + (int)((d.lead_rows[k] + 63) / 64);
 }
 
 int upload_desc(cncpd_ctx* c) {
@@ -195,8 +195,10 @@ int propagate_common(cncpd_ctx* c, char* arena) {
 
 int record(cncpd_ctx* c, int which_ev) {
   if (!c->opts.profile) return CNCPD_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CU(cudaStreamIsCapturing(c->stream, &cs));
   CU(cudaEventRecordWithFlags(c->ev[which_ev], c->stream,
-                              c->opts.use_graph ? cudaEventRecordExternal : cudaEventRecordDefault));
+                              cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault));
   return CNCPD_OK;
 }
 
@@ -241,8 +243,7 @@ int enqueue_sweep(cncpd_ctx* c, int use_w) {
     }
     TRY(enqueue_mode_m(c, n));
     CU(launch_lipschitz(lc, c->dd, c->hd, c->fp64, n, core));
-    CU(launch_update(lc, c->dd, c->hd, c->fp64, c->RP, n, use_w, dw, core));
-    CU(launch_gram(lc, c->dd, c->hd, c->fp64, n, n + 1, 0));
+    CU(launch_update(lc, c->dd, c->hd, c->fp64, c->RP, n, use_w, dw, core));  // includes the Gram of U^(n)
     if (c->lra) CU(launch_cross_gram(lc, c->dd, c->hd, c->fp64, n, n + 1));
   }
   if (c->lra) CU(launch_lra_objective(lc, c->dd, c->hd, c->fp64, core));
@@ -379,7 +380,7 @@ long long kernels_per_replay(cncpd_ctx* c, int redo) {
     const int gsize = (m < c->h) ? c->h : c->N - c->h;
     if (c->lra) n += 2;     // collapsed M, cross Gram
     else if (gsize > 1) n += 1;
-    n += 3;                 // Lipschitz, update, Gram
+    n += 2;                 // Lipschitz, update (with the Gram)
   }
   n += 1;                   // objective
   n += redo ? (c->lra ? 3 : 2) : 1;
@@ -701,6 +702,11 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
   plan_lead_splits(c, d, c->RP, c->fp64, &pel);
   plan_trailing_tiles(d);
   CTRY(dalloc(c, &d.partial, pel * c->fsz));
+  {
+    int gmax = 1;
+    for (int n = 0; n < N; ++n) gmax = std::max(gmax, update_grid(d, c->RP, n));
+    CTRY(dalloc(c, (void**)&d.gpart, (size_t)gmax * K * c->Rmax * c->Rmax * sizeof(double)));
+  }
   {
     std::vector<int64_t> pre(K + 1, 0);
     for (int k = 0; k < K; ++k) pre[k + 1] = pre[k] + d.trail_cols[k] * R[k];

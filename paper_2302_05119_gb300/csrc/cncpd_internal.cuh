@@ -53,6 +53,7 @@ struct DevScalars {
   double lamS[CNCPD_KMAX][CNCPD_RMAX];
   double xnorm2_orig[CNCPD_KMAX];          // ||X^(k)||^2 of the stored tensors (global fit)
   double out_relk[CNCPD_KMAX];             // per-block relative error of an uncommitted evaluation
+  int done_counter[CNCPD_NMAX + 2];        // arrival counters of last-CTA reductions (reset by the last CTA)
 };
 
 struct DevDesc {
@@ -86,7 +87,8 @@ struct DevDesc {
   int64_t partial_off[CNCPD_KMAX];     // element offset of block k's partials
   int nsplit[CNCPD_KMAX];
   int64_t split_rows[CNCPD_KMAX];
-  int lt_prefix[CNCPD_KMAX + 1];       // cumulative 32-row tiles of the trailing-mode contraction
+  double* gpart;                        // per-CTA partial Grams of the fused update (FP64)
+  int lt_prefix[CNCPD_KMAX + 1];       // cumulative 64-row tiles of the trailing-mode contraction
   int tt_prefix[CNCPD_KMAX + 1];       // cumulative (column tile x split) units of the lead-mode contraction
   int tt_ctiles[CNCPD_KMAX];           // column tiles per block
   int tt_cpt;                          // columns per thread of that kernel
@@ -152,6 +154,7 @@ int lead_cpt(int fp64, int RP);
 cudaError_t launch_level2(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int RP, int n);
 cudaError_t launch_gram(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int n_begin, int n_end, int which);
 cudaError_t launch_lipschitz(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int n, int use_core);
+int update_grid(const DevDesc& h_desc, int RP, int n);
 cudaError_t launch_update(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int RP, int n,
                           int use_w, double delta_w, int use_core);
 // commit = 1: write F/relerr/core term of the solver state; 0: only out_relk against xnorm2_orig

@@ -17,19 +17,25 @@
 namespace cncpd {
 
 // ---------------------------------------------------------------------------
-// Trailing contraction: one warp owns 32 consecutive rows (one per lane) and
-// walks the columns in chunks of 32.  A chunk of X (32 rows x 32 columns) is
-// loaded row-coalesced into shared memory and read back transposed; the
-// 32 x R chunk of W_t is formed by the warp itself, so warps never wait on
-// each other.
+// Trailing contraction: one warp owns 64 consecutive rows (lane l: rows l and
+// l + 32) and walks the columns in chunks of 32.  A 64 x 32 chunk of X is
+// loaded row-coalesced (128-bit loads when the row length allows) into a
+// padded shared tile and read back transposed as float4 (row stride 36
+// floats: conflict-free); the 32 x R chunk of W_t is formed by the warp
+// itself, so warps never wait on each other.
 // ---------------------------------------------------------------------------
+template <typename T> struct TrailCfg;
+template <> struct TrailCfg<float> { static constexpr int XS = 36; };
+template <> struct TrailCfg<double> { static constexpr int XS = 34; };
+
 template <int ST, typename T, int RP, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
 k_trailing_contract(const DevDesc* __restrict__ d) {
-  constexpr int XS = 33;
+  constexpr int XS = TrailCfg<T>::XS;
+  constexpr int TR = 64;  // rows per warp tile
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T (*xs)[32][XS] = reinterpret_cast<T (*)[32][XS]>(smem_raw);
-  T (*ws)[32][RP] = reinterpret_cast<T (*)[32][RP]>(smem_raw + sizeof(T) * WARPS * 32 * XS);
+  T (*xs)[TR][XS] = reinterpret_cast<T (*)[TR][XS]>(smem_raw);
+  T (*ws)[32][RP] = reinterpret_cast<T (*)[32][RP]>(smem_raw + sizeof(T) * WARPS * TR * XS);
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int K = d->K, N = d->N, h = d->h;
@@ -37,65 +43,109 @@ k_trailing_contract(const DevDesc* __restrict__ d) {
   for (int g = blockIdx.x * WARPS + warp; g < total; g += gridDim.x * WARPS) {
     int k = 0;
     while (d->lt_prefix[k + 1] <= g) ++k;
-    const int64_t row0 = (int64_t)(g - d->lt_prefix[k]) * 32;
+    const int64_t row0 = (int64_t)(g - d->lt_prefix[k]) * TR;
     const int64_t rows = d->lead_rows[k];
     const int64_t J = d->trail_cols[k];
     const int R = d->R[k];
     const void* X = d->X[k];
     const void* Xlo = d->Xlo[k];
-    T acc[RP];
+    const bool vec = (ST == ST_F32) && (J % 4 == 0);
+    T acc0[RP], acc1[RP];
 #pragma unroll
-    for (int r = 0; r < RP; ++r) acc[r] = T(0);
+    for (int r = 0; r < RP; ++r) acc0[r] = acc1[r] = T(0);
     for (int64_t j0 = 0; j0 < J; j0 += 32) {
       // W_t chunk: lane forms the row for column j0 + lane.
       {
         const int64_t j = j0 + lane;
         T w[RP];
+#pragma unroll
+        for (int r = 0; r < RP; ++r) w[r] = (r < R && j < J) ? T(1) : T(0);
         if (j < J) {
           int idx[CNCPD_NMAX];
           decode(d, k, h, N, j, idx);
-#pragma unroll
-          for (int r = 0; r < RP; ++r) w[r] = (r < R) ? T(1) : T(0);
           for (int m = h; m < N; ++m) {
             const T* U = reinterpret_cast<const T*>(d->U1[k][m]) + (int64_t)idx[m] * R;
 #pragma unroll
             for (int r = 0; r < RP; ++r)
               if (r < R) w[r] *= U[r];
           }
-        } else {
-#pragma unroll
-          for (int r = 0; r < RP; ++r) w[r] = T(0);
         }
 #pragma unroll
         for (int r = 0; r < RP; ++r) ws[warp][lane][r] = w[r];
       }
-      // X chunk, row-coalesced: instruction q loads 32 consecutive columns of row row0+q.
-      {
-        const int64_t j = j0 + lane;
-        const bool jok = j < J;
+      // X chunk (64 x 32) into the padded tile
+      if constexpr (ST == ST_F32) {
+        if (vec && j0 + 32 <= J) {
+          const float* Xf = reinterpret_cast<const float*>(X);
+          const int cq = (lane & 7) * 4;
+          float4 v[16];
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int64_t row = row0 + q * 4 + (lane >> 3);
+            v[q] = (row < rows) ? __ldg(reinterpret_cast<const float4*>(Xf + row * J + j0 + cq))
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+#pragma unroll
+          for (int q = 0; q < 16; ++q) *reinterpret_cast<float4*>(&xs[warp][q * 4 + (lane >> 3)][cq]) = v[q];
+        } else {
+          const int64_t j = j0 + lane;
 #pragma unroll 8
-        for (int q = 0; q < 32; ++q) {
+          for (int q = 0; q < TR; ++q) {
+            const int64_t row = row0 + q;
+            xs[warp][q][lane] = (j < J && row < rows) ? load_x<ST, T>(X, Xlo, row * J + j) : T(0);
+          }
+        }
+      } else {
+        const int64_t j = j0 + lane;
+#pragma unroll 8
+        for (int q = 0; q < TR; ++q) {
           const int64_t row = row0 + q;
-          T v = T(0);
-          if (jok && row < rows) v = load_x<ST, T>(X, Xlo, row * J + j);
-          xs[warp][q][lane] = v;
+          xs[warp][q][lane] = (j < J && row < rows) ? load_x<ST, T>(X, Xlo, row * J + j) : T(0);
         }
       }
       __syncwarp();
-#pragma unroll 4
-      for (int jj = 0; jj < 32; ++jj) {
-        const T x = xs[warp][lane][jj];
+      if constexpr (sizeof(T) == 4) {
+#pragma unroll 2
+        for (int jj = 0; jj < 32; jj += 4) {
+          const float4 xa = *reinterpret_cast<const float4*>(&xs[warp][lane][jj]);
+          const float4 xb = *reinterpret_cast<const float4*>(&xs[warp][lane + 32][jj]);
+          const float a4[4] = {xa.x, xa.y, xa.z, xa.w};
+          const float b4[4] = {xb.x, xb.y, xb.z, xb.w};
 #pragma unroll
-        for (int r = 0; r < RP; ++r) acc[r] = fma(x, ws[warp][jj][r], acc[r]);
+          for (int q = 0; q < 4; ++q) {
+#pragma unroll
+            for (int r = 0; r < RP; ++r) {
+              const T wv = ws[warp][jj + q][r];
+              acc0[r] = fma(a4[q], wv, acc0[r]);
+              acc1[r] = fma(b4[q], wv, acc1[r]);
+            }
+          }
+        }
+      } else {
+#pragma unroll 4
+        for (int jj = 0; jj < 32; ++jj) {
+          const T xa = xs[warp][lane][jj];
+          const T xb = xs[warp][lane + 32][jj];
+#pragma unroll
+          for (int r = 0; r < RP; ++r) {
+            const T wv = ws[warp][jj][r];
+            acc0[r] = fma(xa, wv, acc0[r]);
+            acc1[r] = fma(xb, wv, acc1[r]);
+          }
+        }
       }
       __syncwarp();
     }
-    const int64_t row = row0 + lane;
-    if (row < rows) {
-      T* P = reinterpret_cast<T*>(d->Pl[k]) + row * R;
+    T* P = reinterpret_cast<T*>(d->Pl[k]);
+    if (row0 + lane < rows) {
 #pragma unroll
       for (int r = 0; r < RP; ++r)
-        if (r < R) P[r] = acc[r];
+        if (r < R) P[(row0 + lane) * R + r] = acc0[r];
+    }
+    if (row0 + lane + 32 < rows) {
+#pragma unroll
+      for (int r = 0; r < RP; ++r)
+        if (r < R) P[(row0 + lane + 32) * R + r] = acc1[r];
     }
   }
 }
@@ -147,9 +197,11 @@ struct VecLoad {
 };
 
 template <int ST, typename T, int RP, int CPT>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(256)
 k_lead_contract(const DevDesc* __restrict__ d) {
-  constexpr int CH = 64;  // rows per W_l chunk
+  constexpr int CH = 64;   // rows per W_l chunk
+  constexpr int GR = 4;    // row groups (threads 64*g .. 64*g+63)
+  constexpr int UNR = 4;   // rows loaded per batch by one thread
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T (*wsm)[RP] = reinterpret_cast<T (*)[RP]>(smem_raw);
   T* red = reinterpret_cast<T*>(smem_raw + sizeof(T) * CH * RP);
@@ -194,25 +246,38 @@ k_lead_contract(const DevDesc* __restrict__ d) {
       __syncthreads();
       const int nrow = (int)min((int64_t)CH, re - r0);
       if (col0 < J) {
-#pragma unroll 2
-        for (int i = ty; i < nrow; i += 2) {
-          T x[CPT];
-          VecLoad<ST, T, CPT>::run(X, Xlo, (r0 + i) * J, col0, J, vec_ok, x);
+        for (int i = ty; i < nrow; i += GR * UNR) {
+          T x[UNR][CPT];
 #pragma unroll
-          for (int r = 0; r < RP; ++r) {
-            const T w = wsm[i][r];
+          for (int q = 0; q < UNR; ++q) {
+            const int ii = i + q * GR;
+            if (ii < nrow) {
+              VecLoad<ST, T, CPT>::run(X, Xlo, (r0 + ii) * J, col0, J, vec_ok, x[q]);
+            } else {
 #pragma unroll
-            for (int c = 0; c < CPT; ++c) acc[c][r] = fma(x[c], w, acc[c][r]);
+              for (int c = 0; c < CPT; ++c) x[q][c] = T(0);
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < UNR; ++q) {
+            const int ii = min(i + q * GR, CH - 1);
+#pragma unroll
+            for (int r = 0; r < RP; ++r) {
+              const T w = wsm[ii][r];
+#pragma unroll
+              for (int c = 0; c < CPT; ++c) acc[c][r] = fma(x[q][c], w, acc[c][r]);
+            }
           }
         }
       }
     }
+    // reduce the GR row groups (groups 1..GR-1 park their sums in shared memory)
     __syncthreads();
-    if (ty == 1) {
+    if (ty > 0) {
 #pragma unroll
       for (int c = 0; c < CPT; ++c)
 #pragma unroll
-        for (int r = 0; r < RP; ++r) red[(tx * CPT + c) * RP + r] = acc[c][r];
+        for (int r = 0; r < RP; ++r) red[((ty - 1) * 64 * CPT + tx * CPT + c) * RP + r] = acc[c][r];
     }
     __syncthreads();
     if (ty == 0) {
@@ -222,8 +287,13 @@ k_lead_contract(const DevDesc* __restrict__ d) {
         const int64_t col = col0 + c;
         if (col < J) {
 #pragma unroll
-          for (int r = 0; r < RP; ++r)
-            if (r < R) part[col * R + r] = acc[c][r] + red[(tx * CPT + c) * RP + r];
+          for (int r = 0; r < RP; ++r) {
+            if (r < R) {
+              T s = acc[c][r];
+              for (int g = 1; g < GR; ++g) s += red[((g - 1) * 64 * CPT + tx * CPT + c) * RP + r];
+              part[col * R + r] = s;
+            }
+          }
         }
       }
     }
@@ -249,11 +319,28 @@ __global__ void k_reduce_splits(const DevDesc* __restrict__ d, const int64_t* __
 }
 
 // ---------------------------------------------------------------------------
-// Level 2: M^(n)[i_n, r] = sum over the other modes of n's group of
-// P[.., r] * prod U^(m)[i_m, r].  One CTA per (i_n, block); threads (r, y).
+// Level 2: with the level-1 partial P of n's group viewed as [A][I_n][B][R]
+// (A = product of the group's sizes before n, B = after n),
+//   M^(n)[i_n, r] = sum_{a,b} P[a, i_n, b, r] * Wa[a, r] * Wb[b, r],
+// Wa / Wb the Khatri-Rao rows of the group's other factors.  One CTA per
+// (i_n, block); thread t keeps r = t mod R fixed and strides over the flat
+// (a, b, r) range, so consecutive threads read consecutive P entries.
 // ---------------------------------------------------------------------------
-template <typename T, int RP>
-__global__ void k_level2(const DevDesc* __restrict__ d, int n) {
+template <typename T>
+__device__ __forceinline__ T kr_row(const DevDesc* d, int k, int m0, int m1, int64_t flat, int r, int R) {
+  // prod_{m in [m0, m1)} U^(m)[i_m(flat), r]  (C-order mixed radix)
+  T w = T(1);
+  for (int m = m1 - 1; m >= m0; --m) {
+    const int64_t I = d->dims[k][m];
+    const int64_t im = flat % I;
+    flat /= I;
+    w *= reinterpret_cast<const T*>(d->U1[k][m])[im * R + r];
+  }
+  return w;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_level2(const DevDesc* __restrict__ d, int n) {
   const int k = blockIdx.y;
   const int64_t in = blockIdx.x;
   const int N = d->N, h = d->h;
@@ -262,40 +349,37 @@ __global__ void k_level2(const DevDesc* __restrict__ d, int n) {
   if (in >= In) return;
   const int R = d->R[k];
   const T* P = reinterpret_cast<const T*>((n < h) ? d->Pl[k] : d->Pt[k]);
-  T* M = reinterpret_cast<T*>(d->M[k][n]);
-  const int64_t total = (n < h) ? d->lead_rows[k] : d->trail_cols[k];
-  const int64_t Q = total / In;
-  const int r = threadIdx.x;
-  const int y = threadIdx.y, Y = blockDim.y;
-  typedef typename Acc<T>::type A;
-  A acc = 0;
-  if (r < R) {
-    for (int64_t q = y; q < Q; q += Y) {
-      // decode q over the group's modes other than n (C order), then compose the row.
-      int idx[CNCPD_NMAX];
-      int64_t f = q;
-      for (int m = m1 - 1; m >= m0; --m) {
-        if (m == n) continue;
-        const int64_t I = d->dims[k][m];
-        idx[m] = (int)(f % I);
-        f /= I;
-      }
-      idx[n] = (int)in;
-      int64_t row = 0;
-      for (int m = m0; m < m1; ++m) row = row * d->dims[k][m] + idx[m];
-      T p = P[row * R + r];
-      for (int m = m0; m < m1; ++m)
-        if (m != n) p *= reinterpret_cast<const T*>(d->U1[k][m])[(int64_t)idx[m] * R + r];
-      acc += (A)p;
+  int64_t A = 1, B = 1;
+  for (int m = m0; m < n; ++m) A *= d->dims[k][m];
+  for (int m = n + 1; m < m1; ++m) B *= d->dims[k][m];
+  const int64_t BR = B * R;
+  const int stride = (blockDim.x / R) * R;
+  const int t = threadIdx.x;
+  typedef typename Acc<T>::type AT;
+  AT acc = 0;
+  const int r = t % R;
+  if (t < stride) {
+    const int64_t total = A * BR;
+    const int64_t sq = stride / BR, sr = stride % BR;
+    int64_t a = t / BR, e = t % BR;
+    for (int64_t f = t; f < total; f += stride) {
+      const int64_t b = e / R;
+      T p = P[(a * In + in) * BR + e];
+      if (A > 1) p *= kr_row<T>(d, k, m0, n, a, r, R);
+      if (B > 1) p *= kr_row<T>(d, k, n + 1, m1, b, r, R);
+      acc += (AT)p;
+      a += sq;
+      e += sr;
+      if (e >= BR) { e -= BR; ++a; }
     }
   }
-  __shared__ A red[256];
-  red[y * RP + r] = acc;
+  __shared__ AT red[256];
+  red[t] = acc;
   __syncthreads();
-  if (y == 0 && r < R) {
-    A s = 0;
-    for (int yy = 0; yy < Y; ++yy) s += red[yy * RP + r];
-    M[in * R + r] = (T)s;
+  if (t < R) {
+    AT s = 0;
+    for (int q = t; q < stride; q += R) s += red[q];
+    reinterpret_cast<T*>(d->M[k][n])[in * R + t] = (T)s;
   }
 }
 
@@ -306,14 +390,14 @@ static cudaError_t trailing_impl(const LaunchCfg& c, const DevDesc* dd, const De
   const int total = hd.lt_prefix[hd.K];
   if (total == 0) return cudaSuccess;
   constexpr int WARPS = (sizeof(T) == 8 && RP > 16) ? 4 : 8;
-  constexpr size_t smem = sizeof(T) * WARPS * 32 * (33 + RP);
+  constexpr size_t smem = sizeof(T) * WARPS * (64 * TrailCfg<T>::XS + 32 * RP);
   auto kern = k_trailing_contract<ST, T, RP, WARPS>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   int grid = (total + WARPS - 1) / WARPS;
-  int per_sm = 0;
+  int per_sm = 0;  // trailing tiles are 64 rows
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem);
   if (per_sm < 1) per_sm = 1;
   grid = grid < c.num_sms * per_sm ? grid : c.num_sms * per_sm;
@@ -326,17 +410,17 @@ static cudaError_t lead_impl(const LaunchCfg& c, const DevDesc* dd, const DevDes
   const int total = hd.tt_prefix[hd.K];
   if (total == 0) return cudaSuccess;
   constexpr int CPT = (sizeof(T) == 8) ? (RP <= 16 ? 2 : 1) : (RP <= 20 ? 4 : (RP <= 32 ? 2 : 1));
-  constexpr size_t smem = sizeof(T) * (64 * RP + 64 * CPT * RP);
+  constexpr size_t smem = sizeof(T) * (64 * RP + 3 * 64 * CPT * RP);
   auto kern = k_lead_contract<ST, T, RP, CPT>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
   if (per_sm < 1) per_sm = 1;
   int grid = total < c.num_sms * per_sm ? total : c.num_sms * per_sm;
-  kern<<<grid, 128, smem, c.stream>>>(dd);
+  kern<<<grid, 256, smem, c.stream>>>(dd);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_reduce_splits<T><<<c.num_sms * 4, 256, 0, c.stream>>>(dd, d_red_prefix);
@@ -418,22 +502,14 @@ cudaError_t launch_lead_contract(const LaunchCfg& c, const DevDesc* dd, const De
   CNCPD_DISPATCH_ST_RP(lead_impl, c, dd, hd, d_red_prefix)
 }
 
-template <typename T, int RP>
-static cudaError_t level2_impl(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int n) {
+cudaError_t launch_level2(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int RP, int n) {
+  (void)RP;
   int64_t imax = 0;
   for (int k = 0; k < hd.K; ++k) imax = hd.dims[k][n] > imax ? hd.dims[k][n] : imax;
-  dim3 block(RP, 256 / RP);
   dim3 grid((unsigned)imax, hd.K);
-  k_level2<T, RP><<<grid, block, 0, c.stream>>>(dd, n);
+  if (fp64) k_level2<double><<<grid, 256, 0, c.stream>>>(dd, n);
+  else k_level2<float><<<grid, 256, 0, c.stream>>>(dd, n);
   return cudaGetLastError();
-}
-
-cudaError_t launch_level2(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int RP, int n) {
-#define L2CASE(V) \
-  case V: return fp64 ? level2_impl<double, V>(c, dd, hd, n) : level2_impl<float, V>(c, dd, hd, n);
-  switch (RP) { CNCPD_FOR_EACH_RP(L2CASE) }
-#undef L2CASE
-  return cudaErrorInvalidValue;
 }
 
 }  // namespace cncpd

@@ -10,10 +10,11 @@ namespace cncpd {
 // Largest eigenvalue of a symmetric PSD R x R matrix (R <= 64), called by a
 // whole CTA.  ||H||_2 of Eqs. eqLipsLd / eqLipsLu.  Normalised repeated
 // squaring A <- A^2 / tr(A^2) in FP32 converges to the projector on the
-// leading eigenvector (ratios of eigenvalues are raised to the power 2^s);
-// a column of the limit, refined by four FP64 power iterations, gives the
-// Rayleigh quotient v^T H v / v^T v in FP64.  Returns 0 for a zero matrix and
-// propagates NaN/Inf.
+// leading eigenvector (ratios of eigenvalues are raised to the power 2^s),
+// or on the leading eigenspace when the top eigenvalues agree to FP32
+// precision.  The FP64 value is then a Ritz value of H on one or two columns
+// of the limit (error quadratic in the FP32 angle, ~1e-14 relative).
+// Returns 0 for a zero matrix and propagates NaN/Inf.
 // ---------------------------------------------------------------------------
 // Shared-memory layout of lmax_psd for an R x R problem (dynamic smem):
 // Hs (R*R doubles), v, w (R doubles each), A, B (R*R floats each), red (32 floats).
@@ -74,13 +75,60 @@ __device__ double lmax_psd(const double* Hs, int R, LmaxScratch* s) {
     float m = 0.f;
     for (int i = 0; i < (nt + 31) / 32; ++i) m = fmaxf(m, s->red[i]);
     __syncthreads();
-    if (!(trb > 0.f) || m < 2e-7f) break;
+    if (!(trb > 0.f) || m < 4e-6f) break;
   }
-  // column of the limit with the largest diagonal entry
+  // v1: column of the limit with the largest diagonal entry.  If the limit
+  // has a second direction (leading eigenvalues closer than FP32 resolves),
+  // take the Ritz value of H on span{v1, v2} (2 x 2 closed form); otherwise
+  // refine v1 by FP64 power iterations and take its Rayleigh quotient.
   int jm = 0;
   float dm = -1.f;
   for (int i = 0; i < R; ++i)
     if (s->A[i * R + i] > dm) { dm = s->A[i * R + i]; jm = i; }
+  double n1 = 0.0;
+  for (int i = 0; i < R; ++i) n1 += (double)s->A[i * R + jm] * (double)s->A[i * R + jm];
+  n1 = sqrt(n1) + 1e-300;
+  // residual of every column after projecting out v1; the largest gives v2
+  int j2 = -1;
+  double r2best = 0.0;
+  for (int j = 0; j < R; ++j) {
+    double dot = 0.0, nn = 0.0;
+    for (int i = 0; i < R; ++i) {
+      const double a = s->A[i * R + j];
+      dot += a * (double)s->A[i * R + jm] / n1;
+      nn += a * a;
+    }
+    const double r2 = nn - dot * dot;
+    if (r2 > r2best) { r2best = r2; j2 = j; }
+  }
+  if (j2 >= 0 && r2best > 1e-8) {
+    // v1 = A e_jm / n1 ; v2 = (A e_j2 - (v1 . A e_j2) v1) normalised, in v / w
+    double dot = 0.0;
+    for (int i = 0; i < R; ++i) dot += (double)s->A[i * R + j2] * (double)s->A[i * R + jm] / n1;
+    __syncthreads();
+    for (int i = tid; i < R; i += nt) {
+      s->v[i] = (double)s->A[i * R + jm] / n1;
+      s->w[i] = (double)s->A[i * R + j2] - dot * (double)s->A[i * R + jm] / n1;
+    }
+    __syncthreads();
+    double nw = 0.0;
+    for (int i = 0; i < R; ++i) nw += s->w[i] * s->w[i];
+    nw = sqrt(nw);
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int i = 0; i < R; ++i) {
+      double hv = 0.0, hw = 0.0;
+      for (int l = 0; l < R; ++l) {
+        hv = fma(Hs[i * R + l], s->v[l], hv);
+        hw = fma(Hs[i * R + l], s->w[l] / nw, hw);
+      }
+      a = fma(s->v[i], hv, a);
+      b = fma(s->v[i], hw, b);
+      c = fma(s->w[i] / nw, hw, c);
+    }
+    __syncthreads();
+    const double h = 0.5 * (a - c);
+    return 0.5 * (a + c) + sqrt(h * h + b * b);
+  }
   for (int i = tid; i < R; i += nt) s->v[i] = (double)s->A[i * R + jm] + 1e-30;
   __syncthreads();
   for (int p = 0; p < 4; ++p) {
@@ -210,8 +258,9 @@ cudaError_t launch_lipschitz(const LaunchCfg& c, const DevDesc* dd, const DevDes
   const size_t sm = lmax_smem_bytes(hd.Rmax);
   cudaError_t e = fp64 ? allow_smem(k_lipschitz<double>, sm) : allow_smem(k_lipschitz<float>, sm);
   if (e != cudaSuccess) return e;
-  if (fp64) k_lipschitz<double><<<hd.K, 256, sm, c.stream>>>(dd, n, use_core, 1);
-  else k_lipschitz<float><<<hd.K, 256, sm, c.stream>>>(dd, n, use_core, 1);
+  const int nt = hd.Rmax <= 16 ? 128 : 256;
+  if (fp64) k_lipschitz<double><<<hd.K, nt, sm, c.stream>>>(dd, n, use_core, 1);
+  else k_lipschitz<float><<<hd.K, nt, sm, c.stream>>>(dd, n, use_core, 1);
   return cudaGetLastError();
 }
 
@@ -223,20 +272,36 @@ cudaError_t launch_lipschitz(const LaunchCfg& c, const DevDesc* dd, const DevDes
 //   individual columns: U1 <- P(U_hat - G_hat / L_u^(n,k))
 //   shared columns:     U1 <- P(U_hat_C - sum_k G_hat_C / sum_k L_u^(n,k)),
 //                       the same value written to every block
-//   U2 <- old U1.
-// Thread (c, y) owns column c of row blockIdx.x * ROWS + y, loops over the
-// blocks, and keeps the shared-column gradient sum in a register, so the
-// coupled sum needs no cross-CTA communication.  Rows are owned by exactly
-// one CTA, so the in-place write is race free.
+//   U2 <- old U1,
+// followed by the Gram G^(n,k) = U1^T U1 of the new factor (Table II
+// operation 1): per-CTA partial Grams, summed in CTA order by the last CTA
+// to arrive (deterministic, no waiting).
+// Thread (c, y) owns column c of row blockIdx.x * ROWS + y and walks the
+// blocks in chunks of KC, keeping the shared-column gradient sum in a
+// register, so the coupled sum needs no cross-CTA communication.  Rows are
+// owned by exactly one CTA, so the in-place write is race free.
 // ---------------------------------------------------------------------------
 template <typename T, int RP>
-__global__ void k_update(const DevDesc* __restrict__ d, int n, int use_w, double delta_w, int use_core) {
-  constexpr int ROWS = 256 / RP;
-  __shared__ T Hs[RP * RP];
-  __shared__ T uh[ROWS][RP];
+struct UpdCfg {
+  static constexpr int ROWS = 256 / RP;
+  static constexpr int KC_ = (int)((12288 * 4 / sizeof(T)) / (RP * RP));
+  static constexpr int KC = KC_ < 1 ? 1 : (KC_ > 8 ? 8 : KC_);
+};
+
+template <typename T, int RP>
+__global__ void __launch_bounds__(256) k_update(const DevDesc* __restrict__ d, int n, int use_w, double delta_w,
+                                                int use_core) {
+  constexpr int ROWS = UpdCfg<T, RP>::ROWS;
+  constexpr int KC = UpdCfg<T, RP>::KC;
+  __shared__ T Hs[KC][RP * RP];
+  __shared__ T uh[KC][ROWS][RP];
+  __shared__ int is_last;
   const int c = threadIdx.x;
   const int y = threadIdx.y;
-  const int64_t i = (int64_t)blockIdx.x * ROWS + y;
+  const int tid = c + y * RP;
+  constexpr int NT = RP * ROWS;
+  const int64_t row0 = (int64_t)blockIdx.x * ROWS;
+  const int64_t i = row0 + y;
   const int K = d->K;
   const int Ln = d->L[n];
   const int nonneg = d->nonneg[n];
@@ -246,52 +311,59 @@ __global__ void k_update(const DevDesc* __restrict__ d, int n, int use_w, double
   double LC = 0.0;
   for (int k = 0; k < K; ++k) LC += sc->Lcur_u[n][k];
   const T wC = (T)extrap_weight(w_hat, have_prev, sc->LCprev[n], LC, delta_w);
-  if (blockIdx.x == 0 && c == 0 && y == 0) {
+  if (blockIdx.x == 0 && tid == 0) {
     sc->LCcur[n] = LC;
     sc->have_cur = 1;
   }
 
   T sumC = T(0), uhC = T(0), u1C = T(0);
-  for (int k = 0; k < K; ++k) {
-    const int R = d->R[k];
-    const int64_t In = d->dims[k][n];
-    const double Lk = sc->Lcur_u[n][k];
-    const T wk = (T)extrap_weight(w_hat, have_prev, sc->Lprev_u[n][k], Lk, delta_w);
+  for (int k0 = 0; k0 < K; k0 += KC) {
+    const int kn = min(KC, K - k0);
     __syncthreads();
-    const T* Hk = reinterpret_cast<const T*>(d->H[k]);
-    for (int e = threadIdx.x + threadIdx.y * RP; e < RP * RP; e += RP * ROWS) {
-      const int a = e / RP, b = e % RP;
-      Hs[e] = (a < R && b < R) ? Hk[a * R + b] : T(0);
+    T u1[KC], u2[KC], mv[KC];
+    for (int kk = 0; kk < kn; ++kk) {
+      const int k = k0 + kk;
+      const int R = d->R[k];
+      const T* Hk = reinterpret_cast<const T*>(d->H[k]);
+      for (int e = tid; e < RP * RP; e += NT) {
+        const int a = e / RP, b = e % RP;
+        Hs[kk][e] = (a < R && b < R) ? Hk[a * R + b] : T(0);
+      }
+      const bool valid = (i < d->dims[k][n]) && (c < R);
+      u1[kk] = u2[kk] = mv[kk] = T(0);
+      if (valid) {
+        u1[kk] = reinterpret_cast<const T*>(d->U1[k][n])[i * R + c];
+        u2[kk] = reinterpret_cast<const T*>(d->U2[k][n])[i * R + c];
+        mv[kk] = reinterpret_cast<const T*>(d->M[k][n])[i * R + c];
+      }
+      const T wk = (T)extrap_weight(w_hat, have_prev, sc->Lprev_u[n][k], sc->Lcur_u[n][k], delta_w);
+      const T w = (c < Ln) ? wC : wk;
+      uh[kk][y][c] = valid ? u1[kk] + w * (u1[kk] - u2[kk]) : T(0);
     }
-    const bool valid = (i < In) && (c < R);
-    T* U1 = reinterpret_cast<T*>(d->U1[k][n]);
-    T* U2 = reinterpret_cast<T*>(d->U2[k][n]);
-    T u1 = T(0), u2 = T(0);
-    if (valid) {
-      u1 = U1[i * R + c];
-      u2 = U2[i * R + c];
-    }
-    const T w = (c < Ln) ? wC : wk;
-    const T uhat = u1 + w * (u1 - u2);
-    uh[y][c] = valid ? uhat : T(0);
     __syncthreads();
-    if (valid) {
-      const T lam = use_core ? (T)sc->lam1[k][c] : T(1);
-      T g = -reinterpret_cast<const T*>(d->M[k][n])[i * R + c] * lam;
+    for (int kk = 0; kk < kn; ++kk) {
+      const int k = k0 + kk;
+      const int R = d->R[k];
+      if ((i < d->dims[k][n]) && (c < R)) {
+        const double Lk = sc->Lcur_u[n][k];
+        const T lam = use_core ? (T)sc->lam1[k][c] : T(1);
+        const T uhat = uh[kk][y][c];
+        T g = -mv[kk] * lam;
 #pragma unroll
-      for (int a = 0; a < RP; ++a) g = fma(uh[y][a], Hs[a * RP + c], g);
-      if (c >= Ln) {
-        T nv = u1;
-        if (Lk > 0.0) {
-          nv = uhat - g / (T)Lk;
-          if (nonneg) nv = nv > T(0) ? nv : T(0);
+        for (int a = 0; a < RP; ++a) g = fma(uh[kk][y][a], Hs[kk][a * RP + c], g);
+        if (c >= Ln) {
+          T nv = u1[kk];
+          if (Lk > 0.0) {
+            nv = uhat - g / (T)Lk;
+            if (nonneg) nv = nv > T(0) ? nv : T(0);
+          }
+          reinterpret_cast<T*>(d->U2[k][n])[i * R + c] = u1[kk];
+          reinterpret_cast<T*>(d->U1[k][n])[i * R + c] = nv;
+        } else {
+          sumC += g;
+          uhC = uhat;
+          u1C = u1[kk];
         }
-        U2[i * R + c] = u1;
-        U1[i * R + c] = nv;
-      } else {
-        sumC += g;
-        uhC = uhat;
-        u1C = u1;
       }
     }
   }
@@ -307,17 +379,58 @@ __global__ void k_update(const DevDesc* __restrict__ d, int n, int use_w, double
       reinterpret_cast<T*>(d->U1[k][n])[i * R + c] = nv;
     }
   }
+
+  // ---- Gram of the new rows of this CTA (every block), then the last CTA sums
+  __syncthreads();
+  const int RR = d->Rmax * d->Rmax;
+  for (int k = 0; k < K; ++k) {
+    const int R = d->R[k];
+    const int64_t nrow = min((int64_t)ROWS, d->dims[k][n] - row0);
+    const T* U = reinterpret_cast<const T*>(d->U1[k][n]) + row0 * R;
+    double* gp = d->gpart + ((int64_t)blockIdx.x * K + k) * RR;
+    for (int p = tid; p < R * R; p += NT) {
+      const int a = p / R, b = p % R;
+      T acc = T(0);
+      for (int64_t r = 0; r < nrow; ++r) acc = fma(U[r * R + a], U[r * R + b], acc);
+      gp[p] = (double)acc;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) is_last = (atomicAdd(&sc->done_counter[0], 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (is_last) {
+    __threadfence();
+    for (int k = 0; k < K; ++k) {
+      const int R = d->R[k];
+      double* G = d->G[k][n];
+      for (int p = tid; p < R * R; p += NT) {
+        double s = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(d->gpart + ((int64_t)b * K + k) * RR + p);
+        G[p] = s;
+      }
+    }
+    if (tid == 0) sc->done_counter[0] = 0;
+  }
 }
 
 template <typename T, int RP>
 static cudaError_t update_impl(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int n, int use_w,
                                double delta_w, int use_core) {
-  constexpr int ROWS = 256 / RP;
+  constexpr int ROWS = UpdCfg<T, RP>::ROWS;
   int64_t imax = 0;
   for (int k = 0; k < hd.K; ++k) imax = hd.dims[k][n] > imax ? hd.dims[k][n] : imax;
   const unsigned grid = (unsigned)((imax + ROWS - 1) / ROWS);
   k_update<T, RP><<<grid, dim3(RP, ROWS), 0, c.stream>>>(dd, n, use_w, delta_w, use_core);
   return cudaGetLastError();
+}
+
+// Number of CTAs of the update of mode n (sizes the partial-Gram buffer).
+int update_grid(const DevDesc& hd, int RP, int n) {
+  const int ROWS = 256 / RP;
+  int64_t imax = 0;
+  for (int k = 0; k < hd.K; ++k) imax = hd.dims[k][n] > imax ? hd.dims[k][n] : imax;
+  return (int)((imax + ROWS - 1) / ROWS);
 }
 
 cudaError_t launch_update(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int RP, int n,
@@ -342,69 +455,80 @@ cudaError_t launch_update(const LaunchCfg& c, const DevDesc* dd, const DevDesc& 
 // next core update.  RelErr per Section III-C.  One CTA, threads (r, y).
 // ---------------------------------------------------------------------------
 template <typename T, int RP>
-__global__ void k_objective(const DevDesc* __restrict__ d, int commit) {
+__global__ void __launch_bounds__(256) k_objective(const DevDesc* __restrict__ d, int commit) {
   const int r = threadIdx.x, y = threadIdx.y, Y = blockDim.y;
-  const int K = d->K, N = d->N, n = N - 1;
+  const int tid = r + y * RP;
+  const int NT = RP * Y;
+  const int N = d->N, n = N - 1;
+  const int k = blockIdx.x;
   DevScalars* sc = d->sc;
   __shared__ double red[256];
   __shared__ double cr[RP];
-  double Fsum = 0.0, relsum = 0.0;
-  for (int k = 0; k < K; ++k) {
-    const int R = d->R[k];
-    const int64_t I = d->dims[k][n];
-    const T* M = reinterpret_cast<const T*>(d->M[k][n]);
-    const T* U = reinterpret_cast<const T*>(d->U1[k][n]);
-    double acc = 0.0;
-    if (r < R)
-      for (int64_t i = y; i < I; i += Y) acc = fma((double)M[i * R + r], (double)U[i * R + r], acc);
-    red[y * RP + r] = acc;
-    __syncthreads();
-    if (y == 0) {
-      double s = 0.0;
-      for (int yy = 0; yy < Y; ++yy) s += red[yy * RP + r];
-      cr[r] = s;
-      if (r < R && commit) sc->cterm[k][r] = s;
-    }
-    __syncthreads();
-    if (r == 0 && y == 0) {
-      double ip = 0.0, xx = 0.0;
-      for (int a = 0; a < R; ++a) {
-        const double la = sc->lam1[k][a];
-        ip += la * cr[a];
-        for (int b = 0; b < R; ++b) {
-          double g = 1.0;
-          for (int m = 0; m < N; ++m) g *= d->G[k][m][a * R + b];
-          xx += la * sc->lam1[k][b] * g;
-        }
-      }
-      const double x2 = commit ? sc->xnorm2[k] : sc->xnorm2_orig[k];
-      const double Fk = 0.5 * (x2 - 2.0 * ip + xx);
-      const double rel = x2 > 0.0 ? sqrt(fmax(2.0 * Fk, 0.0) / x2) : 0.0;
-      if (commit) {
-        sc->Fk[k] = Fk;
-        sc->relk[k] = rel;
-        sc->ip[k] = ip;
-        sc->xhat2[k] = xx;
-      } else {
-        sc->out_relk[k] = rel;
-      }
-      Fsum += Fk;
-      relsum += rel;
-    }
-    __syncthreads();
+  __shared__ int is_last;
+  const int R = d->R[k];
+  const int64_t I = d->dims[k][n];
+  const T* M = reinterpret_cast<const T*>(d->M[k][n]);
+  const T* U = reinterpret_cast<const T*>(d->U1[k][n]);
+  double acc = 0.0;
+  if (r < R)
+    for (int64_t i = y; i < I; i += Y) acc = fma((double)M[i * R + r], (double)U[i * R + r], acc);
+  red[tid] = acc;
+  __syncthreads();
+  if (y == 0) {
+    double s = 0.0;
+    for (int yy = 0; yy < Y; ++yy) s += red[yy * RP + r];
+    cr[r] = s;
+    if (r < R && commit) sc->cterm[k][r] = s;
   }
-  if (r == 0 && y == 0 && commit) {
-    sc->F = Fsum;
-    sc->relerr = relsum / K;
-    if (!isfinite(Fsum)) sc->nonfinite = 1;
+  __syncthreads();
+  // ||X_hat||^2 = lambda^T (*_m G^(m)) lambda and <X, X_hat> = lambda^T c
+  double xx = 0.0;
+  for (int p = tid; p < R * R; p += NT) {
+    const int a = p / R, b = p % R;
+    double g = sc->lam1[k][a] * sc->lam1[k][b];
+    for (int m = 0; m < N; ++m) g *= d->G[k][m][p];
+    xx += g;
+  }
+  if (tid < R) xx -= 2.0 * sc->lam1[k][tid] * cr[tid];
+  red[tid] = xx;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int q = 0; q < NT; ++q) t += red[q];
+    const double x2 = commit ? sc->xnorm2[k] : sc->xnorm2_orig[k];
+    const double Fk = 0.5 * (x2 + t);
+    const double rel = x2 > 0.0 ? sqrt(fmax(2.0 * Fk, 0.0) / x2) : 0.0;
+    if (commit) {
+      sc->Fk[k] = Fk;
+      sc->relk[k] = rel;
+    } else {
+      sc->out_relk[k] = rel;
+    }
+  }
+  if (!commit) return;
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) is_last = (atomicAdd(&sc->done_counter[1], 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (is_last && tid == 0) {
+    __threadfence();
+    double F = 0.0, rel = 0.0;
+    for (int q = 0; q < (int)gridDim.x; ++q) {
+      F += __ldcg(&sc->Fk[q]);
+      rel += __ldcg(&sc->relk[q]);
+    }
+    sc->F = F;
+    sc->relerr = rel / gridDim.x;
+    if (!isfinite(F)) sc->nonfinite = 1;
+    sc->done_counter[1] = 0;
   }
 }
 
 cudaError_t launch_objective(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int RP, int commit) {
-#define OCASE(V)                                                                                \
-  case V:                                                                                       \
-    if (fp64) k_objective<double, V><<<1, dim3(V, 256 / V), 0, c.stream>>>(dd, commit);         \
-    else k_objective<float, V><<<1, dim3(V, 256 / V), 0, c.stream>>>(dd, commit);               \
+#define OCASE(V)                                                                                  \
+  case V:                                                                                         \
+    if (fp64) k_objective<double, V><<<hd.K, dim3(V, 256 / V), 0, c.stream>>>(dd, commit);        \
+    else k_objective<float, V><<<hd.K, dim3(V, 256 / V), 0, c.stream>>>(dd, commit);              \
     return cudaGetLastError();
   switch (RP) { CNCPD_FOR_EACH_RP(OCASE) }
 #undef OCASE
