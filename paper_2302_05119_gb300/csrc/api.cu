@@ -620,6 +620,11 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
     }
     d.lead_rows[k] = lr;
     d.trail_cols[k] = tc;
+    if (lr * R[k] >= (1LL << 31) || tc * R[k] >= (1LL << 31)) {
+      std::string msg = "block too large for the two-level tree (level-1 partial above 2^31 entries)";
+      cncpd_destroy(c);
+      return set_err(CNCPD_EINVAL, "%s", msg.c_str());
+    }
   }
   for (int n = 0; n < N; ++n) {
     d.L[n] = c->L[n];

@@ -16,6 +16,16 @@
 
 namespace cncpd {
 
+// 32-bit mixed-radix decode over modes [m0, m1) (each level-1 index range is
+// below 2^31, checked at creation).
+__device__ __forceinline__ void decode32(const DevDesc* d, int k, int m0, int m1, int flat, int* idx) {
+  for (int m = m1 - 1; m >= m0; --m) {
+    const int I = (int)d->dims[k][m];
+    idx[m] = flat % I;
+    flat /= I;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Trailing contraction: one warp owns 64 consecutive rows (lane l: rows l and
 // l + 32) and walks the columns in chunks of 32.  A 64 x 32 chunk of X is
@@ -62,7 +72,7 @@ k_trailing_contract(const DevDesc* __restrict__ d) {
         for (int r = 0; r < RP; ++r) w[r] = (r < R && j < J) ? T(1) : T(0);
         if (j < J) {
           int idx[CNCPD_NMAX];
-          decode(d, k, h, N, j, idx);
+          decode32(d, k, h, N, (int)j, idx);
           for (int m = h; m < N; ++m) {
             const T* U = reinterpret_cast<const T*>(d->U1[k][m]) + (int64_t)idx[m] * R;
 #pragma unroll
@@ -237,7 +247,7 @@ k_lead_contract(const DevDesc* __restrict__ d) {
         T w = T(0);
         if (row < re && r < R) {
           int idx[CNCPD_NMAX];
-          decode(d, k, 0, h, row, idx);
+          decode32(d, k, 0, h, (int)row, idx);
           w = T(1);
           for (int m = 0; m < h; ++m) w *= reinterpret_cast<const T*>(d->U1[k][m])[(int64_t)idx[m] * R + r];
         }
@@ -327,12 +337,14 @@ __global__ void k_reduce_splits(const DevDesc* __restrict__ d, const int64_t* __
 // (a, b, r) range, so consecutive threads read consecutive P entries.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ T kr_row(const DevDesc* d, int k, int m0, int m1, int64_t flat, int r, int R) {
-  // prod_{m in [m0, m1)} U^(m)[i_m(flat), r]  (C-order mixed radix)
+__device__ __forceinline__ T kr_row(const DevDesc* d, int k, int m0, int m1, int flat, int r, int R) {
+  // prod_{m in [m0, m1)} U^(m)[i_m(flat), r]  (C-order mixed radix; 32-bit:
+  // the level-1 partials are limited to 2^31 entries)
+  if (m1 - m0 == 1) return reinterpret_cast<const T*>(d->U1[k][m0])[flat * R + r];
   T w = T(1);
   for (int m = m1 - 1; m >= m0; --m) {
-    const int64_t I = d->dims[k][m];
-    const int64_t im = flat % I;
+    const int I = (int)d->dims[k][m];
+    const int im = flat % I;
     flat /= I;
     w *= reinterpret_cast<const T*>(d->U1[k][m])[im * R + r];
   }
@@ -349,28 +361,29 @@ __global__ void __launch_bounds__(256) k_level2(const DevDesc* __restrict__ d, i
   if (in >= In) return;
   const int R = d->R[k];
   const T* P = reinterpret_cast<const T*>((n < h) ? d->Pl[k] : d->Pt[k]);
-  int64_t A = 1, B = 1;
-  for (int m = m0; m < n; ++m) A *= d->dims[k][m];
-  for (int m = n + 1; m < m1; ++m) B *= d->dims[k][m];
-  const int64_t BR = B * R;
+  int A = 1, B = 1;
+  for (int m = m0; m < n; ++m) A *= (int)d->dims[k][m];
+  for (int m = n + 1; m < m1; ++m) B *= (int)d->dims[k][m];
+  const int BR = B * R;
   const int stride = (blockDim.x / R) * R;
   const int t = threadIdx.x;
   typedef typename Acc<T>::type AT;
   AT acc = 0;
   const int r = t % R;
   if (t < stride) {
-    const int64_t total = A * BR;
-    const int64_t sq = stride / BR, sr = stride % BR;
-    int64_t a = t / BR, e = t % BR;
-    for (int64_t f = t; f < total; f += stride) {
-      const int64_t b = e / R;
-      T p = P[(a * In + in) * BR + e];
-      if (A > 1) p *= kr_row<T>(d, k, m0, n, a, r, R);
-      if (B > 1) p *= kr_row<T>(d, k, n + 1, m1, b, r, R);
+    const int total = A * BR;
+    const int sq = stride / BR, sr = stride % BR;
+    int a = t / BR, e = t % BR, b = e / R;
+    const int bq = sr / R;  // stride and BR are multiples of R
+    for (int f = t; f < total; f += stride) {
+      T p = P[((int64_t)a * In + in) * BR + e];
+      if (n > m0) p *= kr_row<T>(d, k, m0, n, a, r, R);
+      if (n + 1 < m1) p *= kr_row<T>(d, k, n + 1, m1, b, r, R);
       acc += (AT)p;
       a += sq;
       e += sr;
-      if (e >= BR) { e -= BR; ++a; }
+      b += bq;
+      if (e >= BR) { e -= BR; b -= B; ++a; }
     }
   }
   __shared__ AT red[256];

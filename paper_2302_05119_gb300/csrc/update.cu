@@ -2,6 +2,8 @@
 // Lipschitz constants, the fused extrapolate / gradient / step / projection
 // update with the coupled common-column sum, the objective, the core update,
 // and the bookkeeping of iterations and re-updates.
+#include <algorithm>
+
 #include "cncpd_internal.cuh"
 
 namespace cncpd {
@@ -10,10 +12,8 @@ namespace cncpd {
 // Largest eigenvalue of a symmetric PSD R x R matrix (R <= 64), called by a
 // whole CTA.  ||H||_2 of Eqs. eqLipsLd / eqLipsLu.  Normalised repeated
 // squaring A <- A^2 / tr(A^2) in FP32 converges to the projector on the
-// leading eigenvector (ratios of eigenvalues are raised to the power 2^s),
-// or on the leading eigenspace when the top eigenvalues agree to FP32
-// precision.  The FP64 value is then a Ritz value of H on one or two columns
-// of the limit (error quadratic in the FP32 angle, ~1e-14 relative).
+// leading eigenvector (ratios of eigenvalues are raised to the power 2^s).
+// The FP64 value is the Rayleigh quotient of H at a column of the limit.
 // Returns 0 for a zero matrix and propagates NaN/Inf.
 // ---------------------------------------------------------------------------
 // Shared-memory layout of lmax_psd for an R x R problem (dynamic smem):
@@ -77,84 +77,40 @@ __device__ double lmax_psd(const double* Hs, int R, LmaxScratch* s) {
     __syncthreads();
     if (!(trb > 0.f) || m < 4e-6f) break;
   }
-  // v1: column of the limit with the largest diagonal entry.  If the limit
-  // has a second direction (leading eigenvalues closer than FP32 resolves),
-  // take the Ritz value of H on span{v1, v2} (2 x 2 closed form); otherwise
-  // refine v1 by FP64 power iterations and take its Rayleigh quotient.
+  // v: column of the limit with the largest diagonal entry (FP32 accuracy in
+  // every non-leading direction).  One FP64 product y = H v and the Rayleigh
+  // quotient v^T y / v^T v, reduced by warp 0, give L with error quadratic in
+  // that accuracy.  (When the two largest eigenvalues agree to within FP32
+  // resolution the squaring still ends in a rank-one limit, and the error is
+  // bounded by their relative gap.)
   int jm = 0;
   float dm = -1.f;
   for (int i = 0; i < R; ++i)
     if (s->A[i * R + i] > dm) { dm = s->A[i * R + i]; jm = i; }
-  double n1 = 0.0;
-  for (int i = 0; i < R; ++i) n1 += (double)s->A[i * R + jm] * (double)s->A[i * R + jm];
-  n1 = sqrt(n1) + 1e-300;
-  // residual of every column after projecting out v1; the largest gives v2
-  int j2 = -1;
-  double r2best = 0.0;
-  for (int j = 0; j < R; ++j) {
-    double dot = 0.0, nn = 0.0;
-    for (int i = 0; i < R; ++i) {
-      const double a = s->A[i * R + j];
-      dot += a * (double)s->A[i * R + jm] / n1;
-      nn += a * a;
-    }
-    const double r2 = nn - dot * dot;
-    if (r2 > r2best) { r2best = r2; j2 = j; }
-  }
-  if (j2 >= 0 && r2best > 1e-8) {
-    // v1 = A e_jm / n1 ; v2 = (A e_j2 - (v1 . A e_j2) v1) normalised, in v / w
-    double dot = 0.0;
-    for (int i = 0; i < R; ++i) dot += (double)s->A[i * R + j2] * (double)s->A[i * R + jm] / n1;
-    __syncthreads();
-    for (int i = tid; i < R; i += nt) {
-      s->v[i] = (double)s->A[i * R + jm] / n1;
-      s->w[i] = (double)s->A[i * R + j2] - dot * (double)s->A[i * R + jm] / n1;
-    }
-    __syncthreads();
-    double nw = 0.0;
-    for (int i = 0; i < R; ++i) nw += s->w[i] * s->w[i];
-    nw = sqrt(nw);
-    double a = 0.0, b = 0.0, c = 0.0;
-    for (int i = 0; i < R; ++i) {
-      double hv = 0.0, hw = 0.0;
-      for (int l = 0; l < R; ++l) {
-        hv = fma(Hs[i * R + l], s->v[l], hv);
-        hw = fma(Hs[i * R + l], s->w[l] / nw, hw);
-      }
-      a = fma(s->v[i], hv, a);
-      b = fma(s->v[i], hw, b);
-      c = fma(s->w[i] / nw, hw, c);
-    }
-    __syncthreads();
-    const double h = 0.5 * (a - c);
-    return 0.5 * (a + c) + sqrt(h * h + b * b);
-  }
-  for (int i = tid; i < R; i += nt) s->v[i] = (double)s->A[i * R + jm] + 1e-30;
-  __syncthreads();
-  for (int p = 0; p < 4; ++p) {
-    for (int i = tid; i < R; i += nt) {
-      double a = 0.0;
-      for (int l = 0; l < R; ++l) a = fma(Hs[i * R + l], s->v[l], a);
-      s->w[i] = a;
-    }
-    __syncthreads();
-    double nrm = 0.0;
-    for (int i = 0; i < R; ++i) nrm += s->w[i] * s->w[i];
-    nrm = sqrt(nrm);
-    __syncthreads();
-    if (nrm > 0.0)
-      for (int i = tid; i < R; i += nt) s->v[i] = s->w[i] / nrm;
-    __syncthreads();
-  }
-  double num = 0.0, den = 0.0;
-  for (int i = 0; i < R; ++i) {
+  for (int i = tid; i < R; i += nt) {
+    const double vi = (double)s->A[i * R + jm];
     double a = 0.0;
-    for (int l = 0; l < R; ++l) a = fma(Hs[i * R + l], s->v[l], a);
-    num = fma(s->v[i], a, num);
-    den = fma(s->v[i], s->v[i], den);
+    for (int l = 0; l < R; ++l) a = fma(Hs[i * R + l], (double)s->A[l * R + jm], a);
+    s->v[i] = vi * a;   // v_i (H v)_i
+    s->w[i] = vi * vi;  // v_i^2
   }
   __syncthreads();
-  return den > 0.0 ? num / den : 0.0;
+  double num = 0.0, den = 0.0;
+  if (tid < 32) {
+    for (int i = tid; i < R; i += 32) {
+      num += s->v[i];
+      den += s->w[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      num += __shfl_xor_sync(0xffffffffu, num, o);
+      den += __shfl_xor_sync(0xffffffffu, den, o);
+    }
+    if (tid == 0) s->v[0] = den > 0.0 ? num / den : 0.0;
+  }
+  __syncthreads();
+  const double L = s->v[0];
+  __syncthreads();
+  return L;
 }
 
 template <typename KernelT>
@@ -173,11 +129,14 @@ __device__ __forceinline__ double extrap_weight(double w_hat, int have_prev, dou
 
 // ---------------------------------------------------------------------------
 // Grams G = U^T U (Table II operation 1) of modes [n_begin, n_end) of every
-// block; which = 0: the factors U1, which = 1: the LRA factors U~.  FP32
-// partial sums over 64 rows are folded into FP64.
+// block; which = 0: the factors U1, which = 1: the LRA factors U~.  The sum
+// is taken exactly as the fused update forms it -- an FMA chain in the
+// factor type over each tile of `tile` rows, tiles added in FP64 in order --
+// so the two paths give bit-identical Grams.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_gram(const DevDesc* __restrict__ d, int n_begin, int n_end, int which) {
+__global__ void __launch_bounds__(256) k_gram(const DevDesc* __restrict__ d, int n_begin, int n_end, int which,
+                                              int tile) {
   const int nm = n_end - n_begin;
   const int k = blockIdx.x / nm;
   const int n = n_begin + blockIdx.x % nm;
@@ -185,33 +144,16 @@ __global__ void __launch_bounds__(256) k_gram(const DevDesc* __restrict__ d, int
   const int R = which ? d->Rt[k] : d->R[k];
   double* G = which ? d->Gt[k][n] : d->G[k][n];
   const int64_t I = d->dims[k][n];
-  const int P = R * R;
-  __shared__ double red[256];
-  const int tid = threadIdx.x;
-  for (int p0 = 0; p0 < P; p0 += 256) {
-    const int np = min(256, P - p0);
-    const int Y = max(1, 256 / np);
-    const int p = p0 + tid % np;
-    const int y = tid / np;
-    double acc = 0.0;
-    if (y < Y && tid < np * Y) {
-      const int a = p / R, b = p % R;
-      T part = T(0);
-      int cnt = 0;
-      for (int64_t i = y; i < I; i += Y) {
-        part = fma(U[i * R + a], U[i * R + b], part);
-        if (++cnt == 64) { acc += (double)part; part = T(0); cnt = 0; }
-      }
-      acc += (double)part;
+  for (int p = threadIdx.x; p < R * R; p += blockDim.x) {
+    const int a = p / R, b = p % R;
+    double s = 0.0;
+    for (int64_t t0 = 0; t0 < I; t0 += tile) {
+      const int64_t t1 = min(I, t0 + tile);
+      T acc = T(0);
+      for (int64_t i = t0; i < t1; ++i) acc = fma(U[i * R + a], U[i * R + b], acc);
+      s += (double)acc;
     }
-    red[tid] = acc;
-    __syncthreads();
-    if (tid < np) {
-      double s = 0.0;
-      for (int yy = 0; yy < Y; ++yy) s += red[yy * np + tid];
-      G[p0 + tid] = s;
-    }
-    __syncthreads();
+    G[p] = s;
   }
 }
 
@@ -219,8 +161,11 @@ cudaError_t launch_gram(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd
                         int which) {
   if (n_end <= n_begin) return cudaSuccess;
   const int grid = hd.K * (n_end - n_begin);
-  if (fp64) k_gram<double><<<grid, 256, 0, c.stream>>>(dd, n_begin, n_end, which);
-  else k_gram<float><<<grid, 256, 0, c.stream>>>(dd, n_begin, n_end, which);
+  int rmax = 1;
+  for (int k = 0; k < hd.K; ++k) rmax = std::max(rmax, which ? hd.Rt[k] : hd.R[k]);
+  const int tile = std::max(1, 128 / rank_bucket(hd.Rmax));  // rows per CTA of the fused update
+  if (fp64) k_gram<double><<<grid, 256, 0, c.stream>>>(dd, n_begin, n_end, which, tile);
+  else k_gram<float><<<grid, 256, 0, c.stream>>>(dd, n_begin, n_end, which, tile);
   return cudaGetLastError();
 }
 
@@ -283,19 +228,21 @@ cudaError_t launch_lipschitz(const LaunchCfg& c, const DevDesc* dd, const DevDes
 // ---------------------------------------------------------------------------
 template <typename T, int RP>
 struct UpdCfg {
-  static constexpr int ROWS = 256 / RP;
-  static constexpr int KC_ = (int)((12288 * 4 / sizeof(T)) / (RP * RP));
+  static constexpr int ROWS = (128 / RP) > 0 ? 128 / RP : 1;
+  static constexpr int KC_ = (int)((10240 * 4 / sizeof(T)) / (RP * RP));
   static constexpr int KC = KC_ < 1 ? 1 : (KC_ > 8 ? 8 : KC_);
 };
 
 template <typename T, int RP>
-__global__ void __launch_bounds__(256) k_update(const DevDesc* __restrict__ d, int n, int use_w, double delta_w,
+__global__ void __launch_bounds__(128) k_update(const DevDesc* __restrict__ d, int n, int use_w, double delta_w,
                                                 int use_core) {
   constexpr int ROWS = UpdCfg<T, RP>::ROWS;
   constexpr int KC = UpdCfg<T, RP>::KC;
   __shared__ T Hs[KC][RP * RP];
   __shared__ T uh[KC][ROWS][RP];
   __shared__ int is_last;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T (*nu)[ROWS][RP] = reinterpret_cast<T (*)[ROWS][RP]>(smem_raw);  // new rows of every block
   const int c = threadIdx.x;
   const int y = threadIdx.y;
   const int tid = c + y * RP;
@@ -359,6 +306,7 @@ __global__ void __launch_bounds__(256) k_update(const DevDesc* __restrict__ d, i
           }
           reinterpret_cast<T*>(d->U2[k][n])[i * R + c] = u1[kk];
           reinterpret_cast<T*>(d->U1[k][n])[i * R + c] = nv;
+          nu[k][y][c] = nv;
         } else {
           sumC += g;
           uhC = uhat;
@@ -377,6 +325,7 @@ __global__ void __launch_bounds__(256) k_update(const DevDesc* __restrict__ d, i
       const int R = d->R[k];
       reinterpret_cast<T*>(d->U2[k][n])[i * R + c] = u1C;
       reinterpret_cast<T*>(d->U1[k][n])[i * R + c] = nv;
+      nu[k][y][c] = nv;
     }
   }
 
@@ -385,13 +334,12 @@ __global__ void __launch_bounds__(256) k_update(const DevDesc* __restrict__ d, i
   const int RR = d->Rmax * d->Rmax;
   for (int k = 0; k < K; ++k) {
     const int R = d->R[k];
-    const int64_t nrow = min((int64_t)ROWS, d->dims[k][n] - row0);
-    const T* U = reinterpret_cast<const T*>(d->U1[k][n]) + row0 * R;
+    const int nrow = (int)min((int64_t)ROWS, d->dims[k][n] - row0);
     double* gp = d->gpart + ((int64_t)blockIdx.x * K + k) * RR;
     for (int p = tid; p < R * R; p += NT) {
       const int a = p / R, b = p % R;
       T acc = T(0);
-      for (int64_t r = 0; r < nrow; ++r) acc = fma(U[r * R + a], U[r * R + b], acc);
+      for (int r = 0; r < nrow; ++r) acc = fma(nu[k][r][a], nu[k][r][b], acc);
       gp[p] = (double)acc;
     }
   }
@@ -421,13 +369,16 @@ static cudaError_t update_impl(const LaunchCfg& c, const DevDesc* dd, const DevD
   int64_t imax = 0;
   for (int k = 0; k < hd.K; ++k) imax = hd.dims[k][n] > imax ? hd.dims[k][n] : imax;
   const unsigned grid = (unsigned)((imax + ROWS - 1) / ROWS);
-  k_update<T, RP><<<grid, dim3(RP, ROWS), 0, c.stream>>>(dd, n, use_w, delta_w, use_core);
+  const size_t sm = sizeof(T) * (size_t)hd.K * ROWS * RP;
+  cudaError_t e = allow_smem(k_update<T, RP>, sm + sizeof(T) * (UpdCfg<T, RP>::KC * RP * (RP + ROWS)) + 64);
+  if (e != cudaSuccess) return e;
+  k_update<T, RP><<<grid, dim3(RP, ROWS), sm, c.stream>>>(dd, n, use_w, delta_w, use_core);
   return cudaGetLastError();
 }
 
 // Number of CTAs of the update of mode n (sizes the partial-Gram buffer).
 int update_grid(const DevDesc& hd, int RP, int n) {
-  const int ROWS = 256 / RP;
+  const int ROWS = (128 / RP) > 0 ? 128 / RP : 1;
   int64_t imax = 0;
   for (int k = 0; k < hd.K; ++k) imax = hd.dims[k][n] > imax ? hd.dims[k][n] : imax;
   return (int)((imax + ROWS - 1) / ROWS);
