@@ -200,6 +200,32 @@ int cncpd_save_state(cncpd_t h, void **blob, size_t *nbytes);
 int cncpd_load_state(cncpd_t h, const void *blob, size_t nbytes);
 void cncpd_free_blob(void *blob);
 
+/*
+ * Allocation-free MTTKRP for callers that must not let this library call
+ * cudaMalloc (their device memory is owned by another allocator or a fixed
+ * arena, they run under a strict memory budget, or an allocation's implicit
+ * device synchronisation is unacceptable to them).  The paper has no
+ * counterpart: it is a service of this library.
+ *
+ * Computes M[j, r] = sum_{i0, i1} X[i0, i1, j] U0[i0, r] U1[i1, r], the
+ * last-mode MTTKRP X_(3) (U1 (.) U0) of one third-order FP32 tensor, on
+ * `stream` (NULL: legacy default stream), without synchronising it.
+ *  X   device, C order I0 x I1 x I2;  U0: device, I0 x R;  U1: device, I1 x R
+ *  M   device output, I2 x R (row-major);  1 <= R <= 64
+ * Scratch: a fixed 8 MiB device array inside the library (2^21 floats),
+ * held on every GPU that loads the library until the process exits.
+ * I2 * R above 2^21 is rejected with CNCPD_EINVAL.  Nothing in the scratch
+ * needs to start at zero.  All calls share that array, so calls that overlap
+ * on the GPU (different streams, or different host threads on one device)
+ * race and give wrong results; serialise them.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress), so make
+ * it before any stream capture.  Calls no allocating routine.
+ */
+int cncpd_mttkrp_last_mode_noalloc(const float *X, int64_t I0, int64_t I1,
+                                   int64_t I2, const float *U0,
+                                   const float *U1, int R, float *M,
+                                   void *stream);
+
 /* Release every device allocation of the handle (NULL is ignored). */
 void cncpd_destroy(cncpd_t h);
 

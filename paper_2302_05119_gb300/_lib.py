@@ -68,6 +68,8 @@ SIGNATURES = {
     "cncpd_save_state": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_size_t)]),
     "cncpd_load_state": (_I, [_P, _P, ctypes.c_size_t]),
     "cncpd_free_blob": (None, [_P]),
+    "cncpd_mttkrp_last_mode_noalloc": (_I, [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _P, _P,
+                                            _I, _P, _P]),
     "cncpd_destroy": (None, [_P]),
     "cncpd_last_error": (ctypes.c_char_p, []),
 }

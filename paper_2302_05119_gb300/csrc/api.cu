@@ -61,6 +61,8 @@ struct HostScalars {  // mirror of the head of DevScalars read back each iterati
 
 }  // namespace
 
+int cncpd::set_error(int code, const char* msg) { return set_err(code, "%s", msg); }
+
 struct cncpd_ctx {
   int device = 0, num_sms = 0;
   int K = 0, N = 0, h = 0;

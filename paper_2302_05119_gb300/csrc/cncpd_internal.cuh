@@ -141,6 +141,9 @@ inline int rank_bucket(int R) {
 // Implemented in mttkrp.cu / update.cu / lra.cu.  `fp64` selects the FP64
 // factor path (storage ST_F64); otherwise factors are FP32.
 
+// Record the message returned by cncpd_last_error() on this thread; returns code.
+int set_error(int code, const char* msg);
+
 struct LaunchCfg {
   cudaStream_t stream;
   int num_sms;
