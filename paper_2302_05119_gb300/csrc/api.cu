@@ -16,6 +16,8 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "../../include/cncpd.h"
 #include "cncpd_internal.cuh"
 
@@ -55,7 +57,7 @@ double now_s() {
 
 struct HostScalars {  // mirror of the head of DevScalars read back each iteration
   double t, w_hat;
-  int have_prev, have_cur, nonfinite, pad0;
+  int have_prev, have_cur, nonfinite, timeout;
   double F, relerr;
 };
 
@@ -115,6 +117,39 @@ struct cncpd_ctx {
 
 namespace {
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 2-D FP32 tensor map over a rows x cols matrix with row pitch `pitch`
+// elements, box (box_cols x box_rows), out-of-range elements read as zero.
+bool encode_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64_t pitch, int box_cols, int box_rows,
+                CUtensorMapSwizzle swz) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(pitch * 4)};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 int dalloc(cncpd_ctx* c, void** p, size_t bytes) {
   if (bytes == 0) bytes = 16;
   cudaError_t e = cudaMalloc(p, bytes);
@@ -129,6 +164,7 @@ int dalloc(cncpd_ctx* c, void** p, size_t bytes) {
 // Split-K plan of the lead-mode contraction for rank bucket RP.
 void plan_lead_splits(cncpd_ctx* c, DevDesc& d, int RP, int fp64, size_t* partial_elems) {
   const int cpt = lead_cpt(fp64, RP);
+  const int tile_cols = d.use_tma ? 128 : 64 * cpt;
   int64_t tot_rows = 0;
   for (int k = 0; k < d.K; ++k) tot_rows += d.lead_rows[k];
   // aim for ~2 CTAs (of 256 threads) per SM in total, at least 64 rows per split
@@ -137,7 +173,7 @@ void plan_lead_splits(cncpd_ctx* c, DevDesc& d, int RP, int fp64, size_t* partia
   size_t off = 0;
   for (int k = 0; k < d.K; ++k) {
     const int64_t J = d.trail_cols[k];
-    const int ctiles = (int)((J + 64 * cpt - 1) / (64 * cpt));
+    const int ctiles = (int)((J + tile_cols - 1) / tile_cols);
     const int64_t rows = d.lead_rows[k];
     int64_t want = std::max<int64_t>(1, (target_units * rows) / std::max<int64_t>(1, tot_rows) / ctiles);
     int64_t split_rows = (rows + want - 1) / want;
@@ -152,12 +188,14 @@ void plan_lead_splits(cncpd_ctx* c, DevDesc& d, int RP, int fp64, size_t* partia
     d.tt_prefix[k + 1] = d.tt_prefix[k] + ctiles * ns;
   }
   d.tt_cpt = cpt;
+  d.tt_cols = tile_cols;
   *partial_elems = off;
 }
 
 void plan_trailing_tiles(DevDesc& d) {
+  d.lt_rows = d.use_tma ? 256 : 64;
   d.lt_prefix[0] = 0;
-  for (int k = 0; k < d.K; ++k) d.lt_prefix[k + 1] = d.lt_prefix[k] + (int)((d.lead_rows[k] + 63) / 64);
+  for (int k = 0; k < d.K; ++k) d.lt_prefix[k + 1] = d.lt_prefix[k] + (int)((d.lead_rows[k] + d.lt_rows - 1) / d.lt_rows);
 }
 
 int upload_desc(cncpd_ctx* c) {
@@ -220,7 +258,8 @@ int enqueue_mode_m(cncpd_ctx* c, int n) {
 int enqueue_trailing(cncpd_ctx* c, const DevDesc* dd, const DevDesc& hd, int RP) {
   LaunchCfg lc{c->stream, c->num_sms};
   TRY(record(c, 0));
-  CU(launch_trailing_contract(lc, dd, hd, c->st, RP));
+  if (hd.use_tma) CU(launch_trailing_tma(lc, dd, hd, RP));
+  else CU(launch_trailing_contract(lc, dd, hd, c->st, RP));
   TRY(record(c, 1));
   return CNCPD_OK;
 }
@@ -228,8 +267,14 @@ int enqueue_trailing(cncpd_ctx* c, const DevDesc* dd, const DevDesc& hd, int RP)
 int enqueue_lead(cncpd_ctx* c, const DevDesc* dd, const DevDesc& hd, int RP, const int64_t* red_prefix) {
   LaunchCfg lc{c->stream, c->num_sms};
   TRY(record(c, 2));
-  CU(launch_lead_contract(lc, dd, hd, c->st, RP, red_prefix));
-  TRY(record(c, 3));
+  if (hd.use_tma) {
+    CU(launch_lead_tma(lc, dd, hd, RP));
+    TRY(record(c, 3));
+    CU(launch_reduce_splits(lc, dd, c->fp64, red_prefix));
+  } else {
+    CU(launch_lead_contract(lc, dd, hd, c->st, RP, red_prefix));
+    TRY(record(c, 3));
+  }
   return CNCPD_OK;
 }
 
@@ -259,6 +304,15 @@ int enqueue_readback(cncpd_ctx* c) {
 }
 
 size_t arena_bytes(cncpd_ctx* c) { return c->arena_elems * c->fsz; }
+
+// A bounded device-side wait gave up: clear the flag (so the handle can be
+// used again after the caller's decision) and report it.
+int timeout_error(cncpd_ctx* c) {
+  cudaMemsetAsync(&c->sc->timeout, 0, sizeof(int), c->stream);
+  cudaStreamSynchronize(c->stream);
+  c->dirty = true;
+  return set_err(CNCPD_ETIMEOUT, "a bounded device-side wait expired (pipeline stalled); iteration state discarded");
+}
 
 int enqueue_main(cncpd_ctx* c) {
   LaunchCfg lc{c->stream, c->num_sms};
@@ -354,6 +408,7 @@ int initialise(cncpd_ctx* c) {
   }
   TRY(enqueue_readback(c));
   TRY(sync(c));
+  if (c->hs->timeout) return timeout_error(c);
   if (c->hs->nonfinite || !std::isfinite(c->hs->F))
     return set_err(CNCPD_ENONFINITE, "initial objective is not finite (F = %g)", c->hs->F);
   c->F_prev = c->hs->F;
@@ -423,6 +478,7 @@ int run_iterations(cncpd_ctx* c, int n_iters, bool use_eps, cncpd_stats* out) {
       F = c->hs->F;
       st.reupdates++;
     }
+    if (c->hs->timeout) return timeout_error(c);
     if (c->hs->nonfinite || !std::isfinite(F))
       return set_err(CNCPD_ENONFINITE, "objective or Lipschitz constant not finite at iteration %d",
                      c->total_iters + 1);
@@ -647,10 +703,17 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
   CTRY(dalloc(c, (void**)&nout, CNCPD_KMAX * sizeof(double)));
   for (int k = 0; k < K; ++k) {
     const int64_t ne = d.lead_rows[k] * d.trail_cols[k];
+    const int64_t pitch = (d.trail_cols[k] + 15) / 16 * 16;  // rows start on 64-byte (FP32) boundaries
+    d.pitch[k] = pitch;
+    const int64_t nstore = d.lead_rows[k] * pitch;
     void* xb = nullptr;
     void* xlo = nullptr;
-    CTRY(dalloc(c, &xb, ne * xes));
-    if (st == ST_BF16X2) CTRY(dalloc(c, &xlo, ne * xes));
+    CTRY(dalloc(c, &xb, nstore * xes));
+    if (pitch != d.trail_cols[k]) CCU(cudaMemsetAsync(xb, 0, nstore * xes, c->stream));
+    if (st == ST_BF16X2) {
+      CTRY(dalloc(c, &xlo, nstore * xes));
+      if (pitch != d.trail_cols[k]) CCU(cudaMemsetAsync(xlo, 0, nstore * xes, c->stream));
+    }
     const void* src = X[k];
     cudaPointerAttributes pa;
     bool on_dev = false;
@@ -663,7 +726,8 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
       CCU(cudaMemcpyAsync(stage, src, ne * ses, cudaMemcpyHostToDevice, c->stream));
       src = stage;
     }
-    CCU(launch_quantize(c->stream, src, src_f64, xb, xlo, st, ne, nout + k, nscratch, nblk));
+    CCU(launch_quantize(c->stream, src, src_f64, xb, xlo, st, d.lead_rows[k], d.trail_cols[k], pitch, nout + k,
+                        nscratch, nblk));
     d.X[k] = xb;
     d.Xlo[k] = xlo;
   }
@@ -705,6 +769,25 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
     CTRY(dalloc(c, &p, (size_t)R[k] * R[k] * c->fsz));
     d.H[k] = p;
   }
+  // TMA descriptors of X for the FP32 kernels (two box shapes per block)
+  if (st == ST_F32 && tensor_map_encoder()) {
+    std::vector<CUtensorMap> maps(2 * CNCPD_KMAX);
+    bool ok = true;
+    for (int k = 0; k < K && ok; ++k) {
+      ok = encode_map(&maps[k], d.X[k], d.lead_rows[k], d.trail_cols[k], d.pitch[k], 32, 256,
+                      CU_TENSOR_MAP_SWIZZLE_128B) &&
+           encode_map(&maps[CNCPD_KMAX + k], d.X[k], d.lead_rows[k], d.trail_cols[k], d.pitch[k], 128, 64,
+                      CU_TENSOR_MAP_SWIZZLE_NONE);
+    }
+    if (ok) {
+      CUtensorMap* dm = nullptr;
+      CTRY(dalloc(c, (void**)&dm, maps.size() * sizeof(CUtensorMap)));
+      CCU(cudaMemcpyAsync(dm, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, c->stream));
+      d.tmap_trail = dm;
+      d.tmap_lead = dm + CNCPD_KMAX;
+    }
+  }
+  d.use_tma = (d.tmap_trail != nullptr) && tma_rank_supported(c->RP) && !getenv("CNCPD_NO_TMA");
   size_t pel = 0;
   plan_lead_splits(c, d, c->RP, c->fp64, &pel);
   plan_trailing_tiles(d);
@@ -962,6 +1045,7 @@ int cncpd_lra(cncpd_t h, const int* R_tilde, const void* const* Ut0, cncpd_dtype
     h->hd.Vinv[k] = a.Vinv[k] = p;
   }
   size_t pel = 0;
+  a.use_tma = (a.tmap_trail != nullptr) && tma_rank_supported(h->RPt) && !getenv("CNCPD_NO_TMA");
   plan_lead_splits(h, a, h->RPt, h->fp64, &pel);
   plan_trailing_tiles(a);
   TRY(dalloc(h, &a.partial, pel * h->fsz));

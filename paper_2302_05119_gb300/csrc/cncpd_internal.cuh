@@ -14,6 +14,7 @@
 //    MTTKRP of the mode being updated.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -34,7 +35,7 @@ struct DevScalars {
   int have_prev;     // L_prev valid (false in the first iteration)
   int have_cur;      // L_cur written by a sweep
   int nonfinite;     // set when F or a Lipschitz constant is NaN/Inf
-  int pad0;
+  int timeout;       // set when a bounded device-side wait gave up
   double F;          // objective of the last evaluated iterate
   double relerr;     // mean relative error of the same
   double Fk[CNCPD_KMAX];
@@ -88,6 +89,13 @@ struct DevDesc {
   int nsplit[CNCPD_KMAX];
   int64_t split_rows[CNCPD_KMAX];
   double* gpart;                        // per-CTA partial Grams of the fused update (FP64)
+  const CUtensorMap* tmap_trail;        // per-block TMA descriptors of X (FP32 storage), 256 x 32 boxes
+  const CUtensorMap* tmap_lead;         // per-block TMA descriptors of X (FP32 storage), 64 x 128 boxes
+  int use_tma;                          // 1: the TMA kernels run the level-1 contractions
+  int lt_rows;                          // rows per tile of the trailing contraction (64 or 256)
+  int tt_cols;                          // columns per tile of the lead contraction
+  int pad2;
+  int64_t pitch[CNCPD_KMAX];            // row pitch of X^(k) in elements (multiple of 16)
   int lt_prefix[CNCPD_KMAX + 1];       // cumulative 64-row tiles of the trailing-mode contraction
   int tt_prefix[CNCPD_KMAX + 1];       // cumulative (column tile x split) units of the lead-mode contraction
   int tt_ctiles[CNCPD_KMAX];           // column tiles per block
@@ -129,10 +137,10 @@ __device__ __forceinline__ void decode(const DevDesc* d, int k, int m0, int m1, 
 __device__ __forceinline__ int ceil_div_i(int a, int b) { return (a + b - 1) / b; }
 
 // Bucketed padded rank used as a compile-time register count.
-#define CNCPD_FOR_EACH_RP(X) X(4) X(8) X(12) X(16) X(20) X(24) X(32) X(40) X(48) X(64)
+#define CNCPD_FOR_EACH_RP(X) X(4) X(8) X(10) X(12) X(16) X(20) X(24) X(32) X(40) X(48) X(64)
 
 inline int rank_bucket(int R) {
-  const int b[] = {4, 8, 12, 16, 20, 24, 32, 40, 48, 64};
+  const int b[] = {4, 8, 10, 12, 16, 20, 24, 32, 40, 48, 64};
   for (int v : b) if (R <= v) return v;
   return -1;
 }
@@ -154,6 +162,10 @@ cudaError_t launch_trailing_contract(const LaunchCfg& c, const DevDesc* d_desc, 
 cudaError_t launch_lead_contract(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int st, int RP,
                                  const int64_t* d_red_prefix);
 int lead_cpt(int fp64, int RP);
+bool tma_rank_supported(int RP);
+cudaError_t launch_reduce_splits(const LaunchCfg& c, const DevDesc* d_desc, int fp64, const int64_t* d_red_prefix);
+cudaError_t launch_trailing_tma(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int RP);
+cudaError_t launch_lead_tma(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int RP);
 cudaError_t launch_level2(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int RP, int n);
 cudaError_t launch_gram(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int n_begin, int n_end, int which);
 cudaError_t launch_lipschitz(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int n, int use_core);
@@ -165,8 +177,10 @@ cudaError_t launch_objective(const LaunchCfg& c, const DevDesc* d_desc, const De
 cudaError_t launch_core_update(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int use_w, double delta_w);
 cudaError_t launch_iter_begin(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc);
 cudaError_t launch_redo_prepare(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc);
+// Quantise a rows x cols tensor (C order) into storage with row pitch `pitch` (padding zeroed).
 cudaError_t launch_quantize(cudaStream_t s, const void* src, int src_f64, void* dst, void* dst_lo, int st,
-                            int64_t n, double* norm2_out, double* norm2_scratch, int nblk);
+                            int64_t rows, int64_t cols, int64_t pitch, double* norm2_out, double* norm2_scratch,
+                            int nblk);
 cudaError_t launch_convert(cudaStream_t s, const void* src, int src_f64, void* dst, int dst_f64, int64_t n);
 cudaError_t launch_uniform_init(cudaStream_t s, void* dst, int fp64, int64_t n, uint64_t seed);
 cudaError_t launch_lmax_host(const double* d_H, int R, double* d_out, cudaStream_t s);

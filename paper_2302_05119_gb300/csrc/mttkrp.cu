@@ -59,7 +59,8 @@ k_trailing_contract(const DevDesc* __restrict__ d) {
     const int R = d->R[k];
     const void* X = d->X[k];
     const void* Xlo = d->Xlo[k];
-    const bool vec = (ST == ST_F32) && (J % 4 == 0);
+    const int64_t pitch = d->pitch[k];
+    const bool vec = (ST == ST_F32) && (pitch % 4 == 0);
     T acc0[RP], acc1[RP];
 #pragma unroll
     for (int r = 0; r < RP; ++r) acc0[r] = acc1[r] = T(0);
@@ -92,7 +93,7 @@ k_trailing_contract(const DevDesc* __restrict__ d) {
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
             const int64_t row = row0 + q * 4 + (lane >> 3);
-            v[q] = (row < rows) ? __ldg(reinterpret_cast<const float4*>(Xf + row * J + j0 + cq))
+            v[q] = (row < rows) ? __ldg(reinterpret_cast<const float4*>(Xf + row * pitch + j0 + cq))
                                 : make_float4(0.f, 0.f, 0.f, 0.f);
           }
 #pragma unroll
@@ -102,7 +103,7 @@ k_trailing_contract(const DevDesc* __restrict__ d) {
 #pragma unroll 8
           for (int q = 0; q < TR; ++q) {
             const int64_t row = row0 + q;
-            xs[warp][q][lane] = (j < J && row < rows) ? load_x<ST, T>(X, Xlo, row * J + j) : T(0);
+            xs[warp][q][lane] = (j < J && row < rows) ? load_x<ST, T>(X, Xlo, row * pitch + j) : T(0);
           }
         }
       } else {
@@ -110,7 +111,7 @@ k_trailing_contract(const DevDesc* __restrict__ d) {
 #pragma unroll 8
         for (int q = 0; q < TR; ++q) {
           const int64_t row = row0 + q;
-          xs[warp][q][lane] = (j < J && row < rows) ? load_x<ST, T>(X, Xlo, row * J + j) : T(0);
+          xs[warp][q][lane] = (j < J && row < rows) ? load_x<ST, T>(X, Xlo, row * pitch + j) : T(0);
         }
       }
       __syncwarp();
@@ -231,7 +232,8 @@ k_lead_contract(const DevDesc* __restrict__ d) {
     const int64_t rb = (int64_t)split * d->split_rows[k];
     const int64_t re = min(rows, rb + d->split_rows[k]);
     const int64_t col0 = (int64_t)ctile * 64 * CPT + (int64_t)tx * CPT;
-    const bool vec_ok = (J % CPT) == 0;
+    const int64_t pitch = d->pitch[k];
+    const bool vec_ok = (pitch % CPT) == 0;
     const void* X = d->X[k];
     const void* Xlo = d->Xlo[k];
     T acc[CPT][RP];
@@ -262,7 +264,7 @@ k_lead_contract(const DevDesc* __restrict__ d) {
           for (int q = 0; q < UNR; ++q) {
             const int ii = i + q * GR;
             if (ii < nrow) {
-              VecLoad<ST, T, CPT>::run(X, Xlo, (r0 + ii) * J, col0, J, vec_ok, x[q]);
+              VecLoad<ST, T, CPT>::run(X, Xlo, (r0 + ii) * pitch, col0, J, vec_ok, x[q]);
             } else {
 #pragma unroll
               for (int c = 0; c < CPT; ++c) x[q][c] = T(0);
@@ -418,6 +420,12 @@ static cudaError_t trailing_impl(const LaunchCfg& c, const DevDesc* dd, const De
   return cudaGetLastError();
 }
 
+cudaError_t launch_reduce_splits(const LaunchCfg& c, const DevDesc* dd, int fp64, const int64_t* d_red_prefix) {
+  if (fp64) k_reduce_splits<double><<<c.num_sms * 4, 256, 0, c.stream>>>(dd, d_red_prefix);
+  else k_reduce_splits<float><<<c.num_sms * 4, 256, 0, c.stream>>>(dd, d_red_prefix);
+  return cudaGetLastError();
+}
+
 template <int ST, typename T, int RP>
 static cudaError_t lead_impl(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, const int64_t* d_red_prefix) {
   const int total = hd.tt_prefix[hd.K];
@@ -436,8 +444,7 @@ static cudaError_t lead_impl(const LaunchCfg& c, const DevDesc* dd, const DevDes
   kern<<<grid, 256, smem, c.stream>>>(dd);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_reduce_splits<T><<<c.num_sms * 4, 256, 0, c.stream>>>(dd, d_red_prefix);
-  return cudaGetLastError();
+  return launch_reduce_splits(c, dd, sizeof(T) == 8, d_red_prefix);
 }
 
 int lead_cpt(int fp64, int RP) {

@@ -1,0 +1,396 @@
+// TMA-staged level-1 contractions of the dimension tree for FP32 tensors.
+//
+// Both kernels stream X^(k) (viewed as lead_rows x trail_cols, row pitch a
+// multiple of 16 elements) from HBM exactly once.  One producer warp per CTA
+// issues cp.async.bulk.tensor copies of X tiles into a ring of shared-memory
+// stages guarded by mbarriers and writes the matching Khatri-Rao rows of the
+// factors next to them; four consumer warps accumulate with packed
+// fma.rn.f32x2.  CTAs are persistent (one per SM) and walk a static list of
+// work units.  Every mbarrier wait is bounded in time: on expiry the kernel
+// sets the error word, stops issuing copies, waits for the copies already in
+// flight and returns.
+#include "cncpd_internal.cuh"
+#include "tma.cuh"
+
+namespace cncpd {
+
+// 32-bit mixed-radix decode over modes [m0, m1).
+__device__ __forceinline__ void decode32_t(const DevDesc* d, int k, int m0, int m1, int flat, int* idx) {
+  for (int m = m1 - 1; m >= m0; --m) {
+    const int I = (int)d->dims[k][m];
+    idx[m] = flat % I;
+    flat /= I;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Trailing contraction Pl[row, r] = sum_col X[row, col] W_t[col, r].
+// Tile = 256 rows; stage = 256 rows x 32 columns (32 KiB, 128-byte swizzle).
+// Consumer warp w owns rows 64w + lane and 64w + 32 + lane of the tile.
+// ---------------------------------------------------------------------------
+constexpr int TT_ROWS = 256;
+constexpr int TT_BC = 32;
+constexpr int TT_STAGES = 4;
+constexpr int TT_CONS = 4;
+
+template <int RP>
+struct TrailTma {
+  static constexpr int WST = (RP + 3) / 4 * 4;
+  static constexpr uint32_t X_BYTES = TT_ROWS * TT_BC * 4;
+  static constexpr uint32_t W_BYTES = TT_BC * WST * 4;
+  static constexpr size_t SMEM = 1024 + TT_STAGES * (size_t)(X_BYTES + W_BYTES) + 2 * TT_STAGES * 8;
+};
+
+template <int RP>
+__global__ void __launch_bounds__((TT_CONS + 1) * 32, 1) k_trailing_tma(const DevDesc* __restrict__ d) {
+  using S = TrailTma<RP>;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* xs = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  float* ws = reinterpret_cast<float*>(xs + TT_STAGES * S::X_BYTES);
+  uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(ws) + TT_STAGES * S::W_BYTES);
+  uint64_t* empty = full + TT_STAGES;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int* err = &d->sc->timeout;
+  const CUtensorMap* maps = d->tmap_trail;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TT_STAGES; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), TT_CONS);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const int K = d->K, N = d->N, h = d->h;
+  const int total = d->lt_prefix[K];
+
+  if (warp == TT_CONS) {
+    // ------------------------------------------------------------ producer
+    uint32_t it = 0;
+    bool ok = true;
+    for (int g = blockIdx.x; g < total && ok; g += gridDim.x) {
+      int k = 0;
+      while (d->lt_prefix[k + 1] <= g) ++k;
+      const int row0 = (g - d->lt_prefix[k]) * TT_ROWS;
+      const int J = (int)d->trail_cols[k];
+      const int R = d->R[k];
+      const int nch = (J + TT_BC - 1) / TT_BC;
+      if (lane == 0 && g == blockIdx.x) prefetch_tmap(&maps[k]);
+      for (int c = 0; c < nch; ++c, ++it) {
+        const int s = it % TT_STAGES;
+        const uint32_t ph = (it / TT_STAGES) & 1;
+        if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, err)) { ok = false; break; }
+        if (lane == 0) {
+          mbar_expect_tx(smem_u32(&full[s]), S::X_BYTES);
+          tma_load_2d(smem_u32(xs + s * S::X_BYTES), &maps[k], smem_u32(&full[s]), c * TT_BC, row0);
+        }
+        // Khatri-Rao rows of the trailing factors for the 32 columns of this stage
+        const int j = c * TT_BC + lane;
+        float w[S::WST];
+#pragma unroll
+        for (int r = 0; r < S::WST; ++r) w[r] = (j < J && r < R) ? 1.f : 0.f;
+        if (j < J) {
+          int idx[CNCPD_NMAX];
+          decode32_t(d, k, h, N, j, idx);
+          for (int m = h; m < N; ++m) {
+            const float* U = reinterpret_cast<const float*>(d->U1[k][m]) + (int64_t)idx[m] * R;
+#pragma unroll
+            for (int r = 0; r < RP; ++r)
+              if (r < R) w[r] *= U[r];
+          }
+        }
+        float4* wrow = reinterpret_cast<float4*>(ws + s * (S::W_BYTES / 4) + lane * S::WST);
+#pragma unroll
+        for (int q = 0; q < S::WST / 4; ++q) wrow[q] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&full[s]));
+      }
+    }
+    // copies still in flight land before the CTA leaves
+    for (uint32_t i = it > TT_STAGES ? it - TT_STAGES : 0; i < it; ++i)
+      mbar_wait_drain(smem_u32(&full[i % TT_STAGES]), (i / TT_STAGES) & 1);
+    return;
+  }
+
+  // -------------------------------------------------------------- consumers
+  uint32_t it = 0;
+  const int ra = warp * 64 + lane, rb = ra + 32;
+  for (int g = blockIdx.x; g < total; g += gridDim.x) {
+    int k = 0;
+    while (d->lt_prefix[k + 1] <= g) ++k;
+    const int row0 = (g - d->lt_prefix[k]) * TT_ROWS;
+    const int J = (int)d->trail_cols[k];
+    const int R = d->R[k];
+    const int nch = (J + TT_BC - 1) / TT_BC;
+    float acc0[RP], acc1[RP];
+#pragma unroll
+    for (int r = 0; r < RP; ++r) acc0[r] = acc1[r] = 0.f;
+    for (int c = 0; c < nch; ++c, ++it) {
+      const int s = it % TT_STAGES;
+      const uint32_t ph = (it / TT_STAGES) & 1;
+      if (!mbar_wait(smem_u32(&full[s]), ph, err)) return;
+      const unsigned char* xt = xs + s * S::X_BYTES;
+      const float* wt = ws + s * (S::W_BYTES / 4);
+#pragma unroll 2
+      for (int q = 0; q < 8; ++q) {
+        // 128-byte swizzle: 16-byte chunk q of row r sits at chunk q ^ (r & 7)
+        const float4 xa = *reinterpret_cast<const float4*>(xt + ra * 128 + ((q ^ (ra & 7)) << 4));
+        const float4 xb = *reinterpret_cast<const float4*>(xt + rb * 128 + ((q ^ (rb & 7)) << 4));
+        const float av[4] = {xa.x, xa.y, xa.z, xa.w};
+        const float bv[4] = {xb.x, xb.y, xb.z, xb.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float* wr = wt + (4 * q + e) * S::WST;
+#pragma unroll
+          for (int r = 0; r + 4 <= RP; r += 4) {
+            const float4 wv = *reinterpret_cast<const float4*>(wr + r);
+            ffma2(acc0[r], acc0[r + 1], av[e], av[e], wv.x, wv.y);
+            ffma2(acc0[r + 2], acc0[r + 3], av[e], av[e], wv.z, wv.w);
+            ffma2(acc1[r], acc1[r + 1], bv[e], bv[e], wv.x, wv.y);
+            ffma2(acc1[r + 2], acc1[r + 3], bv[e], bv[e], wv.z, wv.w);
+          }
+          if constexpr (RP % 4 == 2) {
+            const float2 wv = *reinterpret_cast<const float2*>(wr + RP - 2);
+            ffma2(acc0[RP - 2], acc0[RP - 1], av[e], av[e], wv.x, wv.y);
+            ffma2(acc1[RP - 2], acc1[RP - 1], bv[e], bv[e], wv.x, wv.y);
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
+    }
+    const int64_t rows = d->lead_rows[k];
+    float* P = reinterpret_cast<float*>(d->Pl[k]);
+    if (row0 + ra < rows) {
+#pragma unroll
+      for (int r = 0; r < RP; ++r)
+        if (r < R) P[(int64_t)(row0 + ra) * R + r] = acc0[r];
+    }
+    if (row0 + rb < rows) {
+#pragma unroll
+      for (int r = 0; r < RP; ++r)
+        if (r < R) P[(int64_t)(row0 + rb) * R + r] = acc1[r];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Lead contraction (split over rows) Pt[col, r] = sum_row X[row, col] W_l[row, r].
+// Unit = 128 columns x one row split; stage = 64 rows x 128 columns (32 KiB).
+// Consumer warp w takes rows w, w + 4, ... of a stage; lane l owns columns
+// 4l .. 4l + 3 (two packed column pairs).  W_l is stored with each value
+// duplicated ({w, w}) so the packed FMA takes it as one operand pair.
+// ---------------------------------------------------------------------------
+constexpr int LT_ROWS = 64;
+constexpr int LT_COLS = 128;
+constexpr int LT_CONS = 4;
+
+template <int RP>
+struct LeadTma {
+  static constexpr int STAGES = RP <= 32 ? 4 : 2;
+  static constexpr uint32_t X_BYTES = LT_ROWS * LT_COLS * 4;
+  static constexpr uint32_t W_BYTES = LT_ROWS * RP * 8;
+  static constexpr uint32_t RED_BYTES = LT_COLS * RP * 4;
+  static constexpr size_t SMEM = 1024 + STAGES * (size_t)(X_BYTES + W_BYTES) + RED_BYTES + 2 * STAGES * 8;
+};
+
+template <int RP>
+__global__ void __launch_bounds__((LT_CONS + 1) * 32, 1) k_lead_tma(const DevDesc* __restrict__ d) {
+  using S = LeadTma<RP>;
+  constexpr int ST = S::STAGES;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* xs = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  float2* wd = reinterpret_cast<float2*>(xs + ST * S::X_BYTES);
+  float* red = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(wd) + ST * S::W_BYTES);
+  uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(red) + S::RED_BYTES);
+  uint64_t* empty = full + ST;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int* err = &d->sc->timeout;
+  const CUtensorMap* maps = d->tmap_lead;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ST; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), LT_CONS);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const int K = d->K, h = d->h;
+  const int total = d->tt_prefix[K];
+
+  if (warp == LT_CONS) {
+    // ------------------------------------------------------------ producer
+    uint32_t it = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < total && ok; u += gridDim.x) {
+      int k = 0;
+      while (d->tt_prefix[k + 1] <= u) ++k;
+      const int local = u - d->tt_prefix[k];
+      const int ctile = local % d->tt_ctiles[k];
+      const int split = local / d->tt_ctiles[k];
+      const int rows = (int)d->lead_rows[k];
+      const int R = d->R[k];
+      const int rb = split * (int)d->split_rows[k];
+      const int re = min(rows, rb + (int)d->split_rows[k]);
+      if (lane == 0 && u == blockIdx.x) prefetch_tmap(&maps[k]);
+      for (int r0 = rb; r0 < re; r0 += LT_ROWS, ++it) {
+        const int s = it % ST;
+        const uint32_t ph = (it / ST) & 1;
+        if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, err)) { ok = false; break; }
+        if (lane == 0) {
+          mbar_expect_tx(smem_u32(&full[s]), S::X_BYTES);
+          tma_load_2d(smem_u32(xs + s * S::X_BYTES), &maps[k], smem_u32(&full[s]), ctile * LT_COLS, r0);
+        }
+        // Khatri-Rao rows of the lead factors, duplicated into pairs
+        float2* wst = wd + s * (S::W_BYTES / 8);
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          const int il = lane + 32 * half;
+          const int row = r0 + il;
+          float w[RP];
+#pragma unroll
+          for (int r = 0; r < RP; ++r) w[r] = (row < re && r < R) ? 1.f : 0.f;
+          if (row < re) {
+            int idx[CNCPD_NMAX];
+            decode32_t(d, k, 0, h, row, idx);
+            for (int m = 0; m < h; ++m) {
+              const float* U = reinterpret_cast<const float*>(d->U1[k][m]) + (int64_t)idx[m] * R;
+#pragma unroll
+              for (int r = 0; r < RP; ++r)
+                if (r < R) w[r] *= U[r];
+            }
+          }
+          float4* dst = reinterpret_cast<float4*>(wst + il * RP);
+#pragma unroll
+          for (int r = 0; r < RP; r += 2) dst[r / 2] = make_float4(w[r], w[r], w[r + 1], w[r + 1]);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&full[s]));
+      }
+    }
+    for (uint32_t i = it > (uint32_t)ST ? it - ST : 0; i < it; ++i)
+      mbar_wait_drain(smem_u32(&full[i % ST]), (i / ST) & 1);
+    return;
+  }
+
+  // -------------------------------------------------------------- consumers
+  uint32_t it = 0;
+  for (int u = blockIdx.x; u < total; u += gridDim.x) {
+    int k = 0;
+    while (d->tt_prefix[k + 1] <= u) ++k;
+    const int local = u - d->tt_prefix[k];
+    const int ctile = local % d->tt_ctiles[k];
+    const int split = local / d->tt_ctiles[k];
+    const int rows = (int)d->lead_rows[k];
+    const int J = (int)d->trail_cols[k];
+    const int R = d->R[k];
+    const int rb = split * (int)d->split_rows[k];
+    const int re = min(rows, rb + (int)d->split_rows[k]);
+    float acc[4][RP];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int r = 0; r < RP; ++r) acc[c][r] = 0.f;
+    for (int r0 = rb; r0 < re; r0 += LT_ROWS, ++it) {
+      const int s = it % ST;
+      const uint32_t ph = (it / ST) & 1;
+      if (!mbar_wait(smem_u32(&full[s]), ph, err)) continue;  // error recorded; keep the barrier schedule
+      const unsigned char* xt = xs + s * S::X_BYTES;
+      const float2* wt = wd + s * (S::W_BYTES / 8);
+#pragma unroll 4
+      for (int i = warp; i < LT_ROWS; i += LT_CONS) {
+        const float4 x = *reinterpret_cast<const float4*>(xt + i * (LT_COLS * 4) + lane * 16);
+        const float4* wr = reinterpret_cast<const float4*>(wt + i * RP);
+#pragma unroll
+        for (int r = 0; r < RP; r += 2) {
+          const float4 wv = wr[r / 2];  // {w_r, w_r, w_r+1, w_r+1}
+          ffma2(acc[0][r], acc[1][r], x.x, x.y, wv.x, wv.y);
+          ffma2(acc[2][r], acc[3][r], x.z, x.w, wv.x, wv.y);
+          ffma2(acc[0][r + 1], acc[1][r + 1], x.x, x.y, wv.z, wv.w);
+          ffma2(acc[2][r + 1], acc[3][r + 1], x.z, x.w, wv.z, wv.w);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
+    }
+    // fixed-order reduction of the four consumer warps: ((w1 + w2) + w3) + w0
+    for (int src = 1; src < LT_CONS; ++src) {
+      named_bar(1, LT_CONS * 32);
+      if (warp == src) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int r = 0; r < RP; ++r) {
+            float* p = red + (lane * 4 + c) * RP + r;
+            *p = (src == 1) ? acc[c][r] : *p + acc[c][r];
+          }
+      }
+    }
+    named_bar(1, LT_CONS * 32);
+    if (warp == 0) {
+      float* part = reinterpret_cast<float*>(d->partial) + d->partial_off[k] + (int64_t)split * J * R;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int col = ctile * LT_COLS + lane * 4 + c;
+        if (col < J) {
+#pragma unroll
+          for (int r = 0; r < RP; ++r)
+            if (r < R) part[(int64_t)col * R + r] = red[(lane * 4 + c) * RP + r] + acc[c][r];
+        }
+      }
+    }
+    named_bar(1, LT_CONS * 32);
+  }
+}
+
+// ------------------------------------------------------------- launchers ----
+
+template <int RP>
+static cudaError_t trailing_tma_impl(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd) {
+  const int total = hd.lt_prefix[hd.K];
+  if (total == 0) return cudaSuccess;
+  const size_t smem = TrailTma<RP>::SMEM;
+  cudaError_t e = cudaFuncSetAttribute(k_trailing_tma<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = total < c.num_sms ? total : c.num_sms;
+  k_trailing_tma<RP><<<grid, (TT_CONS + 1) * 32, smem, c.stream>>>(dd);
+  return cudaGetLastError();
+}
+
+template <int RP>
+static cudaError_t lead_tma_impl(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd) {
+  const int total = hd.tt_prefix[hd.K];
+  if (total == 0) return cudaSuccess;
+  const size_t smem = LeadTma<RP>::SMEM;
+  cudaError_t e = cudaFuncSetAttribute(k_lead_tma<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = total < c.num_sms ? total : c.num_sms;
+  k_lead_tma<RP><<<grid, (LT_CONS + 1) * 32, smem, c.stream>>>(dd);
+  return cudaGetLastError();
+}
+
+#define CNCPD_TMA_RP(X) X(4) X(8) X(10) X(12) X(16) X(20) X(24) X(32)
+
+bool tma_rank_supported(int RP) {
+#define TCASE(V) if (RP == V) return true;
+  CNCPD_TMA_RP(TCASE)
+#undef TCASE
+  return false;
+}
+
+cudaError_t launch_trailing_tma(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int RP) {
+#define TCASE(V) \
+  case V: return trailing_tma_impl<V>(c, dd, hd);
+  switch (RP) { CNCPD_TMA_RP(TCASE) }
+#undef TCASE
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_lead_tma(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int RP) {
+#define TCASE(V) \
+  case V: return lead_tma_impl<V>(c, dd, hd);
+  switch (RP) { CNCPD_TMA_RP(TCASE) }
+#undef TCASE
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace cncpd

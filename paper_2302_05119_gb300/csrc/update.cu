@@ -652,28 +652,32 @@ cudaError_t launch_grad(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd
 // in FP64 (per-CTA partial sums, then a fixed-order sum).
 // ---------------------------------------------------------------------------
 template <typename S>
-__global__ void k_quantize(const S* __restrict__ src, void* dst, void* dst_lo, int st, int64_t n, double* part) {
+__global__ void k_quantize(const S* __restrict__ src, void* dst, void* dst_lo, int st, int64_t rows, int64_t cols,
+                           int64_t pitch, double* part) {
   double acc = 0.0;
+  const int64_t n = rows * cols;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = i / cols;
+    const int64_t o = row * pitch + (i - row * cols);
     const double x = (double)src[i];
     double q;
     if (st == ST_F64) {
-      reinterpret_cast<double*>(dst)[i] = x;
+      reinterpret_cast<double*>(dst)[o] = x;
       q = x;
     } else if (st == ST_F32) {
       const float f = (float)x;
-      reinterpret_cast<float*>(dst)[i] = f;
+      reinterpret_cast<float*>(dst)[o] = f;
       q = f;
     } else if (st == ST_BF16) {
       const __nv_bfloat16 b = __double2bfloat16(x);
-      reinterpret_cast<__nv_bfloat16*>(dst)[i] = b;
+      reinterpret_cast<__nv_bfloat16*>(dst)[o] = b;
       q = (double)__bfloat162float(b);
     } else {
       const float f = (float)x;
       const __nv_bfloat16 hi = __float2bfloat16_rn(f);
       const __nv_bfloat16 lo = __float2bfloat16_rn(f - __bfloat162float(hi));
-      reinterpret_cast<__nv_bfloat16*>(dst)[i] = hi;
-      reinterpret_cast<__nv_bfloat16*>(dst_lo)[i] = lo;
+      reinterpret_cast<__nv_bfloat16*>(dst)[o] = hi;
+      reinterpret_cast<__nv_bfloat16*>(dst_lo)[o] = lo;
       q = (double)(__bfloat162float(hi) + __bfloat162float(lo));
     }
     acc = fma(q, q, acc);
@@ -696,10 +700,14 @@ __global__ void k_sum_partials(const double* part, int n, double* out) {
   }
 }
 
-cudaError_t launch_quantize(cudaStream_t s, const void* src, int src_f64, void* dst, void* dst_lo, int st, int64_t n,
-                            double* norm2_out, double* scratch, int nblk) {
-  if (src_f64) k_quantize<double><<<nblk, 256, 0, s>>>(reinterpret_cast<const double*>(src), dst, dst_lo, st, n, scratch);
-  else k_quantize<float><<<nblk, 256, 0, s>>>(reinterpret_cast<const float*>(src), dst, dst_lo, st, n, scratch);
+cudaError_t launch_quantize(cudaStream_t s, const void* src, int src_f64, void* dst, void* dst_lo, int st,
+                            int64_t rows, int64_t cols, int64_t pitch, double* norm2_out, double* scratch, int nblk) {
+  if (src_f64)
+    k_quantize<double><<<nblk, 256, 0, s>>>(reinterpret_cast<const double*>(src), dst, dst_lo, st, rows, cols, pitch,
+                                            scratch);
+  else
+    k_quantize<float><<<nblk, 256, 0, s>>>(reinterpret_cast<const float*>(src), dst, dst_lo, st, rows, cols, pitch,
+                                           scratch);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_sum_partials<<<1, 32, 0, s>>>(scratch, nblk, norm2_out);
