@@ -289,11 +289,14 @@ int enqueue_sweep(cncpd_ctx* c, int use_w) {
       if (n == c->h) TRY(enqueue_lead(c, c->dd, c->hd, c->RP, c->d_red_prefix));
     }
     TRY(enqueue_mode_m(c, n));
-    CU(launch_lipschitz(lc, c->dd, c->hd, c->fp64, n, core));
-    CU(launch_update(lc, c->dd, c->hd, c->fp64, c->RP, n, use_w, dw, core));  // includes the Gram of U^(n)
+    CU(launch_lipschitz(lc, c->dd, c->hd, c->fp64, n, core, n - 1));  // also the Gram of mode n-1
+    CU(launch_update(lc, c->dd, c->hd, c->fp64, c->RP, n, use_w, dw, core));
     if (c->lra) CU(launch_cross_gram(lc, c->dd, c->hd, c->fp64, n, n + 1));
   }
-  if (c->lra) CU(launch_lra_objective(lc, c->dd, c->hd, c->fp64, core));
+  if (c->lra) {
+    CU(launch_gram(lc, c->dd, c->hd, c->fp64, c->N - 1, c->N, 0));
+    CU(launch_lra_objective(lc, c->dd, c->hd, c->fp64, core));
+  }
   else CU(launch_objective(lc, c->dd, c->hd, c->fp64, c->RP, 1));
   return CNCPD_OK;
 }
@@ -437,9 +440,9 @@ long long kernels_per_replay(cncpd_ctx* c, int redo) {
     const int gsize = (m < c->h) ? c->h : c->N - c->h;
     if (c->lra) n += 2;     // collapsed M, cross Gram
     else if (gsize > 1) n += 1;
-    n += 2;                 // Lipschitz, update (with the Gram)
+    n += 2;                 // Lipschitz (with the previous mode's Gram), update
   }
-  n += 1;                   // objective
+  n += c->lra ? 2 : 1;      // (last Gram +) objective
   n += redo ? (c->lra ? 3 : 2) : 1;
   return n;
 }
@@ -792,11 +795,7 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
   plan_lead_splits(c, d, c->RP, c->fp64, &pel);
   plan_trailing_tiles(d);
   CTRY(dalloc(c, &d.partial, pel * c->fsz));
-  {
-    int gmax = 1;
-    for (int n = 0; n < N; ++n) gmax = std::max(gmax, update_grid(d, c->RP, n));
-    CTRY(dalloc(c, (void**)&d.gpart, (size_t)gmax * K * c->Rmax * c->Rmax * sizeof(double)));
-  }
+
   {
     std::vector<int64_t> pre(K + 1, 0);
     for (int k = 0; k < K; ++k) pre[k + 1] = pre[k] + d.trail_cols[k] * R[k];

@@ -88,7 +88,6 @@ struct DevDesc {
   int64_t partial_off[CNCPD_KMAX];     // element offset of block k's partials
   int nsplit[CNCPD_KMAX];
   int64_t split_rows[CNCPD_KMAX];
-  double* gpart;                        // per-CTA partial Grams of the fused update (FP64)
   const CUtensorMap* tmap_trail;        // per-block TMA descriptors of X (FP32 storage), 256 x 32 boxes
   const CUtensorMap* tmap_lead;         // per-block TMA descriptors of X (FP32 storage), 64 x 128 boxes
   int use_tma;                          // 1: the TMA kernels run the level-1 contractions
@@ -168,8 +167,9 @@ cudaError_t launch_trailing_tma(const LaunchCfg& c, const DevDesc* d_desc, const
 cudaError_t launch_lead_tma(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int RP);
 cudaError_t launch_level2(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int RP, int n);
 cudaError_t launch_gram(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int n_begin, int n_end, int which);
-cudaError_t launch_lipschitz(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int n, int use_core);
-int update_grid(const DevDesc& h_desc, int RP, int n);
+// prev >= 0: first form the Gram of mode `prev` (updated just before)
+cudaError_t launch_lipschitz(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int n, int use_core,
+                             int prev);
 cudaError_t launch_update(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int RP, int n,
                           int use_w, double delta_w, int use_core);
 // commit = 1: write F/relerr/core term of the solver state; 0: only out_relk against xnorm2_orig

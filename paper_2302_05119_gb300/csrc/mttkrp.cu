@@ -12,6 +12,8 @@
 // Gauss-Seidel order is kept: the trailing contraction uses the trailing
 // factors before the lead modes are updated, the lead contraction uses the
 // freshly updated lead factors.
+#include <algorithm>
+
 #include "cncpd_internal.cuh"
 
 namespace cncpd {
@@ -355,6 +357,7 @@ __device__ __forceinline__ T kr_row(const DevDesc* d, int k, int m0, int m1, int
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_level2(const DevDesc* __restrict__ d, int n) {
+  // Generic form (groups of three or more modes): one CTA per (i_n, block).
   const int k = blockIdx.y;
   const int64_t in = blockIdx.x;
   const int N = d->N, h = d->h;
@@ -395,6 +398,79 @@ __global__ void __launch_bounds__(256) k_level2(const DevDesc* __restrict__ d, i
     AT s = 0;
     for (int q = t; q < stride; q += R) s += red[q];
     reinterpret_cast<T*>(d->M[k][n])[in * R + t] = (T)s;
+  }
+}
+
+// Two-mode groups (third- and fourth-order tensors).  With n first in its
+// group, P[i_n][b][r] is contiguous per i_n:  M[i_n, r] = sum_b P W[b, r].
+// With n last, P[a][i_n][r]:  M[i_n, r] = sum_a P W[a, r], and NI
+// consecutive i_n of one a are contiguous.  The weights W (the other mode's
+// factor) are staged once per CTA in shared memory; every CTA produces NI
+// rows of M.
+constexpr int L2_NI = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_level2_pair(const DevDesc* __restrict__ d, int n) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* W = reinterpret_cast<T*>(smem_raw);
+  typedef typename Acc<T>::type AT;
+  __shared__ AT red[256];
+  const int k = blockIdx.y;
+  const int N = d->N, h = d->h;
+  const int m0 = (n < h) ? 0 : h;
+  const int other = (n == m0) ? n + 1 : m0;   // the group's other mode
+  const bool first = (n == m0);
+  const int In = (int)d->dims[k][n];
+  const int Io = (int)d->dims[k][other];
+  const int R = d->R[k];
+  const int i0 = blockIdx.x * L2_NI;
+  if (i0 >= In) return;
+  const int ni = min(L2_NI, In - i0);
+  const T* P = reinterpret_cast<const T*>((n < h) ? d->Pl[k] : d->Pt[k]);
+  const T* Uo = reinterpret_cast<const T*>(d->U1[k][other]);
+  for (int e = threadIdx.x; e < Io * R; e += blockDim.x) W[e] = Uo[e];
+  __syncthreads();
+  T* M = reinterpret_cast<T*>(d->M[k][n]);
+  const int t = threadIdx.x;
+  if (first) {
+    // rows i0 .. i0+ni-1, each a contiguous slab of Io*R; thread keeps r fixed
+    const int BR = Io * R;
+    const int stride = (blockDim.x / R) * R;
+    const int r = t % R;
+    for (int q = 0; q < ni; ++q) {
+      const T* slab = P + (int64_t)(i0 + q) * BR;
+      AT acc = 0;
+      if (t < stride) {
+#pragma unroll 4
+        for (int e = t; e < BR; e += stride) acc += (AT)(slab[e] * W[e]);
+      }
+      red[t] = acc;
+      __syncthreads();
+      if (t < R) {
+        AT s = 0;
+        for (int u = t; u < stride; u += R) s += red[u];
+        M[(int64_t)(i0 + q) * R + t] = (T)s;
+      }
+      __syncthreads();
+    }
+  } else {
+    // segment j in [0, ni*R) of row a starts at P[(a*In + i0)*R]; slices of a
+    const int JR = ni * R;
+    const int nsl = max(1, (int)blockDim.x / JR);
+    const int j = t % JR, sl = t / JR;
+    AT acc = 0;
+    if (sl < nsl) {
+      const int r = j % R;
+#pragma unroll 4
+      for (int a = sl; a < Io; a += nsl) acc += (AT)(P[((int64_t)a * In + i0) * R + j] * W[a * R + r]);
+    }
+    red[t] = acc;
+    __syncthreads();
+    if (t < JR) {
+      AT s = 0;
+      for (int u = 0; u < nsl; ++u) s += red[u * JR + t];
+      M[(int64_t)i0 * R + t] = (T)s;
+    }
   }
 }
 
@@ -524,8 +600,24 @@ cudaError_t launch_lead_contract(const LaunchCfg& c, const DevDesc* dd, const De
 
 cudaError_t launch_level2(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int RP, int n) {
   (void)RP;
-  int64_t imax = 0;
+  const int gsize = (n < hd.h) ? hd.h : hd.N - hd.h;
+  int64_t imax = 0, omax = 0;
   for (int k = 0; k < hd.K; ++k) imax = hd.dims[k][n] > imax ? hd.dims[k][n] : imax;
+  if (gsize == 2) {
+    const int m0 = (n < hd.h) ? 0 : hd.h;
+    const int other = (n == m0) ? n + 1 : m0;
+    for (int k = 0; k < hd.K; ++k) omax = std::max<int64_t>(omax, hd.dims[k][other] * hd.R[k]);
+    const size_t sm = (size_t)omax * (fp64 ? 8 : 4);
+    if (sm <= 160 * 1024) {
+      dim3 grid((unsigned)((imax + L2_NI - 1) / L2_NI), hd.K);
+      cudaError_t e = fp64 ? cudaFuncSetAttribute(k_level2_pair<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
+                           : cudaFuncSetAttribute(k_level2_pair<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+      if (fp64) k_level2_pair<double><<<grid, 256, sm, c.stream>>>(dd, n);
+      else k_level2_pair<float><<<grid, 256, sm, c.stream>>>(dd, n);
+      return cudaGetLastError();
+    }
+  }
   dim3 grid((unsigned)imax, hd.K);
   if (fp64) k_level2<double><<<grid, 256, 0, c.stream>>>(dd, n);
   else k_level2<float><<<grid, 256, 0, c.stream>>>(dd, n);

@@ -1,10 +1,11 @@
 // TMA-staged level-1 contractions of the dimension tree for FP32 tensors.
 //
 // Both kernels stream X^(k) (viewed as lead_rows x trail_cols, row pitch a
-// multiple of 16 elements) from HBM exactly once.  One producer warp per CTA
-// issues cp.async.bulk.tensor copies of X tiles into a ring of shared-memory
-// stages guarded by mbarriers and writes the matching Khatri-Rao rows of the
-// factors next to them; four consumer warps accumulate with packed
+// multiple of 16 elements) from HBM exactly once.  One thread issues
+// cp.async.bulk.tensor copies of X tiles into a ring of shared-memory stages
+// guarded by mbarriers (arrive.expect_tx), a second warp writes the matching
+// Khatri-Rao rows of the factors next to them (the stage is full after both
+// arrivals and all bytes), and four consumer warps accumulate with packed
 // fma.rn.f32x2.  CTAs are persistent (one per SM) and walk a static list of
 // work units.  Every mbarrier wait is bounded in time: on expiry the kernel
 // sets the error word, stops issuing copies, waits for the copies already in
@@ -42,7 +43,7 @@ struct TrailTma {
 };
 
 template <int RP>
-__global__ void __launch_bounds__((TT_CONS + 1) * 32, 1) k_trailing_tma(const DevDesc* __restrict__ d) {
+__global__ void __launch_bounds__((TT_CONS + 2) * 32, 1) k_trailing_tma(const DevDesc* __restrict__ d) {
   using S = TrailTma<RP>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* xs = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -54,7 +55,7 @@ __global__ void __launch_bounds__((TT_CONS + 1) * 32, 1) k_trailing_tma(const De
   const CUtensorMap* maps = d->tmap_trail;
   if (threadIdx.x == 0) {
     for (int s = 0; s < TT_STAGES; ++s) {
-      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&full[s]), 2);  // TMA issuer (with the byte count) + Khatri-Rao warp
       mbar_init(smem_u32(&empty[s]), TT_CONS);
     }
     fence_mbar_init();
@@ -63,8 +64,9 @@ __global__ void __launch_bounds__((TT_CONS + 1) * 32, 1) k_trailing_tma(const De
   const int K = d->K, N = d->N, h = d->h;
   const int total = d->lt_prefix[K];
 
-  if (warp == TT_CONS) {
-    // ------------------------------------------------------------ producer
+  if (warp == TT_CONS + 1) {
+    // ------------------------------------------- TMA issuer (one thread)
+    if (lane != 0) return;
     uint32_t it = 0;
     bool ok = true;
     for (int g = blockIdx.x; g < total && ok; g += gridDim.x) {
@@ -72,17 +74,36 @@ __global__ void __launch_bounds__((TT_CONS + 1) * 32, 1) k_trailing_tma(const De
       while (d->lt_prefix[k + 1] <= g) ++k;
       const int row0 = (g - d->lt_prefix[k]) * TT_ROWS;
       const int J = (int)d->trail_cols[k];
-      const int R = d->R[k];
       const int nch = (J + TT_BC - 1) / TT_BC;
-      if (lane == 0 && g == blockIdx.x) prefetch_tmap(&maps[k]);
+      if (g == blockIdx.x) prefetch_tmap(&maps[k]);
       for (int c = 0; c < nch; ++c, ++it) {
         const int s = it % TT_STAGES;
         const uint32_t ph = (it / TT_STAGES) & 1;
         if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, err)) { ok = false; break; }
-        if (lane == 0) {
-          mbar_expect_tx(smem_u32(&full[s]), S::X_BYTES);
-          tma_load_2d(smem_u32(xs + s * S::X_BYTES), &maps[k], smem_u32(&full[s]), c * TT_BC, row0);
-        }
+        mbar_arrive_expect_tx(smem_u32(&full[s]), S::X_BYTES);
+        tma_load_2d(smem_u32(xs + s * S::X_BYTES), &maps[k], smem_u32(&full[s]), c * TT_BC, row0);
+      }
+    }
+    // copies still in flight land before the CTA leaves
+    for (uint32_t i = it > TT_STAGES ? it - TT_STAGES : 0; i < it; ++i)
+      mbar_wait_drain(smem_u32(&full[i % TT_STAGES]), (i / TT_STAGES) & 1);
+    return;
+  }
+
+  if (warp == TT_CONS) {
+    // -------------------------------------------------- Khatri-Rao warp
+    uint32_t it = 0;
+    bool ok = true;
+    for (int g = blockIdx.x; g < total && ok; g += gridDim.x) {
+      int k = 0;
+      while (d->lt_prefix[k + 1] <= g) ++k;
+      const int J = (int)d->trail_cols[k];
+      const int R = d->R[k];
+      const int nch = (J + TT_BC - 1) / TT_BC;
+      for (int c = 0; c < nch; ++c, ++it) {
+        const int s = it % TT_STAGES;
+        const uint32_t ph = (it / TT_STAGES) & 1;
+        if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, err)) { ok = false; break; }
         // Khatri-Rao rows of the trailing factors for the 32 columns of this stage
         const int j = c * TT_BC + lane;
         float w[S::WST];
@@ -95,7 +116,7 @@ __global__ void __launch_bounds__((TT_CONS + 1) * 32, 1) k_trailing_tma(const De
             const float* U = reinterpret_cast<const float*>(d->U1[k][m]) + (int64_t)idx[m] * R;
 #pragma unroll
             for (int r = 0; r < RP; ++r)
-              if (r < R) w[r] *= U[r];
+              if (r < R) w[r] *= __ldg(U + r);
           }
         }
         float4* wrow = reinterpret_cast<float4*>(ws + s * (S::W_BYTES / 4) + lane * S::WST);
@@ -105,9 +126,6 @@ __global__ void __launch_bounds__((TT_CONS + 1) * 32, 1) k_trailing_tma(const De
         if (lane == 0) mbar_arrive(smem_u32(&full[s]));
       }
     }
-    // copies still in flight land before the CTA leaves
-    for (uint32_t i = it > TT_STAGES ? it - TT_STAGES : 0; i < it; ++i)
-      mbar_wait_drain(smem_u32(&full[i % TT_STAGES]), (i / TT_STAGES) & 1);
     return;
   }
 
@@ -194,7 +212,7 @@ struct LeadTma {
 };
 
 template <int RP>
-__global__ void __launch_bounds__((LT_CONS + 1) * 32, 1) k_lead_tma(const DevDesc* __restrict__ d) {
+__global__ void __launch_bounds__((LT_CONS + 2) * 32, 1) k_lead_tma(const DevDesc* __restrict__ d) {
   using S = LeadTma<RP>;
   constexpr int ST = S::STAGES;
   extern __shared__ unsigned char smem_raw[];
@@ -208,7 +226,7 @@ __global__ void __launch_bounds__((LT_CONS + 1) * 32, 1) k_lead_tma(const DevDes
   const CUtensorMap* maps = d->tmap_lead;
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
-      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&full[s]), 2);  // TMA issuer (with the byte count) + Khatri-Rao warp
       mbar_init(smem_u32(&empty[s]), LT_CONS);
     }
     fence_mbar_init();
@@ -217,8 +235,9 @@ __global__ void __launch_bounds__((LT_CONS + 1) * 32, 1) k_lead_tma(const DevDes
   const int K = d->K, h = d->h;
   const int total = d->tt_prefix[K];
 
-  if (warp == LT_CONS) {
-    // ------------------------------------------------------------ producer
+  if (warp == LT_CONS + 1) {
+    // ------------------------------------------- TMA issuer (one thread)
+    if (lane != 0) return;
     uint32_t it = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < total && ok; u += gridDim.x) {
@@ -228,18 +247,39 @@ __global__ void __launch_bounds__((LT_CONS + 1) * 32, 1) k_lead_tma(const DevDes
       const int ctile = local % d->tt_ctiles[k];
       const int split = local / d->tt_ctiles[k];
       const int rows = (int)d->lead_rows[k];
-      const int R = d->R[k];
       const int rb = split * (int)d->split_rows[k];
       const int re = min(rows, rb + (int)d->split_rows[k]);
-      if (lane == 0 && u == blockIdx.x) prefetch_tmap(&maps[k]);
+      if (u == blockIdx.x) prefetch_tmap(&maps[k]);
       for (int r0 = rb; r0 < re; r0 += LT_ROWS, ++it) {
         const int s = it % ST;
         const uint32_t ph = (it / ST) & 1;
         if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, err)) { ok = false; break; }
-        if (lane == 0) {
-          mbar_expect_tx(smem_u32(&full[s]), S::X_BYTES);
-          tma_load_2d(smem_u32(xs + s * S::X_BYTES), &maps[k], smem_u32(&full[s]), ctile * LT_COLS, r0);
-        }
+        mbar_arrive_expect_tx(smem_u32(&full[s]), S::X_BYTES);
+        tma_load_2d(smem_u32(xs + s * S::X_BYTES), &maps[k], smem_u32(&full[s]), ctile * LT_COLS, r0);
+      }
+    }
+    for (uint32_t i = it > (uint32_t)ST ? it - ST : 0; i < it; ++i)
+      mbar_wait_drain(smem_u32(&full[i % ST]), (i / ST) & 1);
+    return;
+  }
+
+  if (warp == LT_CONS) {
+    // -------------------------------------------------- Khatri-Rao warp
+    uint32_t it = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < total && ok; u += gridDim.x) {
+      int k = 0;
+      while (d->tt_prefix[k + 1] <= u) ++k;
+      const int local = u - d->tt_prefix[k];
+      const int split = local / d->tt_ctiles[k];
+      const int rows = (int)d->lead_rows[k];
+      const int R = d->R[k];
+      const int rb = split * (int)d->split_rows[k];
+      const int re = min(rows, rb + (int)d->split_rows[k]);
+      for (int r0 = rb; r0 < re; r0 += LT_ROWS, ++it) {
+        const int s = it % ST;
+        const uint32_t ph = (it / ST) & 1;
+        if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, err)) { ok = false; break; }
         // Khatri-Rao rows of the lead factors, duplicated into pairs
         float2* wst = wd + s * (S::W_BYTES / 8);
 #pragma unroll
@@ -256,7 +296,7 @@ __global__ void __launch_bounds__((LT_CONS + 1) * 32, 1) k_lead_tma(const DevDes
               const float* U = reinterpret_cast<const float*>(d->U1[k][m]) + (int64_t)idx[m] * R;
 #pragma unroll
               for (int r = 0; r < RP; ++r)
-                if (r < R) w[r] *= U[r];
+                if (r < R) w[r] *= __ldg(U + r);
             }
           }
           float4* dst = reinterpret_cast<float4*>(wst + il * RP);
@@ -267,8 +307,6 @@ __global__ void __launch_bounds__((LT_CONS + 1) * 32, 1) k_lead_tma(const DevDes
         if (lane == 0) mbar_arrive(smem_u32(&full[s]));
       }
     }
-    for (uint32_t i = it > (uint32_t)ST ? it - ST : 0; i < it; ++i)
-      mbar_wait_drain(smem_u32(&full[i % ST]), (i / ST) & 1);
     return;
   }
 
@@ -352,7 +390,7 @@ static cudaError_t trailing_tma_impl(const LaunchCfg& c, const DevDesc* dd, cons
   cudaError_t e = cudaFuncSetAttribute(k_trailing_tma<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = total < c.num_sms ? total : c.num_sms;
-  k_trailing_tma<RP><<<grid, (TT_CONS + 1) * 32, smem, c.stream>>>(dd);
+  k_trailing_tma<RP><<<grid, (TT_CONS + 2) * 32, smem, c.stream>>>(dd);
   return cudaGetLastError();
 }
 
@@ -364,7 +402,7 @@ static cudaError_t lead_tma_impl(const LaunchCfg& c, const DevDesc* dd, const De
   cudaError_t e = cudaFuncSetAttribute(k_lead_tma<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = total < c.num_sms ? total : c.num_sms;
-  k_lead_tma<RP><<<grid, (LT_CONS + 1) * 32, smem, c.stream>>>(dd);
+  k_lead_tma<RP><<<grid, (LT_CONS + 2) * 32, smem, c.stream>>>(dd);
   return cudaGetLastError();
 }
 

@@ -128,44 +128,66 @@ __device__ __forceinline__ double extrap_weight(double w_hat, int have_prev, dou
 }
 
 // ---------------------------------------------------------------------------
-// Grams G = U^T U (Table II operation 1) of modes [n_begin, n_end) of every
-// block; which = 0: the factors U1, which = 1: the LRA factors U~.  The sum
-// is taken exactly as the fused update forms it -- an FMA chain in the
-// factor type over each tile of `tile` rows, tiles added in FP64 in order --
-// so the two paths give bit-identical Grams.
+// Gram G = U^T U (Table II operation 1) of one I x R factor, computed by a
+// whole CTA: U is staged through shared memory GT rows at a time; for every
+// (a, b) an FMA chain in the factor type runs over each tile and the tile
+// sums are added in FP64 in order.  Every kernel that forms a Gram calls
+// this routine, so all of them give bit-identical results.
 // ---------------------------------------------------------------------------
+constexpr int GRAM_TILE = 64;
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_gram(const DevDesc* __restrict__ d, int n_begin, int n_end, int which,
-                                              int tile) {
+__device__ void block_gram(const T* __restrict__ U, int64_t I, int R, double* __restrict__ G, T* tile) {
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int nt = blockDim.x * blockDim.y;
+  const int RR = R * R;
+  double acc[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+  for (int64_t t0 = 0; t0 < I; t0 += GRAM_TILE) {
+    const int n = (int)min((int64_t)GRAM_TILE, I - t0);
+    __syncthreads();
+    for (int e = tid; e < n * R; e += nt) tile[e] = U[t0 * R + e];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int p = q * nt + tid;
+      if (p < RR) {
+        const int a = p / R, b = p % R;
+        T s = T(0);
+        for (int i = 0; i < n; ++i) s = fma(tile[i * R + a], tile[i * R + b], s);
+        acc[q] += (double)s;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int p = q * nt + tid;
+    if (p < RR) G[p] = acc[q];
+  }
+  __syncthreads();
+}
+
+// Grams of modes [n_begin, n_end) of every block; which = 0: the factors
+// U1, which = 1: the LRA factors U~.  One CTA per (block, mode).
+template <typename T>
+__global__ void __launch_bounds__(256) k_gram(const DevDesc* __restrict__ d, int n_begin, int n_end, int which) {
+  __shared__ T tile[GRAM_TILE * CNCPD_RMAX];
   const int nm = n_end - n_begin;
   const int k = blockIdx.x / nm;
   const int n = n_begin + blockIdx.x % nm;
   const T* U = reinterpret_cast<const T*>(which ? d->Ut[k][n] : d->U1[k][n]);
   const int R = which ? d->Rt[k] : d->R[k];
   double* G = which ? d->Gt[k][n] : d->G[k][n];
-  const int64_t I = d->dims[k][n];
-  for (int p = threadIdx.x; p < R * R; p += blockDim.x) {
-    const int a = p / R, b = p % R;
-    double s = 0.0;
-    for (int64_t t0 = 0; t0 < I; t0 += tile) {
-      const int64_t t1 = min(I, t0 + tile);
-      T acc = T(0);
-      for (int64_t i = t0; i < t1; ++i) acc = fma(U[i * R + a], U[i * R + b], acc);
-      s += (double)acc;
-    }
-    G[p] = s;
-  }
+  block_gram<T>(U, d->dims[k][n], R, G, tile);
 }
 
 cudaError_t launch_gram(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int n_begin, int n_end,
                         int which) {
   if (n_end <= n_begin) return cudaSuccess;
   const int grid = hd.K * (n_end - n_begin);
-  int rmax = 1;
-  for (int k = 0; k < hd.K; ++k) rmax = std::max(rmax, which ? hd.Rt[k] : hd.R[k]);
-  const int tile = std::max(1, 128 / rank_bucket(hd.Rmax));  // rows per CTA of the fused update
-  if (fp64) k_gram<double><<<grid, 256, 0, c.stream>>>(dd, n_begin, n_end, which, tile);
-  else k_gram<float><<<grid, 256, 0, c.stream>>>(dd, n_begin, n_end, which, tile);
+  if (fp64) k_gram<double><<<grid, 256, 0, c.stream>>>(dd, n_begin, n_end, which);
+  else k_gram<float><<<grid, 256, 0, c.stream>>>(dd, n_begin, n_end, which);
   return cudaGetLastError();
 }
 
@@ -174,10 +196,14 @@ cudaError_t launch_gram(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd
 // operation 4) and L_u^(n,k) = ||H||_2 (Eq. eqLipsLu).  One CTA per block.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_lipschitz(const DevDesc* __restrict__ d, int n, int use_core, int want_L) {
+__global__ void __launch_bounds__(256) k_lipschitz(const DevDesc* __restrict__ d, int n, int use_core, int want_L,
+                                                   int prev) {
   const int k = blockIdx.x;
   const int R = d->R[k], N = d->N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (prev >= 0)  // Gram of the mode updated just before (Table II operation 1)
+    block_gram<T>(reinterpret_cast<const T*>(d->U1[k][prev]), d->dims[k][prev], R, d->G[k][prev],
+                  reinterpret_cast<T*>(smem_raw));
   LmaxScratch scr;
   scr.carve(smem_raw, R);
   double* Hs = scr.Hs;
@@ -199,13 +225,14 @@ __global__ void __launch_bounds__(256) k_lipschitz(const DevDesc* __restrict__ d
   }
 }
 
-cudaError_t launch_lipschitz(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int n, int use_core) {
-  const size_t sm = lmax_smem_bytes(hd.Rmax);
+cudaError_t launch_lipschitz(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int n, int use_core,
+                             int prev) {
+  const size_t sm = std::max(lmax_smem_bytes(hd.Rmax), (size_t)GRAM_TILE * hd.Rmax * (fp64 ? 8 : 4));
   cudaError_t e = fp64 ? allow_smem(k_lipschitz<double>, sm) : allow_smem(k_lipschitz<float>, sm);
   if (e != cudaSuccess) return e;
   const int nt = hd.Rmax <= 16 ? 128 : 256;
-  if (fp64) k_lipschitz<double><<<hd.K, nt, sm, c.stream>>>(dd, n, use_core, 1);
-  else k_lipschitz<float><<<hd.K, nt, sm, c.stream>>>(dd, n, use_core, 1);
+  if (fp64) k_lipschitz<double><<<hd.K, nt, sm, c.stream>>>(dd, n, use_core, 1, prev);
+  else k_lipschitz<float><<<hd.K, nt, sm, c.stream>>>(dd, n, use_core, 1, prev);
   return cudaGetLastError();
 }
 
@@ -217,10 +244,8 @@ cudaError_t launch_lipschitz(const LaunchCfg& c, const DevDesc* dd, const DevDes
 //   individual columns: U1 <- P(U_hat - G_hat / L_u^(n,k))
 //   shared columns:     U1 <- P(U_hat_C - sum_k G_hat_C / sum_k L_u^(n,k)),
 //                       the same value written to every block
-//   U2 <- old U1,
-// followed by the Gram G^(n,k) = U1^T U1 of the new factor (Table II
-// operation 1): per-CTA partial Grams, summed in CTA order by the last CTA
-// to arrive (deterministic, no waiting).
+//   U2 <- old U1.
+// (The Gram of the new factor is formed by the next kernel that needs it.)
 // Thread (c, y) owns column c of row blockIdx.x * ROWS + y and walks the
 // blocks in chunks of KC, keeping the shared-column gradient sum in a
 // register, so the coupled sum needs no cross-CTA communication.  Rows are
@@ -240,9 +265,7 @@ __global__ void __launch_bounds__(128) k_update(const DevDesc* __restrict__ d, i
   constexpr int KC = UpdCfg<T, RP>::KC;
   __shared__ T Hs[KC][RP * RP];
   __shared__ T uh[KC][ROWS][RP];
-  __shared__ int is_last;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T (*nu)[ROWS][RP] = reinterpret_cast<T (*)[ROWS][RP]>(smem_raw);  // new rows of every block
+
   const int c = threadIdx.x;
   const int y = threadIdx.y;
   const int tid = c + y * RP;
@@ -306,7 +329,6 @@ __global__ void __launch_bounds__(128) k_update(const DevDesc* __restrict__ d, i
           }
           reinterpret_cast<T*>(d->U2[k][n])[i * R + c] = u1[kk];
           reinterpret_cast<T*>(d->U1[k][n])[i * R + c] = nv;
-          nu[k][y][c] = nv;
         } else {
           sumC += g;
           uhC = uhat;
@@ -325,41 +347,9 @@ __global__ void __launch_bounds__(128) k_update(const DevDesc* __restrict__ d, i
       const int R = d->R[k];
       reinterpret_cast<T*>(d->U2[k][n])[i * R + c] = u1C;
       reinterpret_cast<T*>(d->U1[k][n])[i * R + c] = nv;
-      nu[k][y][c] = nv;
     }
   }
 
-  // ---- Gram of the new rows of this CTA (every block), then the last CTA sums
-  __syncthreads();
-  const int RR = d->Rmax * d->Rmax;
-  for (int k = 0; k < K; ++k) {
-    const int R = d->R[k];
-    const int nrow = (int)min((int64_t)ROWS, d->dims[k][n] - row0);
-    double* gp = d->gpart + ((int64_t)blockIdx.x * K + k) * RR;
-    for (int p = tid; p < R * R; p += NT) {
-      const int a = p / R, b = p % R;
-      T acc = T(0);
-      for (int r = 0; r < nrow; ++r) acc = fma(nu[k][r][a], nu[k][r][b], acc);
-      gp[p] = (double)acc;
-    }
-  }
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) is_last = (atomicAdd(&sc->done_counter[0], 1) == (int)gridDim.x - 1);
-  __syncthreads();
-  if (is_last) {
-    __threadfence();
-    for (int k = 0; k < K; ++k) {
-      const int R = d->R[k];
-      double* G = d->G[k][n];
-      for (int p = tid; p < R * R; p += NT) {
-        double s = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(d->gpart + ((int64_t)b * K + k) * RR + p);
-        G[p] = s;
-      }
-    }
-    if (tid == 0) sc->done_counter[0] = 0;
-  }
 }
 
 template <typename T, int RP>
@@ -369,19 +359,8 @@ static cudaError_t update_impl(const LaunchCfg& c, const DevDesc* dd, const DevD
   int64_t imax = 0;
   for (int k = 0; k < hd.K; ++k) imax = hd.dims[k][n] > imax ? hd.dims[k][n] : imax;
   const unsigned grid = (unsigned)((imax + ROWS - 1) / ROWS);
-  const size_t sm = sizeof(T) * (size_t)hd.K * ROWS * RP;
-  cudaError_t e = allow_smem(k_update<T, RP>, sm + sizeof(T) * (UpdCfg<T, RP>::KC * RP * (RP + ROWS)) + 64);
-  if (e != cudaSuccess) return e;
-  k_update<T, RP><<<grid, dim3(RP, ROWS), sm, c.stream>>>(dd, n, use_w, delta_w, use_core);
+  k_update<T, RP><<<grid, dim3(RP, ROWS), 0, c.stream>>>(dd, n, use_w, delta_w, use_core);
   return cudaGetLastError();
-}
-
-// Number of CTAs of the update of mode n (sizes the partial-Gram buffer).
-int update_grid(const DevDesc& hd, int RP, int n) {
-  const int ROWS = (128 / RP) > 0 ? 128 / RP : 1;
-  int64_t imax = 0;
-  for (int k = 0; k < hd.K; ++k) imax = hd.dims[k][n] > imax ? hd.dims[k][n] : imax;
-  return (int)((imax + ROWS - 1) / ROWS);
 }
 
 cudaError_t launch_update(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int RP, int n,
@@ -416,7 +395,10 @@ __global__ void __launch_bounds__(256) k_objective(const DevDesc* __restrict__ d
   __shared__ double red[256];
   __shared__ double cr[RP];
   __shared__ int is_last;
+  __shared__ T tile[GRAM_TILE * RP];
   const int R = d->R[k];
+  if (commit)  // Gram of the last mode, just updated
+    block_gram<T>(reinterpret_cast<const T*>(d->U1[k][n]), d->dims[k][n], R, d->G[k][n], tile);
   const int64_t I = d->dims[k][n];
   const T* M = reinterpret_cast<const T*>(d->M[k][n]);
   const T* U = reinterpret_cast<const T*>(d->U1[k][n]);
@@ -441,11 +423,12 @@ __global__ void __launch_bounds__(256) k_objective(const DevDesc* __restrict__ d
     xx += g;
   }
   if (tid < R) xx -= 2.0 * sc->lam1[k][tid] * cr[tid];
-  red[tid] = xx;
+  for (int o = 16; o > 0; o >>= 1) xx += __shfl_xor_sync(0xffffffffu, xx, o);
+  if ((tid & 31) == 0) red[tid >> 5] = xx;
   __syncthreads();
   if (tid == 0) {
     double t = 0.0;
-    for (int q = 0; q < NT; ++q) t += red[q];
+    for (int q = 0; q < (NT + 31) / 32; ++q) t += red[q];
     const double x2 = commit ? sc->xnorm2[k] : sc->xnorm2_orig[k];
     const double Fk = 0.5 * (x2 + t);
     const double rel = x2 > 0.0 ? sqrt(fmax(2.0 * Fk, 0.0) / x2) : 0.0;
@@ -632,8 +615,8 @@ cudaError_t launch_grad(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd
     const size_t sm = lmax_smem_bytes(hd.Rmax);
     cudaError_t e = fp64 ? allow_smem(k_lipschitz<double>, sm) : allow_smem(k_lipschitz<float>, sm);
     if (e != cudaSuccess) return e;
-    if (fp64) k_lipschitz<double><<<hd.K, 256, sm, c.stream>>>(dd, n, use_core, 0);
-    else k_lipschitz<float><<<hd.K, 256, sm, c.stream>>>(dd, n, use_core, 0);
+    if (fp64) k_lipschitz<double><<<hd.K, 256, sm, c.stream>>>(dd, n, use_core, 0, -1);
+    else k_lipschitz<float><<<hd.K, 256, sm, c.stream>>>(dd, n, use_core, 0, -1);
   }
 #define GCASE(V)                                                                        \
   case V: {                                                                             \
