@@ -327,7 +327,15 @@ __global__ void k_reduce_splits(const DevDesc* __restrict__ d, const int64_t* __
     const T* part = reinterpret_cast<const T*>(d->partial) + d->partial_off[k] + local;
     T s = T(0);
     const int ns = d->nsplit[k];
-    for (int i = 0; i < ns; ++i) s += part[(int64_t)i * stride];
+    int i = 0;
+    for (; i + 8 <= ns; i += 8) {
+      T v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = part[(int64_t)(i + q) * stride];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) s += v[q];
+    }
+    for (; i < ns; ++i) s += part[(int64_t)i * stride];
     reinterpret_cast<T*>(d->Pt[k])[local] = s;
   }
 }
@@ -403,16 +411,11 @@ __global__ void __launch_bounds__(256) k_level2(const DevDesc* __restrict__ d, i
 
 // Two-mode groups (third- and fourth-order tensors).  With n first in its
 // group, P[i_n][b][r] is contiguous per i_n:  M[i_n, r] = sum_b P W[b, r].
-// With n last, P[a][i_n][r]:  M[i_n, r] = sum_a P W[a, r], and NI
-// consecutive i_n of one a are contiguous.  The weights W (the other mode's
-// factor) are staged once per CTA in shared memory; every CTA produces NI
-// rows of M.
-constexpr int L2_NI = 8;
-
+// With n last, P[a][i_n][r]:  M[i_n, r] = sum_a P W[a, r], and ni
+// consecutive i_n of one a are contiguous.  W is the other mode's factor
+// (read through the read-only cache); a CTA produces ni rows of M.
 template <typename T>
-__global__ void __launch_bounds__(256) k_level2_pair(const DevDesc* __restrict__ d, int n) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* W = reinterpret_cast<T*>(smem_raw);
+__global__ void __launch_bounds__(256) k_level2_pair(const DevDesc* __restrict__ d, int n, int ni_max) {
   typedef typename Acc<T>::type AT;
   __shared__ AT red[256];
   const int k = blockIdx.y;
@@ -423,28 +426,32 @@ __global__ void __launch_bounds__(256) k_level2_pair(const DevDesc* __restrict__
   const int In = (int)d->dims[k][n];
   const int Io = (int)d->dims[k][other];
   const int R = d->R[k];
-  const int i0 = blockIdx.x * L2_NI;
+  const int i0 = blockIdx.x * ni_max;
   if (i0 >= In) return;
-  const int ni = min(L2_NI, In - i0);
+  const int ni = min(ni_max, In - i0);
   const T* P = reinterpret_cast<const T*>((n < h) ? d->Pl[k] : d->Pt[k]);
-  const T* Uo = reinterpret_cast<const T*>(d->U1[k][other]);
-  for (int e = threadIdx.x; e < Io * R; e += blockDim.x) W[e] = Uo[e];
-  __syncthreads();
+  const T* W = reinterpret_cast<const T*>(d->U1[k][other]);
   T* M = reinterpret_cast<T*>(d->M[k][n]);
   const int t = threadIdx.x;
   if (first) {
-    // rows i0 .. i0+ni-1, each a contiguous slab of Io*R; thread keeps r fixed
+    // ni contiguous slabs of Io*R; thread keeps r fixed, all slabs at once
     const int BR = Io * R;
     const int stride = (blockDim.x / R) * R;
     const int r = t % R;
-    for (int q = 0; q < ni; ++q) {
-      const T* slab = P + (int64_t)(i0 + q) * BR;
-      AT acc = 0;
-      if (t < stride) {
-#pragma unroll 4
-        for (int e = t; e < BR; e += stride) acc += (AT)(slab[e] * W[e]);
+    AT acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0;
+    if (t < stride) {
+#pragma unroll 2
+      for (int e = t; e < BR; e += stride) {
+        const T w = __ldg(W + e);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (q < ni) acc[q] += (AT)(P[(int64_t)(i0 + q) * BR + e] * w);
       }
-      red[t] = acc;
+    }
+    for (int q = 0; q < ni; ++q) {
+      red[t] = acc[q];
       __syncthreads();
       if (t < R) {
         AT s = 0;
@@ -459,10 +466,10 @@ __global__ void __launch_bounds__(256) k_level2_pair(const DevDesc* __restrict__
     const int nsl = max(1, (int)blockDim.x / JR);
     const int j = t % JR, sl = t / JR;
     AT acc = 0;
-    if (sl < nsl) {
+    if (sl < nsl && t < nsl * JR) {
       const int r = j % R;
-#pragma unroll 4
-      for (int a = sl; a < Io; a += nsl) acc += (AT)(P[((int64_t)a * In + i0) * R + j] * W[a * R + r]);
+#pragma unroll 8
+      for (int a = sl; a < Io; a += nsl) acc += (AT)(P[((int64_t)a * In + i0) * R + j] * __ldg(W + a * R + r));
     }
     red[t] = acc;
     __syncthreads();
@@ -604,19 +611,14 @@ cudaError_t launch_level2(const LaunchCfg& c, const DevDesc* dd, const DevDesc& 
   int64_t imax = 0, omax = 0;
   for (int k = 0; k < hd.K; ++k) imax = hd.dims[k][n] > imax ? hd.dims[k][n] : imax;
   if (gsize == 2) {
-    const int m0 = (n < hd.h) ? 0 : hd.h;
-    const int other = (n == m0) ? n + 1 : m0;
-    for (int k = 0; k < hd.K; ++k) omax = std::max<int64_t>(omax, hd.dims[k][other] * hd.R[k]);
-    const size_t sm = (size_t)omax * (fp64 ? 8 : 4);
-    if (sm <= 160 * 1024) {
-      dim3 grid((unsigned)((imax + L2_NI - 1) / L2_NI), hd.K);
-      cudaError_t e = fp64 ? cudaFuncSetAttribute(k_level2_pair<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
-                           : cudaFuncSetAttribute(k_level2_pair<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      if (e != cudaSuccess) return e;
-      if (fp64) k_level2_pair<double><<<grid, 256, sm, c.stream>>>(dd, n);
-      else k_level2_pair<float><<<grid, 256, sm, c.stream>>>(dd, n);
-      return cudaGetLastError();
-    }
+    (void)omax;
+    // rows per CTA: small enough for ~4 CTAs per SM over all blocks, ni*R <= 256
+    int ni = std::max(1, std::min(8, 256 / std::max(1, hd.Rmax)));
+    while (ni > 1 && ((imax + ni - 1) / ni) * hd.K < 4LL * c.num_sms) ni /= 2;
+    dim3 grid((unsigned)((imax + ni - 1) / ni), hd.K);
+    if (fp64) k_level2_pair<double><<<grid, 256, 0, c.stream>>>(dd, n, ni);
+    else k_level2_pair<float><<<grid, 256, 0, c.stream>>>(dd, n, ni);
+    return cudaGetLastError();
   }
   dim3 grid((unsigned)imax, hd.K);
   if (fp64) k_level2<double><<<grid, 256, 0, c.stream>>>(dd, n);

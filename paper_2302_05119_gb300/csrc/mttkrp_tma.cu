@@ -3,10 +3,10 @@
 // Both kernels stream X^(k) (viewed as lead_rows x trail_cols, row pitch a
 // multiple of 16 elements) from HBM exactly once.  One thread issues
 // cp.async.bulk.tensor copies of X tiles into a ring of shared-memory stages
-// guarded by mbarriers (arrive.expect_tx), a second warp writes the matching
-// Khatri-Rao rows of the factors next to them (the stage is full after both
-// arrivals and all bytes), and four consumer warps accumulate with packed
-// fma.rn.f32x2.  CTAs are persistent (one per SM) and walk a static list of
+// guarded by mbarriers (arrive.expect_tx), three warps take turns writing the
+// matching Khatri-Rao rows of the factors next to them (a stage is full after
+// both arrivals and all bytes), and four consumer warps accumulate with
+// packed fma.rn.f32x2.  CTAs are persistent (one per SM) and walk a static list of
 // work units.  Every mbarrier wait is bounded in time: on expiry the kernel
 // sets the error word, stops issuing copies, waits for the copies already in
 // flight and returns.
@@ -33,6 +33,7 @@ constexpr int TT_ROWS = 256;
 constexpr int TT_BC = 32;
 constexpr int TT_STAGES = 4;
 constexpr int TT_CONS = 4;
+constexpr int NKR = 3;  // Khatri-Rao warps, stage i handled by warp i mod NKR
 
 template <int RP>
 struct TrailTma {
@@ -43,7 +44,7 @@ struct TrailTma {
 };
 
 template <int RP>
-__global__ void __launch_bounds__((TT_CONS + 2) * 32, 1) k_trailing_tma(const DevDesc* __restrict__ d) {
+__global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(const DevDesc* __restrict__ d) {
   using S = TrailTma<RP>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* xs = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -64,7 +65,7 @@ __global__ void __launch_bounds__((TT_CONS + 2) * 32, 1) k_trailing_tma(const De
   const int K = d->K, N = d->N, h = d->h;
   const int total = d->lt_prefix[K];
 
-  if (warp == TT_CONS + 1) {
+  if (warp == TT_CONS + NKR) {
     // ------------------------------------------- TMA issuer (one thread)
     if (lane != 0) return;
     uint32_t it = 0;
@@ -90,8 +91,9 @@ __global__ void __launch_bounds__((TT_CONS + 2) * 32, 1) k_trailing_tma(const De
     return;
   }
 
-  if (warp == TT_CONS) {
-    // -------------------------------------------------- Khatri-Rao warp
+  if (warp >= TT_CONS) {
+    // ------------------------------------------------- Khatri-Rao warps
+    const int kw = warp - TT_CONS;
     uint32_t it = 0;
     bool ok = true;
     for (int g = blockIdx.x; g < total && ok; g += gridDim.x) {
@@ -101,6 +103,7 @@ __global__ void __launch_bounds__((TT_CONS + 2) * 32, 1) k_trailing_tma(const De
       const int R = d->R[k];
       const int nch = (J + TT_BC - 1) / TT_BC;
       for (int c = 0; c < nch; ++c, ++it) {
+        if ((int)(it % NKR) != kw) continue;
         const int s = it % TT_STAGES;
         const uint32_t ph = (it / TT_STAGES) & 1;
         if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, err)) { ok = false; break; }
@@ -212,7 +215,7 @@ struct LeadTma {
 };
 
 template <int RP>
-__global__ void __launch_bounds__((LT_CONS + 2) * 32, 1) k_lead_tma(const DevDesc* __restrict__ d) {
+__global__ void __launch_bounds__((LT_CONS + NKR + 1) * 32, 1) k_lead_tma(const DevDesc* __restrict__ d) {
   using S = LeadTma<RP>;
   constexpr int ST = S::STAGES;
   extern __shared__ unsigned char smem_raw[];
@@ -235,7 +238,7 @@ __global__ void __launch_bounds__((LT_CONS + 2) * 32, 1) k_lead_tma(const DevDes
   const int K = d->K, h = d->h;
   const int total = d->tt_prefix[K];
 
-  if (warp == LT_CONS + 1) {
+  if (warp == LT_CONS + NKR) {
     // ------------------------------------------- TMA issuer (one thread)
     if (lane != 0) return;
     uint32_t it = 0;
@@ -263,8 +266,9 @@ __global__ void __launch_bounds__((LT_CONS + 2) * 32, 1) k_lead_tma(const DevDes
     return;
   }
 
-  if (warp == LT_CONS) {
-    // -------------------------------------------------- Khatri-Rao warp
+  if (warp >= LT_CONS) {
+    // ------------------------------------------------- Khatri-Rao warps
+    const int kw = warp - LT_CONS;
     uint32_t it = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < total && ok; u += gridDim.x) {
@@ -277,6 +281,7 @@ __global__ void __launch_bounds__((LT_CONS + 2) * 32, 1) k_lead_tma(const DevDes
       const int rb = split * (int)d->split_rows[k];
       const int re = min(rows, rb + (int)d->split_rows[k]);
       for (int r0 = rb; r0 < re; r0 += LT_ROWS, ++it) {
+        if ((int)(it % NKR) != kw) continue;
         const int s = it % ST;
         const uint32_t ph = (it / ST) & 1;
         if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, err)) { ok = false; break; }
@@ -390,7 +395,7 @@ static cudaError_t trailing_tma_impl(const LaunchCfg& c, const DevDesc* dd, cons
   cudaError_t e = cudaFuncSetAttribute(k_trailing_tma<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = total < c.num_sms ? total : c.num_sms;
-  k_trailing_tma<RP><<<grid, (TT_CONS + 2) * 32, smem, c.stream>>>(dd);
+  k_trailing_tma<RP><<<grid, (TT_CONS + NKR + 1) * 32, smem, c.stream>>>(dd);
   return cudaGetLastError();
 }
 
@@ -402,7 +407,7 @@ static cudaError_t lead_tma_impl(const LaunchCfg& c, const DevDesc* dd, const De
   cudaError_t e = cudaFuncSetAttribute(k_lead_tma<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = total < c.num_sms ? total : c.num_sms;
-  k_lead_tma<RP><<<grid, (LT_CONS + 2) * 32, smem, c.stream>>>(dd);
+  k_lead_tma<RP><<<grid, (LT_CONS + NKR + 1) * 32, smem, c.stream>>>(dd);
   return cudaGetLastError();
 }
 

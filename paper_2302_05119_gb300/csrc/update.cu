@@ -137,26 +137,32 @@ __device__ __forceinline__ double extrap_weight(double w_hat, int have_prev, dou
 constexpr int GRAM_TILE = 64;
 
 template <typename T>
-__device__ void block_gram(const T* __restrict__ U, int64_t I, int R, double* __restrict__ G, T* tile) {
+__device__ void block_gram(const T* __restrict__ U, int64_t I, int R, double* __restrict__ G, T* buf, int cap_rows) {
+  // buf holds cap_rows rows (a multiple of GRAM_TILE); rows are staged in as
+  // few round trips as the buffer allows, the arithmetic order is fixed.
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
   const int nt = blockDim.x * blockDim.y;
   const int RR = R * R;
   double acc[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) acc[q] = 0.0;
-  for (int64_t t0 = 0; t0 < I; t0 += GRAM_TILE) {
-    const int n = (int)min((int64_t)GRAM_TILE, I - t0);
+  for (int64_t s0 = 0; s0 < I; s0 += cap_rows) {
+    const int ns = (int)min((int64_t)cap_rows, I - s0);
     __syncthreads();
-    for (int e = tid; e < n * R; e += nt) tile[e] = U[t0 * R + e];
+    for (int e = tid; e < ns * R; e += nt) buf[e] = U[s0 * R + e];
     __syncthreads();
+    for (int t0 = 0; t0 < ns; t0 += GRAM_TILE) {
+      const int n = min(GRAM_TILE, ns - t0);
+      const T* tile = buf + t0 * R;
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int p = q * nt + tid;
-      if (p < RR) {
-        const int a = p / R, b = p % R;
-        T s = T(0);
-        for (int i = 0; i < n; ++i) s = fma(tile[i * R + a], tile[i * R + b], s);
-        acc[q] += (double)s;
+      for (int q = 0; q < 16; ++q) {
+        const int p = q * nt + tid;
+        if (p < RR) {
+          const int a = p / R, b = p % R;
+          T s = T(0);
+          for (int i = 0; i < n; ++i) s = fma(tile[i * R + a], tile[i * R + b], s);
+          acc[q] += (double)s;
+        }
       }
     }
   }
@@ -172,14 +178,15 @@ __device__ void block_gram(const T* __restrict__ U, int64_t I, int R, double* __
 // U1, which = 1: the LRA factors U~.  One CTA per (block, mode).
 template <typename T>
 __global__ void __launch_bounds__(256) k_gram(const DevDesc* __restrict__ d, int n_begin, int n_end, int which) {
-  __shared__ T tile[GRAM_TILE * CNCPD_RMAX];
+  constexpr int CAP = (32768 / (int)sizeof(T)) / CNCPD_RMAX / GRAM_TILE * GRAM_TILE;
+  __shared__ T tile[CAP * CNCPD_RMAX];
   const int nm = n_end - n_begin;
   const int k = blockIdx.x / nm;
   const int n = n_begin + blockIdx.x % nm;
   const T* U = reinterpret_cast<const T*>(which ? d->Ut[k][n] : d->U1[k][n]);
   const int R = which ? d->Rt[k] : d->R[k];
   double* G = which ? d->Gt[k][n] : d->G[k][n];
-  block_gram<T>(U, d->dims[k][n], R, G, tile);
+  block_gram<T>(U, d->dims[k][n], R, G, tile, CAP * CNCPD_RMAX / R / GRAM_TILE * GRAM_TILE);
 }
 
 cudaError_t launch_gram(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int n_begin, int n_end,
@@ -197,13 +204,13 @@ cudaError_t launch_gram(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) k_lipschitz(const DevDesc* __restrict__ d, int n, int use_core, int want_L,
-                                                   int prev) {
+                                                   int prev, int gram_rows) {
   const int k = blockIdx.x;
   const int R = d->R[k], N = d->N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (prev >= 0)  // Gram of the mode updated just before (Table II operation 1)
     block_gram<T>(reinterpret_cast<const T*>(d->U1[k][prev]), d->dims[k][prev], R, d->G[k][prev],
-                  reinterpret_cast<T*>(smem_raw));
+                  reinterpret_cast<T*>(smem_raw), gram_rows);
   LmaxScratch scr;
   scr.carve(smem_raw, R);
   double* Hs = scr.Hs;
@@ -227,12 +234,20 @@ __global__ void __launch_bounds__(256) k_lipschitz(const DevDesc* __restrict__ d
 
 cudaError_t launch_lipschitz(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int n, int use_core,
                              int prev) {
-  const size_t sm = std::max(lmax_smem_bytes(hd.Rmax), (size_t)GRAM_TILE * hd.Rmax * (fp64 ? 8 : 4));
+  // Gram staging: up to 32 KiB of rows (whole factor when it fits)
+  int64_t imax = 0;
+  for (int k = 0; k < hd.K; ++k)
+    for (int m = 0; m < hd.N; ++m) imax = std::max<int64_t>(imax, hd.dims[k][m]);
+  const int es = fp64 ? 8 : 4;
+  int64_t rows = std::min<int64_t>((imax + GRAM_TILE - 1) / GRAM_TILE * GRAM_TILE,
+                                   std::max<int64_t>(GRAM_TILE, (32768 / es / std::max(1, hd.Rmax)) / GRAM_TILE * GRAM_TILE));
+  const int gram_rows = (int)rows;
+  const size_t sm = std::max(lmax_smem_bytes(hd.Rmax), (size_t)gram_rows * hd.Rmax * es);
   cudaError_t e = fp64 ? allow_smem(k_lipschitz<double>, sm) : allow_smem(k_lipschitz<float>, sm);
   if (e != cudaSuccess) return e;
   const int nt = hd.Rmax <= 16 ? 128 : 256;
-  if (fp64) k_lipschitz<double><<<hd.K, nt, sm, c.stream>>>(dd, n, use_core, 1, prev);
-  else k_lipschitz<float><<<hd.K, nt, sm, c.stream>>>(dd, n, use_core, 1, prev);
+  if (fp64) k_lipschitz<double><<<hd.K, nt, sm, c.stream>>>(dd, n, use_core, 1, prev, gram_rows);
+  else k_lipschitz<float><<<hd.K, nt, sm, c.stream>>>(dd, n, use_core, 1, prev, gram_rows);
   return cudaGetLastError();
 }
 
@@ -276,15 +291,28 @@ __global__ void __launch_bounds__(128) k_update(const DevDesc* __restrict__ d, i
   const int Ln = d->L[n];
   const int nonneg = d->nonneg[n];
   DevScalars* sc = d->sc;
-  const double w_hat = use_w ? sc->w_hat : 0.0;
-  const int have_prev = sc->have_prev;
-  double LC = 0.0;
-  for (int k = 0; k < K; ++k) LC += sc->Lcur_u[n][k];
-  const T wC = (T)extrap_weight(w_hat, have_prev, sc->LCprev[n], LC, delta_w);
-  if (blockIdx.x == 0 && tid == 0) {
-    sc->LCcur[n] = LC;
-    sc->have_cur = 1;
+  __shared__ T wsh[CNCPD_KMAX + 1];
+  __shared__ double LCs;
+  {
+    // extrapolation weights (Eqs. eqextrawu and reading R3), one FP64
+    // evaluation per block instead of one per thread
+    const double w_hat = use_w ? sc->w_hat : 0.0;
+    const int have_prev = sc->have_prev;
+    if (tid < K) wsh[tid] = (T)extrap_weight(w_hat, have_prev, sc->Lprev_u[n][tid], sc->Lcur_u[n][tid], delta_w);
+    if (tid == K) {
+      double LC = 0.0;
+      for (int k = 0; k < K; ++k) LC += sc->Lcur_u[n][k];
+      LCs = LC;
+      wsh[K] = (T)extrap_weight(w_hat, have_prev, sc->LCprev[n], LC, delta_w);
+      if (blockIdx.x == 0) {
+        sc->LCcur[n] = LC;
+        sc->have_cur = 1;
+      }
+    }
+    __syncthreads();
   }
+  const double LC = LCs;
+  const T wC = wsh[K];
 
   T sumC = T(0), uhC = T(0), u1C = T(0);
   for (int k0 = 0; k0 < K; k0 += KC) {
@@ -306,8 +334,7 @@ __global__ void __launch_bounds__(128) k_update(const DevDesc* __restrict__ d, i
         u2[kk] = reinterpret_cast<const T*>(d->U2[k][n])[i * R + c];
         mv[kk] = reinterpret_cast<const T*>(d->M[k][n])[i * R + c];
       }
-      const T wk = (T)extrap_weight(w_hat, have_prev, sc->Lprev_u[n][k], sc->Lcur_u[n][k], delta_w);
-      const T w = (c < Ln) ? wC : wk;
+      const T w = (c < Ln) ? wC : wsh[k];
       uh[kk][y][c] = valid ? u1[kk] + w * (u1[kk] - u2[kk]) : T(0);
     }
     __syncthreads();
@@ -395,10 +422,12 @@ __global__ void __launch_bounds__(256) k_objective(const DevDesc* __restrict__ d
   __shared__ double red[256];
   __shared__ double cr[RP];
   __shared__ int is_last;
-  __shared__ T tile[GRAM_TILE * RP];
+  constexpr int CAP = (16384 / (int)sizeof(T)) / RP / GRAM_TILE * GRAM_TILE > 0
+                          ? (16384 / (int)sizeof(T)) / RP / GRAM_TILE * GRAM_TILE : GRAM_TILE;
+  __shared__ T tile[CAP * RP];
   const int R = d->R[k];
   if (commit)  // Gram of the last mode, just updated
-    block_gram<T>(reinterpret_cast<const T*>(d->U1[k][n]), d->dims[k][n], R, d->G[k][n], tile);
+    block_gram<T>(reinterpret_cast<const T*>(d->U1[k][n]), d->dims[k][n], R, d->G[k][n], tile, CAP);
   const int64_t I = d->dims[k][n];
   const T* M = reinterpret_cast<const T*>(d->M[k][n]);
   const T* U = reinterpret_cast<const T*>(d->U1[k][n]);
@@ -615,8 +644,8 @@ cudaError_t launch_grad(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd
     const size_t sm = lmax_smem_bytes(hd.Rmax);
     cudaError_t e = fp64 ? allow_smem(k_lipschitz<double>, sm) : allow_smem(k_lipschitz<float>, sm);
     if (e != cudaSuccess) return e;
-    if (fp64) k_lipschitz<double><<<hd.K, 256, sm, c.stream>>>(dd, n, use_core, 0, -1);
-    else k_lipschitz<float><<<hd.K, 256, sm, c.stream>>>(dd, n, use_core, 0, -1);
+    if (fp64) k_lipschitz<double><<<hd.K, 256, sm, c.stream>>>(dd, n, use_core, 0, -1, GRAM_TILE);
+    else k_lipschitz<float><<<hd.K, 256, sm, c.stream>>>(dd, n, use_core, 0, -1, GRAM_TILE);
   }
 #define GCASE(V)                                                                        \
   case V: {                                                                             \
