@@ -288,8 +288,13 @@ int enqueue_sweep(cncpd_ctx* c, int use_w) {
       if (n == 0) TRY(enqueue_trailing(c, c->dd, c->hd, c->RP));
       if (n == c->h) TRY(enqueue_lead(c, c->dd, c->hd, c->RP, c->d_red_prefix));
     }
-    TRY(enqueue_mode_m(c, n));
-    CU(launch_lipschitz(lc, c->dd, c->hd, c->fp64, n, core, n - 1));  // also the Gram of mode n-1
+    if (!c->lra && level2_is_pair(c->hd, n)) {
+      // level 2 of mode n and H / L of mode n (with the Gram of mode n-1) in one launch
+      CU(launch_mode_prep(lc, c->dd, c->hd, c->fp64, n, core, n - 1, 1));
+    } else {
+      TRY(enqueue_mode_m(c, n));
+      CU(launch_lipschitz(lc, c->dd, c->hd, c->fp64, n, core, n - 1));  // also the Gram of mode n-1
+    }
     CU(launch_update(lc, c->dd, c->hd, c->fp64, c->RP, n, use_w, dw, core));
     if (c->lra) CU(launch_cross_gram(lc, c->dd, c->hd, c->fp64, n, n + 1));
   }
@@ -439,8 +444,8 @@ long long kernels_per_replay(cncpd_ctx* c, int redo) {
   for (int m = 0; m < c->N; ++m) {
     const int gsize = (m < c->h) ? c->h : c->N - c->h;
     if (c->lra) n += 2;     // collapsed M, cross Gram
-    else if (gsize > 1) n += 1;
-    n += 2;                 // Lipschitz (with the previous mode's Gram), update
+    else if (gsize > 2) n += 1;  // generic level 2 (pairs share the Lipschitz launch)
+    n += 2;                 // Lipschitz (+ level 2, + the previous mode's Gram), update
   }
   n += c->lra ? 2 : 1;      // (last Gram +) objective
   n += redo ? (c->lra ? 3 : 2) : 1;

@@ -106,8 +106,8 @@ struct DevDesc {
 
 // -------------------------------------------------------------- helpers ----
 
-template <typename T> struct Acc;  // wide accumulator type for reductions
-template <> struct Acc<float> { typedef double type; };
+template <typename T> struct Acc;  // accumulator type of the level-2 partial sums
+template <> struct Acc<float> { typedef float type; };  // short in-kernel sums
 template <> struct Acc<double> { typedef double type; };
 
 template <int ST, typename T>
@@ -167,6 +167,11 @@ cudaError_t launch_trailing_tma(const LaunchCfg& c, const DevDesc* d_desc, const
 cudaError_t launch_lead_tma(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int RP);
 cudaError_t launch_level2(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int RP, int n);
 cudaError_t launch_gram(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int n_begin, int n_end, int which);
+// Level-2 of mode n (two-mode groups) and H / L of mode n in one launch
+// (CTAs 0..K-1: Lipschitz; the rest: level 2).  with_level2 = 0: Lipschitz only.
+cudaError_t launch_mode_prep(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int n,
+                             int use_core, int prev, int with_level2);
+bool level2_is_pair(const DevDesc& h_desc, int n);
 // prev >= 0: first form the Gram of mode `prev` (updated just before)
 cudaError_t launch_lipschitz(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int n, int use_core,
                              int prev);

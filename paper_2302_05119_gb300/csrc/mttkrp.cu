@@ -409,78 +409,6 @@ __global__ void __launch_bounds__(256) k_level2(const DevDesc* __restrict__ d, i
   }
 }
 
-// Two-mode groups (third- and fourth-order tensors).  With n first in its
-// group, P[i_n][b][r] is contiguous per i_n:  M[i_n, r] = sum_b P W[b, r].
-// With n last, P[a][i_n][r]:  M[i_n, r] = sum_a P W[a, r], and ni
-// consecutive i_n of one a are contiguous.  W is the other mode's factor
-// (read through the read-only cache); a CTA produces ni rows of M.
-template <typename T>
-__global__ void __launch_bounds__(256) k_level2_pair(const DevDesc* __restrict__ d, int n, int ni_max) {
-  typedef typename Acc<T>::type AT;
-  __shared__ AT red[256];
-  const int k = blockIdx.y;
-  const int N = d->N, h = d->h;
-  const int m0 = (n < h) ? 0 : h;
-  const int other = (n == m0) ? n + 1 : m0;   // the group's other mode
-  const bool first = (n == m0);
-  const int In = (int)d->dims[k][n];
-  const int Io = (int)d->dims[k][other];
-  const int R = d->R[k];
-  const int i0 = blockIdx.x * ni_max;
-  if (i0 >= In) return;
-  const int ni = min(ni_max, In - i0);
-  const T* P = reinterpret_cast<const T*>((n < h) ? d->Pl[k] : d->Pt[k]);
-  const T* W = reinterpret_cast<const T*>(d->U1[k][other]);
-  T* M = reinterpret_cast<T*>(d->M[k][n]);
-  const int t = threadIdx.x;
-  if (first) {
-    // ni contiguous slabs of Io*R; thread keeps r fixed, all slabs at once
-    const int BR = Io * R;
-    const int stride = (blockDim.x / R) * R;
-    const int r = t % R;
-    AT acc[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = 0;
-    if (t < stride) {
-#pragma unroll 2
-      for (int e = t; e < BR; e += stride) {
-        const T w = __ldg(W + e);
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if (q < ni) acc[q] += (AT)(P[(int64_t)(i0 + q) * BR + e] * w);
-      }
-    }
-    for (int q = 0; q < ni; ++q) {
-      red[t] = acc[q];
-      __syncthreads();
-      if (t < R) {
-        AT s = 0;
-        for (int u = t; u < stride; u += R) s += red[u];
-        M[(int64_t)(i0 + q) * R + t] = (T)s;
-      }
-      __syncthreads();
-    }
-  } else {
-    // segment j in [0, ni*R) of row a starts at P[(a*In + i0)*R]; slices of a
-    const int JR = ni * R;
-    const int nsl = max(1, (int)blockDim.x / JR);
-    const int j = t % JR, sl = t / JR;
-    AT acc = 0;
-    if (sl < nsl && t < nsl * JR) {
-      const int r = j % R;
-#pragma unroll 8
-      for (int a = sl; a < Io; a += nsl) acc += (AT)(P[((int64_t)a * In + i0) * R + j] * __ldg(W + a * R + r));
-    }
-    red[t] = acc;
-    __syncthreads();
-    if (t < JR) {
-      AT s = 0;
-      for (int u = 0; u < nsl; ++u) s += red[u * JR + t];
-      M[(int64_t)i0 * R + t] = (T)s;
-    }
-  }
-}
-
 // ------------------------------------------------------------- launchers ----
 
 template <int ST, typename T, int RP>
@@ -610,16 +538,8 @@ cudaError_t launch_level2(const LaunchCfg& c, const DevDesc* dd, const DevDesc& 
   const int gsize = (n < hd.h) ? hd.h : hd.N - hd.h;
   int64_t imax = 0, omax = 0;
   for (int k = 0; k < hd.K; ++k) imax = hd.dims[k][n] > imax ? hd.dims[k][n] : imax;
-  if (gsize == 2) {
-    (void)omax;
-    // rows per CTA: small enough for ~4 CTAs per SM over all blocks, ni*R <= 256
-    int ni = std::max(1, std::min(8, 256 / std::max(1, hd.Rmax)));
-    while (ni > 1 && ((imax + ni - 1) / ni) * hd.K < 4LL * c.num_sms) ni /= 2;
-    dim3 grid((unsigned)((imax + ni - 1) / ni), hd.K);
-    if (fp64) k_level2_pair<double><<<grid, 256, 0, c.stream>>>(dd, n, ni);
-    else k_level2_pair<float><<<grid, 256, 0, c.stream>>>(dd, n, ni);
-    return cudaGetLastError();
-  }
+  (void)omax;
+  if (gsize == 2) return launch_mode_prep(c, dd, hd, fp64, n, 0, -1, 2);
   dim3 grid((unsigned)imax, hd.K);
   if (fp64) k_level2<double><<<grid, 256, 0, c.stream>>>(dd, n);
   else k_level2<float><<<grid, 256, 0, c.stream>>>(dd, n);

@@ -48,9 +48,10 @@ __device__ double lmax_psd(const double* Hs, int R, LmaxScratch* s) {
   if (!isfinite(tr)) return tr;
   if (!(tr > 0.0)) return 0.0;
   const int RR = R * R;
-  for (int e = tid; e < RR; e += nt) s->A[e] = (float)(Hs[e] / tr);
+  const double itr = 1.0 / tr;
+  for (int e = tid; e < RR; e += nt) s->A[e] = (float)(Hs[e] * itr);
   __syncthreads();
-  for (int it = 0; it < 64; ++it) {
+  for (int it = 0; it < 32; ++it) {
     for (int e = tid; e < RR; e += nt) {
       const int i = e / R, j = e % R;
       float acc = 0.f;
@@ -68,7 +69,11 @@ __device__ double lmax_psd(const double* Hs, int R, LmaxScratch* s) {
         s->A[e] = nv;
       }
     }
-    // CTA max of dmax
+    if ((it & 3) != 3 && (trb > 0.f)) {
+      __syncthreads();
+      continue;
+    }
+    // every fourth squaring: CTA max of the last change
     for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
     if ((tid & 31) == 0) s->red[tid >> 5] = dmax;
     __syncthreads();
@@ -203,11 +208,9 @@ cudaError_t launch_gram(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd
 // operation 4) and L_u^(n,k) = ||H||_2 (Eq. eqLipsLu).  One CTA per block.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_lipschitz(const DevDesc* __restrict__ d, int n, int use_core, int want_L,
-                                                   int prev, int gram_rows) {
-  const int k = blockIdx.x;
+__device__ void lipschitz_body(const DevDesc* __restrict__ d, int k, int n, int use_core, int want_L, int prev,
+                               int gram_rows, unsigned char* smem_raw) {
   const int R = d->R[k], N = d->N;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   if (prev >= 0)  // Gram of the mode updated just before (Table II operation 1)
     block_gram<T>(reinterpret_cast<const T*>(d->U1[k][prev]), d->dims[k][prev], R, d->G[k][prev],
                   reinterpret_cast<T*>(smem_raw), gram_rows);
@@ -232,8 +235,95 @@ __global__ void __launch_bounds__(256) k_lipschitz(const DevDesc* __restrict__ d
   }
 }
 
-cudaError_t launch_lipschitz(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int n, int use_core,
-                             int prev) {
+template <typename T>
+__global__ void __launch_bounds__(256) k_lipschitz(const DevDesc* __restrict__ d, int n, int use_core, int want_L,
+                                                   int prev, int gram_rows) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  lipschitz_body<T>(d, blockIdx.x, n, use_core, want_L, prev, gram_rows, smem_raw);
+}
+
+// Two-mode groups (third- and fourth-order tensors).  With n first in its
+// group, P[i_n][b][r] is contiguous per i_n:  M[i_n, r] = sum_b P W[b, r].
+// With n last, P[a][i_n][r]:  M[i_n, r] = sum_a P W[a, r], and ni
+// consecutive i_n of one a are contiguous.  W is the other mode's factor
+// (read through the read-only cache); a CTA produces ni rows of M.
+template <typename T>
+__device__ void level2_pair_body(const DevDesc* __restrict__ d, int k, int bx, int n, int ni_max) {
+  __shared__ T red[256];
+  const int N = d->N, h = d->h;
+  const int m0 = (n < h) ? 0 : h;
+  const int other = (n == m0) ? n + 1 : m0;   // the group's other mode
+  const bool first = (n == m0);
+  const int In = (int)d->dims[k][n];
+  const int Io = (int)d->dims[k][other];
+  const int R = d->R[k];
+  const int i0 = bx * ni_max;
+  if (i0 >= In) return;
+  const int ni = min(ni_max, In - i0);
+  const T* P = reinterpret_cast<const T*>((n < h) ? d->Pl[k] : d->Pt[k]);
+  const T* W = reinterpret_cast<const T*>(d->U1[k][other]);
+  T* M = reinterpret_cast<T*>(d->M[k][n]);
+  const int t = threadIdx.x;
+  if (first) {
+    const int BR = Io * R;
+    const int stride = (blockDim.x / R) * R;
+    T acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = T(0);
+    if (t < stride) {
+#pragma unroll 2
+      for (int e = t; e < BR; e += stride) {
+        const T w = __ldg(W + e);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (q < ni) acc[q] = fma(P[(int64_t)(i0 + q) * BR + e], w, acc[q]);
+      }
+    }
+    for (int q = 0; q < ni; ++q) {
+      red[t] = acc[q];
+      __syncthreads();
+      if (t < R) {
+        T s = T(0);
+        for (int u = t; u < stride; u += R) s += red[u];
+        M[(int64_t)(i0 + q) * R + t] = s;
+      }
+      __syncthreads();
+    }
+  } else {
+    const int JR = ni * R;
+    const int nsl = max(1, (int)blockDim.x / JR);
+    const int j = t % JR, sl = t / JR;
+    T acc = T(0);
+    if (sl < nsl && t < nsl * JR) {
+      const int r = j % R;
+#pragma unroll 8
+      for (int a = sl; a < Io; a += nsl) acc = fma(P[((int64_t)a * In + i0) * R + j], __ldg(W + a * R + r), acc);
+    }
+    red[t] = acc;
+    __syncthreads();
+    if (t < JR) {
+      T s = T(0);
+      for (int u = 0; u < nsl; ++u) s += red[u * JR + t];
+      M[(int64_t)i0 * R + t] = s;
+    }
+  }
+}
+
+// CTAs [0, nlip): H and L of mode n for block blockIdx.x; the rest: level 2
+// of mode n, nx CTAs per block.
+template <typename T>
+__global__ void __launch_bounds__(256) k_mode_prep(const DevDesc* __restrict__ d, int n, int use_core, int prev,
+                                                   int gram_rows, int nlip, int nx, int ni) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if ((int)blockIdx.x < nlip) {
+    lipschitz_body<T>(d, blockIdx.x, n, use_core, 1, prev, gram_rows, smem_raw);
+  } else {
+    const int b = blockIdx.x - nlip;
+    level2_pair_body<T>(d, b / nx, b % nx, n, ni);
+  }
+}
+
+static void lipschitz_smem(const DevDesc& hd, int fp64, int* gram_rows, size_t* sm) {
   // Gram staging: up to 32 KiB of rows (whole factor when it fits)
   int64_t imax = 0;
   for (int k = 0; k < hd.K; ++k)
@@ -241,8 +331,45 @@ cudaError_t launch_lipschitz(const LaunchCfg& c, const DevDesc* dd, const DevDes
   const int es = fp64 ? 8 : 4;
   int64_t rows = std::min<int64_t>((imax + GRAM_TILE - 1) / GRAM_TILE * GRAM_TILE,
                                    std::max<int64_t>(GRAM_TILE, (32768 / es / std::max(1, hd.Rmax)) / GRAM_TILE * GRAM_TILE));
-  const int gram_rows = (int)rows;
-  const size_t sm = std::max(lmax_smem_bytes(hd.Rmax), (size_t)gram_rows * hd.Rmax * es);
+  *gram_rows = (int)rows;
+  *sm = std::max(lmax_smem_bytes(hd.Rmax), (size_t)rows * hd.Rmax * es);
+}
+
+bool level2_is_pair(const DevDesc& hd, int n) {
+  const int gsize = (n < hd.h) ? hd.h : hd.N - hd.h;
+  return gsize == 2;
+}
+
+cudaError_t launch_mode_prep(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int n, int use_core,
+                             int prev, int with_level2) {
+  // with_level2: 0 = Lipschitz only, 1 = Lipschitz + level 2, 2 = level 2 only
+  int gram_rows = GRAM_TILE;
+  size_t sm = 0;
+  const int nlip = (with_level2 == 2) ? 0 : hd.K;
+  if (nlip) lipschitz_smem(hd, fp64, &gram_rows, &sm);
+  int nx = 0, ni = 1;
+  if (with_level2) {
+    int64_t imax = 0;
+    for (int k = 0; k < hd.K; ++k) imax = std::max<int64_t>(imax, hd.dims[k][n]);
+    // rows per CTA: small enough for ~4 CTAs per SM over all blocks, ni*R <= 256
+    ni = std::max(1, std::min(8, 256 / std::max(1, hd.Rmax)));
+    while (ni > 1 && ((imax + ni - 1) / ni) * hd.K < 4LL * c.num_sms) ni /= 2;
+    nx = (int)((imax + ni - 1) / ni);
+  }
+  const int grid = nlip + nx * hd.K;
+  if (grid == 0) return cudaSuccess;
+  cudaError_t e = fp64 ? allow_smem(k_mode_prep<double>, sm) : allow_smem(k_mode_prep<float>, sm);
+  if (e != cudaSuccess) return e;
+  if (fp64) k_mode_prep<double><<<grid, 256, sm, c.stream>>>(dd, n, use_core, prev, gram_rows, nlip, nx, ni);
+  else k_mode_prep<float><<<grid, 256, sm, c.stream>>>(dd, n, use_core, prev, gram_rows, nlip, nx, ni);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lipschitz(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int n, int use_core,
+                             int prev) {
+  int gram_rows;
+  size_t sm;
+  lipschitz_smem(hd, fp64, &gram_rows, &sm);
   cudaError_t e = fp64 ? allow_smem(k_lipschitz<double>, sm) : allow_smem(k_lipschitz<float>, sm);
   if (e != cudaSuccess) return e;
   const int nt = hd.Rmax <= 16 ? 128 : 256;
