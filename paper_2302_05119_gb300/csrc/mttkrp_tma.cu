@@ -142,9 +142,10 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
     const int J = (int)d->trail_cols[k];
     const int R = d->R[k];
     const int nch = (J + TT_BC - 1) / TT_BC;
-    float acc0[RP], acc1[RP];
+    constexpr int RH = RP / 2;
+    uint64_t acc0[RH], acc1[RH];  // pairs (r, r+1) of the two rows' sums
 #pragma unroll
-    for (int r = 0; r < RP; ++r) acc0[r] = acc1[r] = 0.f;
+    for (int p = 0; p < RH; ++p) acc0[p] = acc1[p] = 0ull;
     for (int c = 0; c < nch; ++c, ++it) {
       const int s = it % TT_STAGES;
       const uint32_t ph = (it / TT_STAGES) & 1;
@@ -160,36 +161,47 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
         const float bv[4] = {xb.x, xb.y, xb.z, xb.w};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const float* wr = wt + (4 * q + e) * S::WST;
+          const uint64_t a2 = pack2(av[e], av[e]);
+          const uint64_t b2 = pack2(bv[e], bv[e]);
+          const uint64_t* wr = reinterpret_cast<const uint64_t*>(wt + (4 * q + e) * S::WST);
 #pragma unroll
-          for (int r = 0; r + 4 <= RP; r += 4) {
-            const float4 wv = *reinterpret_cast<const float4*>(wr + r);
-            ffma2(acc0[r], acc0[r + 1], av[e], av[e], wv.x, wv.y);
-            ffma2(acc0[r + 2], acc0[r + 3], av[e], av[e], wv.z, wv.w);
-            ffma2(acc1[r], acc1[r + 1], bv[e], bv[e], wv.x, wv.y);
-            ffma2(acc1[r + 2], acc1[r + 3], bv[e], bv[e], wv.z, wv.w);
+          for (int p = 0; p + 2 <= RH; p += 2) {
+            const ulonglong2 w = *reinterpret_cast<const ulonglong2*>(wr + p);
+            ffma2x(acc0[p], a2, w.x);
+            ffma2x(acc0[p + 1], a2, w.y);
+            ffma2x(acc1[p], b2, w.x);
+            ffma2x(acc1[p + 1], b2, w.y);
           }
-          if constexpr (RP % 4 == 2) {
-            const float2 wv = *reinterpret_cast<const float2*>(wr + RP - 2);
-            ffma2(acc0[RP - 2], acc0[RP - 1], av[e], av[e], wv.x, wv.y);
-            ffma2(acc1[RP - 2], acc1[RP - 1], bv[e], bv[e], wv.x, wv.y);
+          if constexpr (RH % 2 == 1) {
+            const uint64_t w = wr[RH - 1];
+            ffma2x(acc0[RH - 1], a2, w);
+            ffma2x(acc1[RH - 1], b2, w);
           }
         }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
     }
+    float acc0f[RP], acc1f[RP];
+#pragma unroll
+    for (int p = 0; p < RH; ++p) {
+      const float2 u = unpack2(acc0[p]), v = unpack2(acc1[p]);
+      acc0f[2 * p] = u.x;
+      acc0f[2 * p + 1] = u.y;
+      acc1f[2 * p] = v.x;
+      acc1f[2 * p + 1] = v.y;
+    }
     const int64_t rows = d->lead_rows[k];
     float* P = reinterpret_cast<float*>(d->Pl[k]);
     if (row0 + ra < rows) {
 #pragma unroll
       for (int r = 0; r < RP; ++r)
-        if (r < R) P[(int64_t)(row0 + ra) * R + r] = acc0[r];
+        if (r < R) P[(int64_t)(row0 + ra) * R + r] = acc0f[r];
     }
     if (row0 + rb < rows) {
 #pragma unroll
       for (int r = 0; r < RP; ++r)
-        if (r < R) P[(int64_t)(row0 + rb) * R + r] = acc1[r];
+        if (r < R) P[(int64_t)(row0 + rb) * R + r] = acc1f[r];
     }
   }
 }
@@ -328,11 +340,11 @@ __global__ void __launch_bounds__((LT_CONS + NKR + 1) * 32, 1) k_lead_tma(const 
     const int R = d->R[k];
     const int rb = split * (int)d->split_rows[k];
     const int re = min(rows, rb + (int)d->split_rows[k]);
-    float acc[4][RP];
+    uint64_t acc2[2][RP];  // [column pair][r]: {sum of column 2c, sum of column 2c+1}
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
+    for (int c = 0; c < 2; ++c)
 #pragma unroll
-      for (int r = 0; r < RP; ++r) acc[c][r] = 0.f;
+      for (int r = 0; r < RP; ++r) acc2[c][r] = 0ull;
     for (int r0 = rb; r0 < re; r0 += LT_ROWS, ++it) {
       const int s = it % ST;
       const uint32_t ph = (it / ST) & 1;
@@ -341,19 +353,28 @@ __global__ void __launch_bounds__((LT_CONS + NKR + 1) * 32, 1) k_lead_tma(const 
       const float2* wt = wd + s * (S::W_BYTES / 8);
 #pragma unroll 4
       for (int i = warp; i < LT_ROWS; i += LT_CONS) {
-        const float4 x = *reinterpret_cast<const float4*>(xt + i * (LT_COLS * 4) + lane * 16);
-        const float4* wr = reinterpret_cast<const float4*>(wt + i * RP);
+        const ulonglong2 x = *reinterpret_cast<const ulonglong2*>(xt + i * (LT_COLS * 4) + lane * 16);
+        const ulonglong2* wr = reinterpret_cast<const ulonglong2*>(wt + i * RP);
 #pragma unroll
         for (int r = 0; r < RP; r += 2) {
-          const float4 wv = wr[r / 2];  // {w_r, w_r, w_r+1, w_r+1}
-          ffma2(acc[0][r], acc[1][r], x.x, x.y, wv.x, wv.y);
-          ffma2(acc[2][r], acc[3][r], x.z, x.w, wv.x, wv.y);
-          ffma2(acc[0][r + 1], acc[1][r + 1], x.x, x.y, wv.z, wv.w);
-          ffma2(acc[2][r + 1], acc[3][r + 1], x.z, x.w, wv.z, wv.w);
+          const ulonglong2 w = wr[r / 2];  // {w_r, w_r}, {w_r+1, w_r+1}
+          ffma2x(acc2[0][r], x.x, w.x);
+          ffma2x(acc2[1][r], x.y, w.x);
+          ffma2x(acc2[0][r + 1], x.x, w.y);
+          ffma2x(acc2[1][r + 1], x.y, w.y);
         }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
+    }
+    float acc[4][RP];
+#pragma unroll
+    for (int r = 0; r < RP; ++r) {
+      const float2 u = unpack2(acc2[0][r]), v = unpack2(acc2[1][r]);
+      acc[0][r] = u.x;
+      acc[1][r] = u.y;
+      acc[2][r] = v.x;
+      acc[3][r] = v.y;
     }
     // fixed-order reduction of the four consumer warps: ((w1 + w2) + w3) + w0
     for (int src = 1; src < LT_CONS; ++src) {

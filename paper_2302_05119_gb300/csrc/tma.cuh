@@ -54,9 +54,9 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_timer_ns();
-  for (;;) {
+  for (uint32_t n = 1;; ++n) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (global_timer_ns() - t0 > 2000000000ull || *((volatile int*)err) != 0) {
+    if ((n & 31) == 0 && (global_timer_ns() - t0 > 2000000000ull || *((volatile int*)err) != 0)) {
       atomicExch(err, 1);
       return false;
     }
@@ -68,8 +68,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* er
 __device__ __forceinline__ void mbar_wait_drain(uint32_t bar, uint32_t parity) {
   if (mbar_try_wait(bar, parity)) return;
   const uint64_t t0 = global_timer_ns();
-  while (!mbar_try_wait(bar, parity))
-    if (global_timer_ns() - t0 > 2000000000ull) return;
+  for (uint32_t n = 1; !mbar_try_wait(bar, parity); ++n)
+    if ((n & 31) == 0 && global_timer_ns() - t0 > 2000000000ull) return;
 }
 
 // 2-D tiled TMA load of the box at (c0 = innermost coordinate, c1) into
@@ -96,6 +96,22 @@ __device__ __forceinline__ void ffma2(float& d0, float& d1, float a0, float a1, 
       "mov.b64 {%0, %1}, rd;\n\t}"
       : "+f"(d0), "+f"(d1)
       : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+
+// Packed pairs of FP32 values held in one 64-bit register.
+__device__ __forceinline__ uint64_t pack2(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 unpack2(uint64_t v) {
+  float2 f;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(f.x), "=f"(f.y) : "l"(v));
+  return f;
+}
+// acc = a * b + acc on both FP32 lanes (round to nearest).
+__device__ __forceinline__ void ffma2x(uint64_t& acc, uint64_t a, uint64_t b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
 }
 
 // Named barrier among `count` threads (id 1..15; 0 is __syncthreads).
