@@ -31,8 +31,8 @@ __device__ __forceinline__ void decode32_t(const DevDesc* d, int k, int m0, int 
 // ---------------------------------------------------------------------------
 constexpr int TT_ROWS = 256;
 constexpr int TT_BC = 32;
-constexpr int TT_STAGES = 4;
 constexpr int TT_CONS = 4;
+constexpr size_t SMEM_LIMIT = 232448;  // 227 KiB of dynamic shared memory per CTA
 constexpr int NKR = 3;  // Khatri-Rao warps, stage i handled by warp i mod NKR
 
 template <int RP>
@@ -40,22 +40,26 @@ struct TrailTma {
   static constexpr int WST = (RP + 3) / 4 * 4;
   static constexpr uint32_t X_BYTES = TT_ROWS * TT_BC * 4;
   static constexpr uint32_t W_BYTES = TT_BC * WST * 4;
-  static constexpr size_t SMEM = 1024 + TT_STAGES * (size_t)(X_BYTES + W_BYTES) + 2 * TT_STAGES * 8;
+  // as many stages as fit (at most 6): bytes in flight hide the memory latency
+  static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 128) / (X_BYTES + W_BYTES));
+  static constexpr int STAGES = STAGES_FIT > 6 ? 6 : STAGES_FIT;
+  static constexpr size_t SMEM = 1024 + STAGES * (size_t)(X_BYTES + W_BYTES) + 2 * STAGES * 8;
 };
 
 template <int RP>
 __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(const DevDesc* __restrict__ d) {
   using S = TrailTma<RP>;
+  constexpr int TST = S::STAGES;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* xs = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  float* ws = reinterpret_cast<float*>(xs + TT_STAGES * S::X_BYTES);
-  uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(ws) + TT_STAGES * S::W_BYTES);
-  uint64_t* empty = full + TT_STAGES;
+  float* ws = reinterpret_cast<float*>(xs + TST * S::X_BYTES);
+  uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(ws) + TST * S::W_BYTES);
+  uint64_t* empty = full + TST;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int* err = &d->sc->timeout;
   const CUtensorMap* maps = d->tmap_trail;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < TT_STAGES; ++s) {
+    for (int s = 0; s < TST; ++s) {
       mbar_init(smem_u32(&full[s]), 2);  // TMA issuer (with the byte count) + Khatri-Rao warp
       mbar_init(smem_u32(&empty[s]), TT_CONS);
     }
@@ -78,16 +82,16 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
       const int nch = (J + TT_BC - 1) / TT_BC;
       if (g == blockIdx.x) prefetch_tmap(&maps[k]);
       for (int c = 0; c < nch; ++c, ++it) {
-        const int s = it % TT_STAGES;
-        const uint32_t ph = (it / TT_STAGES) & 1;
+        const int s = it % TST;
+        const uint32_t ph = (it / TST) & 1;
         if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, err)) { ok = false; break; }
         mbar_arrive_expect_tx(smem_u32(&full[s]), S::X_BYTES);
         tma_load_2d(smem_u32(xs + s * S::X_BYTES), &maps[k], smem_u32(&full[s]), c * TT_BC, row0);
       }
     }
     // copies still in flight land before the CTA leaves
-    for (uint32_t i = it > TT_STAGES ? it - TT_STAGES : 0; i < it; ++i)
-      mbar_wait_drain(smem_u32(&full[i % TT_STAGES]), (i / TT_STAGES) & 1);
+    for (uint32_t i = it > TST ? it - TST : 0; i < it; ++i)
+      mbar_wait_drain(smem_u32(&full[i % TST]), (i / TST) & 1);
     return;
   }
 
@@ -104,8 +108,8 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
       const int nch = (J + TT_BC - 1) / TT_BC;
       for (int c = 0; c < nch; ++c, ++it) {
         if ((int)(it % NKR) != kw) continue;
-        const int s = it % TT_STAGES;
-        const uint32_t ph = (it / TT_STAGES) & 1;
+        const int s = it % TST;
+        const uint32_t ph = (it / TST) & 1;
         if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, err)) { ok = false; break; }
         // Khatri-Rao rows of the trailing factors for the 32 columns of this stage
         const int j = c * TT_BC + lane;
@@ -147,8 +151,8 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
 #pragma unroll
     for (int p = 0; p < RH; ++p) acc0[p] = acc1[p] = 0ull;
     for (int c = 0; c < nch; ++c, ++it) {
-      const int s = it % TT_STAGES;
-      const uint32_t ph = (it / TT_STAGES) & 1;
+      const int s = it % TST;
+      const uint32_t ph = (it / TST) & 1;
       if (!mbar_wait(smem_u32(&full[s]), ph, err)) return;
       const unsigned char* xt = xs + s * S::X_BYTES;
       const float* wt = ws + s * (S::W_BYTES / 4);
@@ -219,10 +223,11 @@ constexpr int LT_CONS = 4;
 
 template <int RP>
 struct LeadTma {
-  static constexpr int STAGES = RP <= 32 ? 4 : 2;
   static constexpr uint32_t X_BYTES = LT_ROWS * LT_COLS * 4;
   static constexpr uint32_t W_BYTES = LT_ROWS * RP * 8;
   static constexpr uint32_t RED_BYTES = LT_COLS * RP * 4;
+  static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 128 - RED_BYTES) / (X_BYTES + W_BYTES));
+  static constexpr int STAGES = STAGES_FIT > 6 ? 6 : STAGES_FIT;
   static constexpr size_t SMEM = 1024 + STAGES * (size_t)(X_BYTES + W_BYTES) + RED_BYTES + 2 * STAGES * 8;
 };
 
