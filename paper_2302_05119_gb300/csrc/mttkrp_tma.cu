@@ -5,7 +5,7 @@
 // cp.async.bulk.tensor copies of X tiles into a ring of shared-memory stages
 // guarded by mbarriers (arrive.expect_tx), three warps take turns writing the
 // matching Khatri-Rao rows of the factors next to them (a stage is full after
-// both arrivals and all bytes), and four consumer warps accumulate with
+// both arrivals and all bytes), and eight consumer warps accumulate with
 // packed fma.rn.f32x2.  CTAs are persistent (one per SM) and walk a static list of
 // work units.  Every mbarrier wait is bounded in time: on expiry the kernel
 // sets the error word, stops issuing copies, waits for the copies already in
@@ -27,11 +27,14 @@ __device__ __forceinline__ void decode32_t(const DevDesc* d, int k, int m0, int 
 // ---------------------------------------------------------------------------
 // Trailing contraction Pl[row, r] = sum_col X[row, col] W_t[col, r].
 // Tile = 256 rows; stage = 256 rows x 32 columns (32 KiB, 128-byte swizzle).
-// Consumer warp w owns rows 64w + lane and 64w + 32 + lane of the tile.
+// Consumer warp w owns rows 64(w % 4) + lane and 64(w % 4) + 32 + lane of the
+// tile and columns 16(w / 4) .. 16(w / 4) + 15 of every stage; the two
+// column halves are added at the end of the tile.  Two consumer warps per
+// scheduler hide the shared-memory latency of one another.
 // ---------------------------------------------------------------------------
 constexpr int TT_ROWS = 256;
 constexpr int TT_BC = 32;
-constexpr int TT_CONS = 4;
+constexpr int TT_CONS = 8;  // 4 row groups x 2 column halves
 constexpr size_t SMEM_LIMIT = 232448;  // 227 KiB of dynamic shared memory per CTA
 constexpr int NKR = 3;  // Khatri-Rao warps, stage i handled by warp i mod NKR
 
@@ -40,10 +43,11 @@ struct TrailTma {
   static constexpr int WST = (RP + 3) / 4 * 4;
   static constexpr uint32_t X_BYTES = TT_ROWS * TT_BC * 4;
   static constexpr uint32_t W_BYTES = TT_BC * WST * 4;
+  static constexpr uint32_t RED_BYTES = TT_ROWS * RP * 4;  // column-half partial sums
   // as many stages as fit (at most 6): bytes in flight hide the memory latency
-  static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 128) / (X_BYTES + W_BYTES));
+  static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 128 - RED_BYTES) / (X_BYTES + W_BYTES));
   static constexpr int STAGES = STAGES_FIT > 6 ? 6 : STAGES_FIT;
-  static constexpr size_t SMEM = 1024 + STAGES * (size_t)(X_BYTES + W_BYTES) + 2 * STAGES * 8;
+  static constexpr size_t SMEM = 1024 + STAGES * (size_t)(X_BYTES + W_BYTES) + RED_BYTES + 2 * STAGES * 8;
 };
 
 template <int RP>
@@ -53,7 +57,8 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
   extern __shared__ unsigned char smem_raw[];
   unsigned char* xs = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   float* ws = reinterpret_cast<float*>(xs + TST * S::X_BYTES);
-  uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(ws) + TST * S::W_BYTES);
+  float* red = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(ws) + TST * S::W_BYTES);
+  uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(red) + S::RED_BYTES);
   uint64_t* empty = full + TST;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int* err = &d->sc->timeout;
@@ -138,7 +143,8 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
 
   // -------------------------------------------------------------- consumers
   uint32_t it = 0;
-  const int ra = warp * 64 + lane, rb = ra + 32;
+  const int rg = warp & 3, ch = warp >> 2;
+  const int ra = rg * 64 + lane, rb = ra + 32;
   for (int g = blockIdx.x; g < total; g += gridDim.x) {
     int k = 0;
     while (d->lt_prefix[k + 1] <= g) ++k;
@@ -153,11 +159,11 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
     for (int c = 0; c < nch; ++c, ++it) {
       const int s = it % TST;
       const uint32_t ph = (it / TST) & 1;
-      if (!mbar_wait(smem_u32(&full[s]), ph, err)) return;
+      if (!mbar_wait(smem_u32(&full[s]), ph, err)) continue;  // error recorded; keep the barrier schedule
       const unsigned char* xt = xs + s * S::X_BYTES;
       const float* wt = ws + s * (S::W_BYTES / 4);
 #pragma unroll 2
-      for (int q = 0; q < 8; ++q) {
+      for (int q = 4 * ch; q < 4 * ch + 4; ++q) {
         // 128-byte swizzle: 16-byte chunk q of row r sits at chunk q ^ (r & 7)
         const float4 xa = *reinterpret_cast<const float4*>(xt + ra * 128 + ((q ^ (ra & 7)) << 4));
         const float4 xb = *reinterpret_cast<const float4*>(xt + rb * 128 + ((q ^ (rb & 7)) << 4));
@@ -195,6 +201,22 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
       acc1f[2 * p] = v.x;
       acc1f[2 * p + 1] = v.y;
     }
+    // second column half hands its sums to the first (fixed order: half 0 + half 1)
+    named_bar(1, TT_CONS * 32);
+    if (ch == 1) {
+#pragma unroll
+      for (int r = 0; r < RP; ++r) {
+        red[ra * RP + r] = acc0f[r];
+        red[rb * RP + r] = acc1f[r];
+      }
+    }
+    named_bar(1, TT_CONS * 32);
+    if (ch == 1) continue;
+#pragma unroll
+    for (int r = 0; r < RP; ++r) {
+      acc0f[r] += red[ra * RP + r];
+      acc1f[r] += red[rb * RP + r];
+    }
     const int64_t rows = d->lead_rows[k];
     float* P = reinterpret_cast<float*>(d->Pl[k]);
     if (row0 + ra < rows) {
@@ -213,13 +235,13 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
 // ---------------------------------------------------------------------------
 // Lead contraction (split over rows) Pt[col, r] = sum_row X[row, col] W_l[row, r].
 // Unit = 128 columns x one row split; stage = 64 rows x 128 columns (32 KiB).
-// Consumer warp w takes rows w, w + 4, ... of a stage; lane l owns columns
+// Consumer warp w takes rows w, w + 8, ... of a stage; lane l owns columns
 // 4l .. 4l + 3 (two packed column pairs).  W_l is stored with each value
 // duplicated ({w, w}) so the packed FMA takes it as one operand pair.
 // ---------------------------------------------------------------------------
 constexpr int LT_ROWS = 64;
 constexpr int LT_COLS = 128;
-constexpr int LT_CONS = 4;
+constexpr int LT_CONS = 8;
 
 template <int RP>
 struct LeadTma {
@@ -381,7 +403,7 @@ __global__ void __launch_bounds__((LT_CONS + NKR + 1) * 32, 1) k_lead_tma(const 
       acc[2][r] = v.x;
       acc[3][r] = v.y;
     }
-    // fixed-order reduction of the four consumer warps: ((w1 + w2) + w3) + w0
+    // fixed-order reduction of the consumer warps: (((w1 + w2) + w3) + ...) + w0
     for (int src = 1; src < LT_CONS; ++src) {
       named_bar(1, LT_CONS * 32);
       if (warp == src) {
