@@ -164,7 +164,7 @@ int dalloc(cncpd_ctx* c, void** p, size_t bytes) {
 // Split-K plan of the lead-mode contraction for rank bucket RP.
 void plan_lead_splits(cncpd_ctx* c, DevDesc& d, int RP, int fp64, size_t* partial_elems) {
   const int cpt = lead_cpt(fp64, RP);
-  const int tile_cols = d.use_tma ? 128 : 64 * cpt;
+  const int tile_cols = d.use_tma ? 256 : 64 * cpt;
   int64_t tot_rows = 0;
   for (int k = 0; k < d.K; ++k) tot_rows += d.lead_rows[k];
   // aim for ~2 CTAs (of 256 threads) per SM in total, at least 64 rows per split
@@ -178,7 +178,7 @@ void plan_lead_splits(cncpd_ctx* c, DevDesc& d, int RP, int fp64, size_t* partia
     int64_t want = std::max<int64_t>(1, (target_units * rows) / std::max<int64_t>(1, tot_rows) / ctiles);
     int64_t split_rows = (rows + want - 1) / want;
     split_rows = std::max<int64_t>(split_rows, 64);
-    split_rows = ((split_rows + 63) / 64) * 64;
+    split_rows = ((split_rows + 63) / 64) * 64;  // whole stages of the lead contraction
     const int ns = (int)((rows + split_rows - 1) / split_rows);
     d.tt_ctiles[k] = ctiles;
     d.nsplit[k] = ns;
@@ -784,7 +784,7 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
     for (int k = 0; k < K && ok; ++k) {
       ok = encode_map(&maps[k], d.X[k], d.lead_rows[k], d.trail_cols[k], d.pitch[k], 32, 256,
                       CU_TENSOR_MAP_SWIZZLE_128B) &&
-           encode_map(&maps[CNCPD_KMAX + k], d.X[k], d.lead_rows[k], d.trail_cols[k], d.pitch[k], 128, 64,
+           encode_map(&maps[CNCPD_KMAX + k], d.X[k], d.lead_rows[k], d.trail_cols[k], d.pitch[k], 256, 32,
                       CU_TENSOR_MAP_SWIZZLE_NONE);
     }
     if (ok) {

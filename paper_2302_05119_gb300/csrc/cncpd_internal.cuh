@@ -89,7 +89,7 @@ struct DevDesc {
   int nsplit[CNCPD_KMAX];
   int64_t split_rows[CNCPD_KMAX];
   const CUtensorMap* tmap_trail;        // per-block TMA descriptors of X (FP32 storage), 256 x 32 boxes
-  const CUtensorMap* tmap_lead;         // per-block TMA descriptors of X (FP32 storage), 64 x 128 boxes
+  const CUtensorMap* tmap_lead;         // per-block TMA descriptors of X (FP32 storage), 32 x 256 boxes
   int use_tma;                          // 1: the TMA kernels run the level-1 contractions
   int lt_rows;                          // rows per tile of the trailing contraction (64 or 256)
   int tt_cols;                          // columns per tile of the lead contraction

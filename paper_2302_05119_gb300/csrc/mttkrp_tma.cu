@@ -234,19 +234,20 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
 
 // ---------------------------------------------------------------------------
 // Lead contraction (split over rows) Pt[col, r] = sum_row X[row, col] W_l[row, r].
-// Unit = 128 columns x one row split; stage = 64 rows x 128 columns (32 KiB).
-// Consumer warp w takes rows w, w + 8, ... of a stage; lane l owns columns
-// 4l .. 4l + 3 (two packed column pairs).  W_l is stored with each value
-// duplicated ({w, w}) so the packed FMA takes it as one operand pair.
+// Unit = 256 columns x one row split; stage = 32 rows x 256 columns (32 KiB,
+// whole 1 KiB rows when the tensor has 256 trailing columns).  Consumer warp
+// w owns columns 64 (w % 4) + 2 lane, + 1 and rows 16 (w / 4) .. + 15 of
+// every stage; the two row halves are added at the end of the unit.
 // ---------------------------------------------------------------------------
-constexpr int LT_ROWS = 64;
-constexpr int LT_COLS = 128;
+constexpr int LT_ROWS = 32;
+constexpr int LT_COLS = 256;
 constexpr int LT_CONS = 8;
 
 template <int RP>
 struct LeadTma {
+  static constexpr int WST = (RP + 3) / 4 * 4;
   static constexpr uint32_t X_BYTES = LT_ROWS * LT_COLS * 4;
-  static constexpr uint32_t W_BYTES = LT_ROWS * RP * 8;
+  static constexpr uint32_t W_BYTES = LT_ROWS * WST * 4;
   static constexpr uint32_t RED_BYTES = LT_COLS * RP * 4;
   static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 128 - RED_BYTES) / (X_BYTES + W_BYTES));
   static constexpr int STAGES = STAGES_FIT > 6 ? 6 : STAGES_FIT;
@@ -257,10 +258,11 @@ template <int RP>
 __global__ void __launch_bounds__((LT_CONS + NKR + 1) * 32, 1) k_lead_tma(const DevDesc* __restrict__ d) {
   using S = LeadTma<RP>;
   constexpr int ST = S::STAGES;
+  constexpr int RH = RP / 2;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* xs = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  float2* wd = reinterpret_cast<float2*>(xs + ST * S::X_BYTES);
-  float* red = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(wd) + ST * S::W_BYTES);
+  float* ws = reinterpret_cast<float*>(xs + ST * S::X_BYTES);
+  float* red = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(ws) + ST * S::W_BYTES);
   uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(red) + S::RED_BYTES);
   uint64_t* empty = full + ST;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -324,29 +326,24 @@ __global__ void __launch_bounds__((LT_CONS + NKR + 1) * 32, 1) k_lead_tma(const 
         const int s = it % ST;
         const uint32_t ph = (it / ST) & 1;
         if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, err)) { ok = false; break; }
-        // Khatri-Rao rows of the lead factors, duplicated into pairs
-        float2* wst = wd + s * (S::W_BYTES / 8);
+        // Khatri-Rao row of the lead factors for row r0 + lane
+        const int row = r0 + lane;
+        float w[S::WST];
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          const int il = lane + 32 * half;
-          const int row = r0 + il;
-          float w[RP];
+        for (int r = 0; r < S::WST; ++r) w[r] = (row < re && r < R) ? 1.f : 0.f;
+        if (row < re) {
+          int idx[CNCPD_NMAX];
+          decode32_t(d, k, 0, h, row, idx);
+          for (int m = 0; m < h; ++m) {
+            const float* U = reinterpret_cast<const float*>(d->U1[k][m]) + (int64_t)idx[m] * R;
 #pragma unroll
-          for (int r = 0; r < RP; ++r) w[r] = (row < re && r < R) ? 1.f : 0.f;
-          if (row < re) {
-            int idx[CNCPD_NMAX];
-            decode32_t(d, k, 0, h, row, idx);
-            for (int m = 0; m < h; ++m) {
-              const float* U = reinterpret_cast<const float*>(d->U1[k][m]) + (int64_t)idx[m] * R;
-#pragma unroll
-              for (int r = 0; r < RP; ++r)
-                if (r < R) w[r] *= __ldg(U + r);
-            }
+            for (int r = 0; r < RP; ++r)
+              if (r < R) w[r] *= __ldg(U + r);
           }
-          float4* dst = reinterpret_cast<float4*>(wst + il * RP);
-#pragma unroll
-          for (int r = 0; r < RP; r += 2) dst[r / 2] = make_float4(w[r], w[r], w[r + 1], w[r + 1]);
         }
+        float4* dst = reinterpret_cast<float4*>(ws + s * (S::W_BYTES / 4) + lane * S::WST);
+#pragma unroll
+        for (int q = 0; q < S::WST / 4; ++q) dst[q] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&full[s]));
       }
@@ -355,6 +352,8 @@ __global__ void __launch_bounds__((LT_CONS + NKR + 1) * 32, 1) k_lead_tma(const 
   }
 
   // -------------------------------------------------------------- consumers
+  const int cg = warp & 3, rh = warp >> 2;
+  const int colw = cg * 64 + 2 * lane;  // first of this lane's two columns within the tile
   uint32_t it = 0;
   for (int u = blockIdx.x; u < total; u += gridDim.x) {
     int k = 0;
@@ -367,69 +366,69 @@ __global__ void __launch_bounds__((LT_CONS + NKR + 1) * 32, 1) k_lead_tma(const 
     const int R = d->R[k];
     const int rb = split * (int)d->split_rows[k];
     const int re = min(rows, rb + (int)d->split_rows[k]);
-    uint64_t acc2[2][RP];  // [column pair][r]: {sum of column 2c, sum of column 2c+1}
+    uint64_t acc[2][RH];  // [column][pair of ranks]
 #pragma unroll
     for (int c = 0; c < 2; ++c)
 #pragma unroll
-      for (int r = 0; r < RP; ++r) acc2[c][r] = 0ull;
+      for (int p = 0; p < RH; ++p) acc[c][p] = 0ull;
     for (int r0 = rb; r0 < re; r0 += LT_ROWS, ++it) {
       const int s = it % ST;
       const uint32_t ph = (it / ST) & 1;
       if (!mbar_wait(smem_u32(&full[s]), ph, err)) continue;  // error recorded; keep the barrier schedule
       const unsigned char* xt = xs + s * S::X_BYTES;
-      const float2* wt = wd + s * (S::W_BYTES / 8);
-#pragma unroll 4
-      for (int i = warp; i < LT_ROWS; i += LT_CONS) {
-        const ulonglong2 x = *reinterpret_cast<const ulonglong2*>(xt + i * (LT_COLS * 4) + lane * 16);
-        const ulonglong2* wr = reinterpret_cast<const ulonglong2*>(wt + i * RP);
+      const float* wt = ws + s * (S::W_BYTES / 4);
+#pragma unroll 8
+      for (int i = rh * 16; i < rh * 16 + 16; ++i) {
+        const float2 x = *reinterpret_cast<const float2*>(xt + i * (LT_COLS * 4) + colw * 4);
+        const uint64_t x0 = pack2(x.x, x.x), x1 = pack2(x.y, x.y);
+        const uint64_t* wr = reinterpret_cast<const uint64_t*>(wt + i * S::WST);
 #pragma unroll
-        for (int r = 0; r < RP; r += 2) {
-          const ulonglong2 w = wr[r / 2];  // {w_r, w_r}, {w_r+1, w_r+1}
-          ffma2x(acc2[0][r], x.x, w.x);
-          ffma2x(acc2[1][r], x.y, w.x);
-          ffma2x(acc2[0][r + 1], x.x, w.y);
-          ffma2x(acc2[1][r + 1], x.y, w.y);
+        for (int p = 0; p + 2 <= RH; p += 2) {
+          const ulonglong2 w = *reinterpret_cast<const ulonglong2*>(wr + p);
+          ffma2x(acc[0][p], x0, w.x);
+          ffma2x(acc[0][p + 1], x0, w.y);
+          ffma2x(acc[1][p], x1, w.x);
+          ffma2x(acc[1][p + 1], x1, w.y);
+        }
+        if constexpr (RH % 2 == 1) {
+          const uint64_t w = wr[RH - 1];
+          ffma2x(acc[0][RH - 1], x0, w);
+          ffma2x(acc[1][RH - 1], x1, w);
         }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
     }
-    float acc[4][RP];
+    float accf[2][RP];
 #pragma unroll
-    for (int r = 0; r < RP; ++r) {
-      const float2 u = unpack2(acc2[0][r]), v = unpack2(acc2[1][r]);
-      acc[0][r] = u.x;
-      acc[1][r] = u.y;
-      acc[2][r] = v.x;
-      acc[3][r] = v.y;
-    }
-    // fixed-order reduction of the consumer warps: (((w1 + w2) + w3) + ...) + w0
-    for (int src = 1; src < LT_CONS; ++src) {
-      named_bar(1, LT_CONS * 32);
-      if (warp == src) {
+    for (int c = 0; c < 2; ++c)
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-          for (int r = 0; r < RP; ++r) {
-            float* p = red + (lane * 4 + c) * RP + r;
-            *p = (src == 1) ? acc[c][r] : *p + acc[c][r];
-          }
+      for (int p = 0; p < RH; ++p) {
+        const float2 v = unpack2(acc[c][p]);
+        accf[c][2 * p] = v.x;
+        accf[c][2 * p + 1] = v.y;
       }
+    // the second row half hands its sums to the first (fixed order: half 0 + half 1)
+    named_bar(1, LT_CONS * 32);
+    if (rh == 1) {
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int r = 0; r < RP; ++r) red[(colw + c) * RP + r] = accf[c][r];
     }
     named_bar(1, LT_CONS * 32);
-    if (warp == 0) {
+    if (rh == 0) {
       float* part = reinterpret_cast<float*>(d->partial) + d->partial_off[k] + (int64_t)split * J * R;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int col = ctile * LT_COLS + lane * 4 + c;
+      for (int c = 0; c < 2; ++c) {
+        const int col = ctile * LT_COLS + colw + c;
         if (col < J) {
 #pragma unroll
           for (int r = 0; r < RP; ++r)
-            if (r < R) part[(int64_t)col * R + r] = red[(lane * 4 + c) * RP + r] + acc[c][r];
+            if (r < R) part[(int64_t)col * R + r] = accf[c][r] + red[(colw + c) * RP + r];
         }
       }
     }
-    named_bar(1, LT_CONS * 32);
   }
 }
 
