@@ -98,6 +98,8 @@ struct cncpd_ctx {
   cudaGraphExec_t g_main = nullptr, g_redo = nullptr;
   int main_runs = 0, redo_runs = 0;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t side = nullptr;                // branch for work independent of a tensor pass
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
   // LRA
   bool lra = false;
@@ -278,17 +280,38 @@ int enqueue_lead(cncpd_ctx* c, const DevDesc* dd, const DevDesc& hd, int RP, con
   return CNCPD_OK;
 }
 
+// Launch H / L of mode n (with the Gram of mode n-1) on the side stream so
+// that it runs concurrently with the tensor pass enqueued next on the main
+// stream; the main stream joins before the update of mode n.
+int fork_lipschitz(cncpd_ctx* c, int n, int core) {
+  LaunchCfg ls{c->side, c->num_sms};
+  CU(cudaEventRecord(c->ev_fork, c->stream));
+  CU(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+  CU(launch_lipschitz(ls, c->dd, c->hd, c->fp64, n, core, n - 1));
+  CU(cudaEventRecord(c->ev_join, c->side));
+  return CNCPD_OK;
+}
+
 int enqueue_sweep(cncpd_ctx* c, int use_w) {
   LaunchCfg lc{c->stream, c->num_sms};
   const double dw = c->opts.delta_w;
   const int core = c->opts.use_core;
   if (core) CU(launch_core_update(lc, c->dd, c->hd, use_w, dw));
   for (int n = 0; n < c->N; ++n) {
-    if (!c->lra) {
+    bool forked = false;
+    if (!c->lra && (n == 0 || n == c->h)) {
+      // the pass needs the factors updated so far; H / L of mode n only needs
+      // the Grams, which are final as well: run them side by side
+      TRY(fork_lipschitz(c, n, core));
+      forked = true;
       if (n == 0) TRY(enqueue_trailing(c, c->dd, c->hd, c->RP));
-      if (n == c->h) TRY(enqueue_lead(c, c->dd, c->hd, c->RP, c->d_red_prefix));
+      else TRY(enqueue_lead(c, c->dd, c->hd, c->RP, c->d_red_prefix));
     }
-    if (!c->lra && level2_is_pair(c->hd, n)) {
+    if (forked) {
+      if (level2_is_pair(c->hd, n)) CU(launch_mode_prep(lc, c->dd, c->hd, c->fp64, n, core, -1, 2));
+      else TRY(enqueue_mode_m(c, n));
+      CU(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    } else if (!c->lra && level2_is_pair(c->hd, n)) {
       // level 2 of mode n and H / L of mode n (with the Gram of mode n-1) in one launch
       CU(launch_mode_prep(lc, c->dd, c->hd, c->fp64, n, core, n - 1, 1));
     } else {
@@ -578,6 +601,9 @@ void cncpd_destroy(cncpd_t h) {
   if (h->hs) cudaFreeHost(h->hs);
   for (auto& e : h->ev)
     if (e) cudaEventDestroy(e);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->side) cudaStreamDestroy(h->side);
   if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -657,6 +683,9 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
 
   CCU(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
   CCU(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+  CCU(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+  CCU(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+  CCU(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
   CCU(cudaMallocHost((void**)&c->hs, sizeof(HostScalars)));
   for (auto& e : c->ev) CCU(cudaEventCreate(&e));
   // order after the caller's stream

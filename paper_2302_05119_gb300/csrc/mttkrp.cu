@@ -314,29 +314,38 @@ k_lead_contract(const DevDesc* __restrict__ d) {
   }
 }
 
-// Sum of the split partials in fixed order s = 0, 1, ... into Pt.
+// Sum of the split partials into Pt: a CTA takes 32 consecutive entries;
+// thread group g (of 8) adds splits g, g + 8, ... and the 8 group sums are
+// added in group order (fixed order: deterministic).
 template <typename T>
-__global__ void k_reduce_splits(const DevDesc* __restrict__ d, const int64_t* __restrict__ prefix) {
+__global__ void __launch_bounds__(256) k_reduce_splits(const DevDesc* __restrict__ d, const int64_t* __restrict__ prefix) {
+  __shared__ T red[8][32];
   const int K = d->K;
   const int64_t total = prefix[K];
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    int k = 0;
-    while (prefix[k + 1] <= e) ++k;
-    const int64_t local = e - prefix[k];
-    const int64_t stride = d->trail_cols[k] * d->R[k];
-    const T* part = reinterpret_cast<const T*>(d->partial) + d->partial_off[k] + local;
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  for (int64_t e0 = (int64_t)blockIdx.x * 32; e0 < total; e0 += (int64_t)gridDim.x * 32) {
+    const int64_t e = e0 + lane;
     T s = T(0);
-    const int ns = d->nsplit[k];
-    int i = 0;
-    for (; i + 8 <= ns; i += 8) {
-      T v[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] = part[(int64_t)(i + q) * stride];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) s += v[q];
+    if (e < total) {
+      int k = 0;
+      while (prefix[k + 1] <= e) ++k;
+      const int64_t local = e - prefix[k];
+      const int64_t stride = d->trail_cols[k] * d->R[k];
+      const T* part = reinterpret_cast<const T*>(d->partial) + d->partial_off[k] + local;
+      const int ns = d->nsplit[k];
+#pragma unroll 4
+      for (int i = g; i < ns; i += 8) s += part[(int64_t)i * stride];
     }
-    for (; i < ns; ++i) s += part[(int64_t)i * stride];
-    reinterpret_cast<T*>(d->Pt[k])[local] = s;
+    red[g][lane] = s;
+    __syncthreads();
+    if (g == 0 && e < total) {
+      T t = red[0][lane];
+      for (int q = 1; q < 8; ++q) t += red[q][lane];
+      int k = 0;
+      while (prefix[k + 1] <= e) ++k;
+      reinterpret_cast<T*>(d->Pt[k])[e - prefix[k]] = t;
+    }
+    __syncthreads();
   }
 }
 
@@ -432,8 +441,8 @@ static cudaError_t trailing_impl(const LaunchCfg& c, const DevDesc* dd, const De
 }
 
 cudaError_t launch_reduce_splits(const LaunchCfg& c, const DevDesc* dd, int fp64, const int64_t* d_red_prefix) {
-  if (fp64) k_reduce_splits<double><<<c.num_sms * 4, 256, 0, c.stream>>>(dd, d_red_prefix);
-  else k_reduce_splits<float><<<c.num_sms * 4, 256, 0, c.stream>>>(dd, d_red_prefix);
+  if (fp64) k_reduce_splits<double><<<c.num_sms * 8, 256, 0, c.stream>>>(dd, d_red_prefix);
+  else k_reduce_splits<float><<<c.num_sms * 8, 256, 0, c.stream>>>(dd, d_red_prefix);
   return cudaGetLastError();
 }
 

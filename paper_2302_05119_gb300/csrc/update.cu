@@ -39,6 +39,7 @@ struct LmaxScratch {
   }
 };
 
+template <typename TT>
 __device__ double lmax_psd(const double* Hs, int R, LmaxScratch* s) {
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
   const int nt = blockDim.x * blockDim.y;
@@ -92,25 +93,27 @@ __device__ double lmax_psd(const double* Hs, int R, LmaxScratch* s) {
   float dm = -1.f;
   for (int i = 0; i < R; ++i)
     if (s->A[i * R + i] > dm) { dm = s->A[i * R + i]; jm = i; }
+  // (TT = float on the FP32 path: L to FP32 accuracy is ample there and
+  // FP64 arithmetic is slow on this part; TT = double on the FP64 path.)
   for (int i = tid; i < R; i += nt) {
-    const double vi = (double)s->A[i * R + jm];
-    double a = 0.0;
-    for (int l = 0; l < R; ++l) a = fma(Hs[i * R + l], (double)s->A[l * R + jm], a);
-    s->v[i] = vi * a;   // v_i (H v)_i
-    s->w[i] = vi * vi;  // v_i^2
+    const TT vi = (TT)s->A[i * R + jm];
+    TT a = TT(0);
+    for (int l = 0; l < R; ++l) a = fma((TT)Hs[i * R + l], (TT)s->A[l * R + jm], a);
+    s->v[i] = (double)(vi * a);   // v_i (H v)_i
+    s->w[i] = (double)(vi * vi);  // v_i^2
   }
   __syncthreads();
-  double num = 0.0, den = 0.0;
   if (tid < 32) {
+    TT num = TT(0), den = TT(0);
     for (int i = tid; i < R; i += 32) {
-      num += s->v[i];
-      den += s->w[i];
+      num += (TT)s->v[i];
+      den += (TT)s->w[i];
     }
     for (int o = 16; o > 0; o >>= 1) {
       num += __shfl_xor_sync(0xffffffffu, num, o);
       den += __shfl_xor_sync(0xffffffffu, den, o);
     }
-    if (tid == 0) s->v[0] = den > 0.0 ? num / den : 0.0;
+    if (tid == 0) s->v[0] = den > TT(0) ? (double)(num / den) : 0.0;
   }
   __syncthreads();
   const double L = s->v[0];
@@ -124,12 +127,13 @@ static cudaError_t allow_smem(KernelT kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-__device__ __forceinline__ double extrap_weight(double w_hat, int have_prev, double Lprev, double Lcur,
-                                                double delta_w) {
-  // Eqs. eqextrawd / eqextrawu; first iteration reads the ratio as 1.
-  if (!(Lcur > 0.0)) return 0.0;
-  const double ratio = have_prev ? Lprev / Lcur : 1.0;
-  return fmin(w_hat, delta_w * sqrt(ratio));
+template <typename TT>
+__device__ __forceinline__ TT extrap_weight(double w_hat, int have_prev, double Lprev, double Lcur, double delta_w) {
+  // Eqs. eqextrawd / eqextrawu; first iteration reads the ratio as 1.  TT is
+  // the factor precision (FP32 on the FP32 path; FP64 is slow on this part).
+  if (!(Lcur > 0.0)) return TT(0);
+  const TT ratio = have_prev ? (TT)Lprev / (TT)Lcur : TT(1);
+  return min((TT)w_hat, (TT)delta_w * sqrt(ratio));
 }
 
 // ---------------------------------------------------------------------------
@@ -144,10 +148,17 @@ constexpr int GRAM_TILE = 64;
 template <typename T>
 __device__ void block_gram(const T* __restrict__ U, int64_t I, int R, double* __restrict__ G, T* buf, int cap_rows) {
   // buf holds cap_rows rows (a multiple of GRAM_TILE); rows are staged in as
-  // few round trips as the buffer allows, the arithmetic order is fixed.
+  // few round trips as the buffer allows.  For small R each pair's rows are
+  // split into SL = max(1, 256 / R^2) interleaved slices (an FMA chain in the
+  // factor type each); per tile the slice sums are added in slice order in
+  // FP64, tiles in order.  The order depends only on R, so every kernel that
+  // calls this routine gets bit-identical Grams.
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
   const int nt = blockDim.x * blockDim.y;
   const int RR = R * R;
+  const int SL = max(1, 256 / RR);
+  const int items = RR * SL;  // <= 256 whenever SL > 1
+  __shared__ double slice_sum[256];
   double acc[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) acc[q] = 0.0;
@@ -159,15 +170,38 @@ __device__ void block_gram(const T* __restrict__ U, int64_t I, int R, double* __
     for (int t0 = 0; t0 < ns; t0 += GRAM_TILE) {
       const int n = min(GRAM_TILE, ns - t0);
       const T* tile = buf + t0 * R;
+      if (SL == 1) {
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int p = q * nt + tid;
-        if (p < RR) {
+        for (int q = 0; q < 16; ++q) {
+          const int p = q * nt + tid;
+          if (p < RR) {
+            const int a = p / R, b = p % R;
+            T s = T(0);
+#pragma unroll 4
+            for (int i = 0; i < n; ++i) s = fma(tile[i * R + a], tile[i * R + b], s);
+            acc[q] += (double)s;
+          }
+        }
+      } else {
+        for (int wi = tid; wi < items; wi += nt) {
+          const int p = wi / SL, sl = wi % SL;
           const int a = p / R, b = p % R;
           T s = T(0);
-          for (int i = 0; i < n; ++i) s = fma(tile[i * R + a], tile[i * R + b], s);
-          acc[q] += (double)s;
+#pragma unroll 4
+          for (int i = sl; i < n; i += SL) s = fma(tile[i * R + a], tile[i * R + b], s);
+          slice_sum[wi] = (double)s;
         }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int p = q * nt + tid;
+          if (p < RR) {
+            double t = 0.0;
+            for (int sl = 0; sl < SL; ++sl) t += slice_sum[p * SL + sl];
+            acc[q] += t;
+          }
+        }
+        __syncthreads();
       }
     }
   }
@@ -228,7 +262,7 @@ __device__ void lipschitz_body(const DevDesc* __restrict__ d, int k, int n, int 
     Hout[e] = (T)h;
   }
   if (!want_L) return;
-  const double L = lmax_psd(Hs, R, &scr);
+  const double L = lmax_psd<T>(Hs, R, &scr);
   if (threadIdx.x == 0) {
     sc->Lcur_u[n][k] = L;
     if (!isfinite(L)) atomicExch(&sc->nonfinite, 1);
@@ -425,12 +459,12 @@ __global__ void __launch_bounds__(128) k_update(const DevDesc* __restrict__ d, i
     // evaluation per block instead of one per thread
     const double w_hat = use_w ? sc->w_hat : 0.0;
     const int have_prev = sc->have_prev;
-    if (tid < K) wsh[tid] = (T)extrap_weight(w_hat, have_prev, sc->Lprev_u[n][tid], sc->Lcur_u[n][tid], delta_w);
+    if (tid < K) wsh[tid] = extrap_weight<T>(w_hat, have_prev, sc->Lprev_u[n][tid], sc->Lcur_u[n][tid], delta_w);
     if (tid == K) {
       double LC = 0.0;
       for (int k = 0; k < K; ++k) LC += sc->Lcur_u[n][k];
       LCs = LC;
-      wsh[K] = (T)extrap_weight(w_hat, have_prev, sc->LCprev[n], LC, delta_w);
+      wsh[K] = extrap_weight<T>(w_hat, have_prev, sc->LCprev[n], LC, delta_w);
       if (blockIdx.x == 0) {
         sc->LCcur[n] = LC;
         sc->have_cur = 1;
@@ -643,8 +677,8 @@ __global__ void __launch_bounds__(256) k_core_update(const DevDesc* __restrict__
     for (int m = 0; m < N; ++m) h *= d->G[k][m][e];
     Hs[e] = h;
   }
-  const double Ld = lmax_psd(Hs, R, &scr);
-  const double w = extrap_weight(use_w ? sc->w_hat : 0.0, sc->have_prev, sc->Ldprev[k], Ld, delta_w);
+  const double Ld = lmax_psd<double>(Hs, R, &scr);
+  const double w = extrap_weight<double>(use_w ? sc->w_hat : 0.0, sc->have_prev, sc->Ldprev[k], Ld, delta_w);
   for (int a = threadIdx.x; a < R; a += blockDim.x) lh[a] = sc->lam1[k][a] + w * (sc->lam1[k][a] - sc->lam2[k][a]);
   __syncthreads();
   if (Ld > 0.0) {
@@ -901,7 +935,7 @@ __global__ void k_lmax_one(const double* H, int R, double* out) {
   scr.carve(smem_raw, R);
   double* Hs = scr.Hs;
   for (int e = threadIdx.x; e < R * R; e += blockDim.x) Hs[e] = H[e];
-  const double L = lmax_psd(Hs, R, &scr);
+  const double L = lmax_psd<double>(Hs, R, &scr);
   if (threadIdx.x == 0) *out = L;
 }
 
