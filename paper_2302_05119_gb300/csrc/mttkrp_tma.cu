@@ -27,14 +27,15 @@ __device__ __forceinline__ void decode32_t(const DevDesc* d, int k, int m0, int 
 // ---------------------------------------------------------------------------
 // Trailing contraction Pl[row, r] = sum_col X[row, col] W_t[col, r].
 // Tile = 256 rows; stage = 256 rows x 32 columns (32 KiB, 128-byte swizzle).
-// Consumer warp w owns rows 64(w % 4) + lane and 64(w % 4) + 32 + lane of the
-// tile and columns 16(w / 4) .. 16(w / 4) + 15 of every stage; the two
-// column halves are added at the end of the tile.  Two consumer warps per
-// scheduler hide the shared-memory latency of one another.
+// Consumer warp w owns rows 128 (w % 2) + 32 j + lane (j = 0..3) of the tile
+// and columns 8 (w / 2) .. 8 (w / 2) + 7 of every stage, so each Khatri-Rao
+// value read from shared memory feeds four rows; the four column quarters are
+// added at the end of the tile.  Two consumer warps per scheduler hide the
+// shared-memory latency of one another.
 // ---------------------------------------------------------------------------
 constexpr int TT_ROWS = 256;
 constexpr int TT_BC = 32;
-constexpr int TT_CONS = 8;  // 4 row groups x 2 column halves
+constexpr int TT_CONS = 8;  // 2 row halves x 4 column quarters
 constexpr size_t SMEM_LIMIT = 232448;  // 227 KiB of dynamic shared memory per CTA
 constexpr int NKR = 3;  // Khatri-Rao warps, stage i handled by warp i mod NKR
 
@@ -43,7 +44,7 @@ struct TrailTma {
   static constexpr int WST = (RP + 3) / 4 * 4;
   static constexpr uint32_t X_BYTES = TT_ROWS * TT_BC * 4;
   static constexpr uint32_t W_BYTES = TT_BC * WST * 4;
-  static constexpr uint32_t RED_BYTES = TT_ROWS * RP * 4;  // column-half partial sums
+  static constexpr uint32_t RED_BYTES = 3 * TT_ROWS * RP * 4;  // partial sums of column quarters 1..3
   // as many stages as fit (at most 6): bytes in flight hide the memory latency
   static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 128 - RED_BYTES) / (X_BYTES + W_BYTES));
   static constexpr int STAGES = STAGES_FIT > 6 ? 6 : STAGES_FIT;
@@ -143,8 +144,8 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
 
   // -------------------------------------------------------------- consumers
   uint32_t it = 0;
-  const int rg = warp & 3, ch = warp >> 2;
-  const int ra = rg * 64 + lane, rb = ra + 32;
+  const int rq = warp & 1, cq = warp >> 1;  // row half (128 rows, 4 per lane), column quarter (8 columns)
+  constexpr int RH = RP / 2;
   for (int g = blockIdx.x; g < total; g += gridDim.x) {
     int k = 0;
     while (d->lt_prefix[k + 1] <= g) ++k;
@@ -152,82 +153,87 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
     const int J = (int)d->trail_cols[k];
     const int R = d->R[k];
     const int nch = (J + TT_BC - 1) / TT_BC;
-    constexpr int RH = RP / 2;
-    uint64_t acc0[RH], acc1[RH];  // pairs (r, r+1) of the two rows' sums
+    uint64_t acc[4][RH];  // [row j][pair of ranks]
 #pragma unroll
-    for (int p = 0; p < RH; ++p) acc0[p] = acc1[p] = 0ull;
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int p = 0; p < RH; ++p) acc[j][p] = 0ull;
     for (int c = 0; c < nch; ++c, ++it) {
       const int s = it % TST;
       const uint32_t ph = (it / TST) & 1;
       if (!mbar_wait(smem_u32(&full[s]), ph, err)) continue;  // error recorded; keep the barrier schedule
       const unsigned char* xt = xs + s * S::X_BYTES;
       const float* wt = ws + s * (S::W_BYTES / 4);
-#pragma unroll 2
-      for (int q = 4 * ch; q < 4 * ch + 4; ++q) {
-        // 128-byte swizzle: 16-byte chunk q of row r sits at chunk q ^ (r & 7)
-        const float4 xa = *reinterpret_cast<const float4*>(xt + ra * 128 + ((q ^ (ra & 7)) << 4));
-        const float4 xb = *reinterpret_cast<const float4*>(xt + rb * 128 + ((q ^ (rb & 7)) << 4));
-        const float av[4] = {xa.x, xa.y, xa.z, xa.w};
-        const float bv[4] = {xb.x, xb.y, xb.z, xb.w};
+#pragma unroll
+      for (int q = 2 * cq; q < 2 * cq + 2; ++q) {
+        float xv[4][4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          // 128-byte swizzle: 16-byte chunk q of row r sits at chunk q ^ (r & 7)
+          const int r = rq * 128 + 32 * j + lane;
+          const float4 x = *reinterpret_cast<const float4*>(xt + r * 128 + ((q ^ (r & 7)) << 4));
+          xv[j][0] = x.x; xv[j][1] = x.y; xv[j][2] = x.z; xv[j][3] = x.w;
+        }
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const uint64_t a2 = pack2(av[e], av[e]);
-          const uint64_t b2 = pack2(bv[e], bv[e]);
           const uint64_t* wr = reinterpret_cast<const uint64_t*>(wt + (4 * q + e) * S::WST);
+          uint64_t x2[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) x2[j] = pack2(xv[j][e], xv[j][e]);
 #pragma unroll
           for (int p = 0; p + 2 <= RH; p += 2) {
             const ulonglong2 w = *reinterpret_cast<const ulonglong2*>(wr + p);
-            ffma2x(acc0[p], a2, w.x);
-            ffma2x(acc0[p + 1], a2, w.y);
-            ffma2x(acc1[p], b2, w.x);
-            ffma2x(acc1[p + 1], b2, w.y);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              ffma2x(acc[j][p], x2[j], w.x);
+              ffma2x(acc[j][p + 1], x2[j], w.y);
+            }
           }
           if constexpr (RH % 2 == 1) {
             const uint64_t w = wr[RH - 1];
-            ffma2x(acc0[RH - 1], a2, w);
-            ffma2x(acc1[RH - 1], b2, w);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) ffma2x(acc[j][RH - 1], x2[j], w);
           }
         }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
     }
-    float acc0f[RP], acc1f[RP];
-#pragma unroll
-    for (int p = 0; p < RH; ++p) {
-      const float2 u = unpack2(acc0[p]), v = unpack2(acc1[p]);
-      acc0f[2 * p] = u.x;
-      acc0f[2 * p + 1] = u.y;
-      acc1f[2 * p] = v.x;
-      acc1f[2 * p + 1] = v.y;
-    }
-    // second column half hands its sums to the first (fixed order: half 0 + half 1)
+    // column quarters 1..3 park their sums; quarter 0 adds them in order
     named_bar(1, TT_CONS * 32);
-    if (ch == 1) {
+    if (cq > 0) {
 #pragma unroll
-      for (int r = 0; r < RP; ++r) {
-        red[ra * RP + r] = acc0f[r];
-        red[rb * RP + r] = acc1f[r];
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int p = 0; p < RH; ++p) {
+          const float2 v = unpack2(acc[j][p]);
+          const int r = rq * 128 + 32 * j + lane;
+          red[((cq - 1) * TT_ROWS + r) * RP + 2 * p] = v.x;
+          red[((cq - 1) * TT_ROWS + r) * RP + 2 * p + 1] = v.y;
+        }
+    }
+    named_bar(1, TT_CONS * 32);
+    if (cq == 0) {
+      const int64_t rows = d->lead_rows[k];
+      float* P = reinterpret_cast<float*>(d->Pl[k]);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = rq * 128 + 32 * j + lane;
+        if (row0 + r < rows) {
+#pragma unroll
+          for (int p = 0; p < RH; ++p) {
+            const float2 v = unpack2(acc[j][p]);
+            float o0 = v.x, o1 = v.y;
+#pragma unroll
+            for (int q4 = 0; q4 < 3; ++q4) {
+              o0 += red[(q4 * TT_ROWS + r) * RP + 2 * p];
+              o1 += red[(q4 * TT_ROWS + r) * RP + 2 * p + 1];
+            }
+            if (2 * p < R) P[(int64_t)(row0 + r) * R + 2 * p] = o0;
+            if (2 * p + 1 < R) P[(int64_t)(row0 + r) * R + 2 * p + 1] = o1;
+          }
+        }
       }
-    }
-    named_bar(1, TT_CONS * 32);
-    if (ch == 1) continue;
-#pragma unroll
-    for (int r = 0; r < RP; ++r) {
-      acc0f[r] += red[ra * RP + r];
-      acc1f[r] += red[rb * RP + r];
-    }
-    const int64_t rows = d->lead_rows[k];
-    float* P = reinterpret_cast<float*>(d->Pl[k]);
-    if (row0 + ra < rows) {
-#pragma unroll
-      for (int r = 0; r < RP; ++r)
-        if (r < R) P[(int64_t)(row0 + ra) * R + r] = acc0f[r];
-    }
-    if (row0 + rb < rows) {
-#pragma unroll
-      for (int r = 0; r < RP; ++r)
-        if (r < R) P[(int64_t)(row0 + rb) * R + r] = acc1f[r];
     }
   }
 }
