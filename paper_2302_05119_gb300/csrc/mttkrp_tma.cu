@@ -242,8 +242,9 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
 // Lead contraction (split over rows) Pt[col, r] = sum_row X[row, col] W_l[row, r].
 // Unit = 256 columns x one row split; stage = 32 rows x 256 columns (32 KiB,
 // whole 1 KiB rows when the tensor has 256 trailing columns).  Consumer warp
-// w owns columns 64 (w % 4) + 2 lane, + 1 and rows 16 (w / 4) .. + 15 of
-// every stage; the two row halves are added at the end of the unit.
+// w owns columns 128 (w % 2) + 4 lane .. + 3 and rows 8 (w / 2) .. + 7 of
+// every stage, so each Khatri-Rao value read from shared memory feeds four
+// columns; the four row quarters are added at the end of the unit.
 // ---------------------------------------------------------------------------
 constexpr int LT_ROWS = 32;
 constexpr int LT_COLS = 256;
@@ -254,7 +255,7 @@ struct LeadTma {
   static constexpr int WST = (RP + 3) / 4 * 4;
   static constexpr uint32_t X_BYTES = LT_ROWS * LT_COLS * 4;
   static constexpr uint32_t W_BYTES = LT_ROWS * WST * 4;
-  static constexpr uint32_t RED_BYTES = LT_COLS * RP * 4;
+  static constexpr uint32_t RED_BYTES = 3 * LT_COLS * RP * 4;  // partial sums of row quarters 1..3
   static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 128 - RED_BYTES) / (X_BYTES + W_BYTES));
   static constexpr int STAGES = STAGES_FIT > 6 ? 6 : STAGES_FIT;
   static constexpr size_t SMEM = 1024 + STAGES * (size_t)(X_BYTES + W_BYTES) + RED_BYTES + 2 * STAGES * 8;
@@ -358,8 +359,8 @@ __global__ void __launch_bounds__((LT_CONS + NKR + 1) * 32, 1) k_lead_tma(const 
   }
 
   // -------------------------------------------------------------- consumers
-  const int cg = warp & 3, rh = warp >> 2;
-  const int colw = cg * 64 + 2 * lane;  // first of this lane's two columns within the tile
+  const int ch = warp & 1, rq = warp >> 1;  // column half (128 columns, 4 per lane), row quarter (8 rows)
+  const int colw = ch * 128 + 4 * lane;    // first of this lane's four columns within the tile
   uint32_t it = 0;
   for (int u = blockIdx.x; u < total; u += gridDim.x) {
     int k = 0;
@@ -372,9 +373,9 @@ __global__ void __launch_bounds__((LT_CONS + NKR + 1) * 32, 1) k_lead_tma(const 
     const int R = d->R[k];
     const int rb = split * (int)d->split_rows[k];
     const int re = min(rows, rb + (int)d->split_rows[k]);
-    uint64_t acc[2][RH];  // [column][pair of ranks]
+    uint64_t acc[4][RH];  // [column][pair of ranks]
 #pragma unroll
-    for (int c = 0; c < 2; ++c)
+    for (int c = 0; c < 4; ++c)
 #pragma unroll
       for (int p = 0; p < RH; ++p) acc[c][p] = 0ull;
     for (int r0 = rb; r0 < re; r0 += LT_ROWS, ++it) {
@@ -383,10 +384,10 @@ __global__ void __launch_bounds__((LT_CONS + NKR + 1) * 32, 1) k_lead_tma(const 
       if (!mbar_wait(smem_u32(&full[s]), ph, err)) continue;  // error recorded; keep the barrier schedule
       const unsigned char* xt = xs + s * S::X_BYTES;
       const float* wt = ws + s * (S::W_BYTES / 4);
-#pragma unroll 8
-      for (int i = rh * 16; i < rh * 16 + 16; ++i) {
-        const float2 x = *reinterpret_cast<const float2*>(xt + i * (LT_COLS * 4) + colw * 4);
-        const uint64_t x0 = pack2(x.x, x.x), x1 = pack2(x.y, x.y);
+#pragma unroll 4
+      for (int i = rq * 8; i < rq * 8 + 8; ++i) {
+        const float4 x = *reinterpret_cast<const float4*>(xt + i * (LT_COLS * 4) + colw * 4);
+        const uint64_t x0 = pack2(x.x, x.x), x1 = pack2(x.y, x.y), x2 = pack2(x.z, x.z), x3 = pack2(x.w, x.w);
         const uint64_t* wr = reinterpret_cast<const uint64_t*>(wt + i * S::WST);
 #pragma unroll
         for (int p = 0; p + 2 <= RH; p += 2) {
@@ -395,43 +396,53 @@ __global__ void __launch_bounds__((LT_CONS + NKR + 1) * 32, 1) k_lead_tma(const 
           ffma2x(acc[0][p + 1], x0, w.y);
           ffma2x(acc[1][p], x1, w.x);
           ffma2x(acc[1][p + 1], x1, w.y);
+          ffma2x(acc[2][p], x2, w.x);
+          ffma2x(acc[2][p + 1], x2, w.y);
+          ffma2x(acc[3][p], x3, w.x);
+          ffma2x(acc[3][p + 1], x3, w.y);
         }
         if constexpr (RH % 2 == 1) {
           const uint64_t w = wr[RH - 1];
           ffma2x(acc[0][RH - 1], x0, w);
           ffma2x(acc[1][RH - 1], x1, w);
+          ffma2x(acc[2][RH - 1], x2, w);
+          ffma2x(acc[3][RH - 1], x3, w);
         }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
     }
-    float accf[2][RP];
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-#pragma unroll
-      for (int p = 0; p < RH; ++p) {
-        const float2 v = unpack2(acc[c][p]);
-        accf[c][2 * p] = v.x;
-        accf[c][2 * p + 1] = v.y;
-      }
-    // the second row half hands its sums to the first (fixed order: half 0 + half 1)
+    // row quarters 1..3 park their sums; quarter 0 adds them in order
     named_bar(1, LT_CONS * 32);
-    if (rh == 1) {
+    if (rq > 0) {
 #pragma unroll
-      for (int c = 0; c < 2; ++c)
+      for (int c = 0; c < 4; ++c)
 #pragma unroll
-        for (int r = 0; r < RP; ++r) red[(colw + c) * RP + r] = accf[c][r];
+        for (int p = 0; p < RH; ++p) {
+          const float2 v = unpack2(acc[c][p]);
+          red[((rq - 1) * LT_COLS + colw + c) * RP + 2 * p] = v.x;
+          red[((rq - 1) * LT_COLS + colw + c) * RP + 2 * p + 1] = v.y;
+        }
     }
     named_bar(1, LT_CONS * 32);
-    if (rh == 0) {
+    if (rq == 0) {
       float* part = reinterpret_cast<float*>(d->partial) + d->partial_off[k] + (int64_t)split * J * R;
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
+      for (int c = 0; c < 4; ++c) {
         const int col = ctile * LT_COLS + colw + c;
         if (col < J) {
 #pragma unroll
-          for (int r = 0; r < RP; ++r)
-            if (r < R) part[(int64_t)col * R + r] = accf[c][r] + red[(colw + c) * RP + r];
+          for (int p = 0; p < RH; ++p) {
+            const float2 v = unpack2(acc[c][p]);
+            float o0 = v.x, o1 = v.y;
+#pragma unroll
+            for (int q4 = 0; q4 < 3; ++q4) {
+              o0 += red[(q4 * LT_COLS + colw + c) * RP + 2 * p];
+              o1 += red[(q4 * LT_COLS + colw + c) * RP + 2 * p + 1];
+            }
+            if (2 * p < R) part[(int64_t)col * R + 2 * p] = o0;
+            if (2 * p + 1 < R) part[(int64_t)col * R + 2 * p + 1] = o1;
+          }
         }
       }
     }
