@@ -272,7 +272,7 @@ int enqueue_lead(cncpd_ctx* c, const DevDesc* dd, const DevDesc& hd, int RP, con
   if (hd.use_tma) {
     CU(launch_lead_tma(lc, dd, hd, RP));
     TRY(record(c, 3));
-    CU(launch_reduce_splits(lc, dd, c->fp64, red_prefix));
+    CU(launch_reduce_splits(lc, hd, c->fp64));
   } else {
     CU(launch_lead_contract(lc, dd, hd, c->st, RP, red_prefix));
     TRY(record(c, 3));
@@ -325,7 +325,7 @@ int enqueue_sweep(cncpd_ctx* c, int use_w) {
     CU(launch_gram(lc, c->dd, c->hd, c->fp64, c->N - 1, c->N, 0));
     CU(launch_lra_objective(lc, c->dd, c->hd, c->fp64, core));
   }
-  else CU(launch_objective(lc, c->dd, c->hd, c->fp64, c->RP, 1));
+  else CU(launch_objective(lc, c->dd, c->hd, c->fp64, c->RP, 1, 1));
   return CNCPD_OK;
 }
 
@@ -347,7 +347,7 @@ int timeout_error(cncpd_ctx* c) {
 
 int enqueue_main(cncpd_ctx* c) {
   LaunchCfg lc{c->stream, c->num_sms};
-  CU(launch_iter_begin(lc, c->dd, c->hd));
+  CU(launch_iter_begin(lc, c->dd, c->hd, c->opts.use_core));
   CU(cudaMemcpyAsync(c->AS, c->A2, arena_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
   TRY(enqueue_sweep(c, 1));
   return enqueue_readback(c);
@@ -435,7 +435,7 @@ int initialise(cncpd_ctx* c) {
   } else {
     TRY(enqueue_lead(c, c->dd, c->hd, c->RP, c->d_red_prefix));
     TRY(enqueue_mode_m(c, n));
-    CU(launch_objective(lc, c->dd, c->hd, c->fp64, c->RP, 1));
+    CU(launch_objective(lc, c->dd, c->hd, c->fp64, c->RP, 1, 0));
   }
   TRY(enqueue_readback(c));
   TRY(sync(c));
@@ -782,6 +782,16 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
   CTRY(dalloc(c, (void**)&c->A1, off * c->fsz));
   CTRY(dalloc(c, (void**)&c->A2, off * c->fsz));
   CTRY(dalloc(c, (void**)&c->AS, off * c->fsz));
+  const size_t rr = (size_t)c->Rmax * c->Rmax;
+  CTRY(dalloc(c, (void**)&d.Gbase, (size_t)K * N * rr * sizeof(double)));
+  CTRY(dalloc(c, &d.Hbase, (size_t)K * rr * c->fsz));
+  for (int n = 0; n < N; ++n) {
+    int64_t imax = 0;
+    for (int k = 0; k < K; ++k) imax = std::max<int64_t>(imax, c->dim(k, n));
+    d.gr[n] = gram_chunk_rows(c->RP, imax);
+    d.gnc[n] = (int)((imax + d.gr[n] - 1) / d.gr[n]);
+    CTRY(dalloc(c, (void**)&d.Gp[n], (size_t)K * d.gnc[n] * rr * sizeof(double)));
+  }
   for (int k = 0; k < K; ++k)
     for (int n = 0; n < N; ++n) {
       d.U1[k][n] = c->U1p(k, n);
@@ -789,9 +799,7 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
       void* m = nullptr;
       CTRY(dalloc(c, &m, (size_t)c->dim(k, n) * R[k] * c->fsz));
       d.M[k][n] = m;
-      double* g = nullptr;
-      CTRY(dalloc(c, (void**)&g, (size_t)R[k] * R[k] * sizeof(double)));
-      d.G[k][n] = g;
+      d.G[k][n] = d.Gbase + ((size_t)k * N + n) * rr;
     }
   for (int k = 0; k < K; ++k) {
     void* p = nullptr;
@@ -803,8 +811,7 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
       CTRY(dalloc(c, &p, (size_t)d.trail_cols[k] * R[k] * c->fsz));
       d.Pt[k] = p;
     }
-    CTRY(dalloc(c, &p, (size_t)R[k] * R[k] * c->fsz));
-    d.H[k] = p;
+    d.H[k] = static_cast<char*>(d.Hbase) + (size_t)k * rr * c->fsz;
   }
   // TMA descriptors of X for the FP32 kernels (two box shapes per block)
   if (st == ST_F32 && tensor_map_encoder()) {
@@ -957,7 +964,7 @@ int cncpd_objective_grad(cncpd_t h, double* F, void* const* gradU, void* const* 
     for (int n = 0; n < h->N; ++n) CU(launch_collapsed_m(lc, h->dd, h->hd, h->fp64, n));
   } else {
     TRY(all_modes_m(h));
-    CU(launch_objective(lc, h->dd, h->hd, h->fp64, h->RP, 1));
+    CU(launch_objective(lc, h->dd, h->hd, h->fp64, h->RP, 1, 0));
   }
   TRY(enqueue_readback(h));
   TRY(sync(h));
@@ -1006,7 +1013,7 @@ int cncpd_global_fit(cncpd_t h, double* fit) {
   if (r == CNCPD_OK) r = enqueue_mode_m(h, h->N - 1);
   h->lra = was_lra;
   TRY(r);
-  CU(launch_objective(lc, h->dd, h->hd, h->fp64, h->RP, 0));
+  CU(launch_objective(lc, h->dd, h->hd, h->fp64, h->RP, 0, 0));
   std::vector<double> rel(h->K);
   CU(cudaMemcpyAsync(rel.data(), h->sc->out_relk, h->K * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   TRY(sync(h));
@@ -1049,6 +1056,13 @@ int cncpd_lra(cncpd_t h, const int* R_tilde, const void* const* Ut0, cncpd_dtype
   DevDesc& a = h->hd_als;
   a = h->hd;
   a.Rmax = rtmax;
+  // ALS Grams are formed by one CTA per factor (no chunk partials, no arenas)
+  a.Gbase = nullptr;
+  a.Hbase = nullptr;
+  for (int n = 0; n < N; ++n) {
+    a.Gp[n] = nullptr;
+    a.gr[n] = a.gnc[n] = 0;
+  }
   for (int k = 0; k < K; ++k) {
     a.R[k] = a.Rt[k] = R_tilde[k];
     for (int n = 0; n < N; ++n) {

@@ -102,6 +102,15 @@ struct DevDesc {
   int pad1;
   DevScalars* sc;
   int* err;                            // device error word (bounded waits, bad state)
+  // Grams and H live in arenas: G^(m,k) = Gbase + (k*N + m)*Rmax^2, H^(k) = Hbase + k*Rmax^2
+  double* Gbase;
+  void* Hbase;
+  // Gram partials of each mode (null: Grams are formed by one CTA per factor).
+  // Rows of U^(n,k) are cut into chunks of gr[n] rows; chunk c of block k
+  // holds the FP64-stored partial sums at Gp[n] + (k*gnc[n] + c)*Rmax^2.
+  double* Gp[CNCPD_NMAX];
+  int gr[CNCPD_NMAX];
+  int gnc[CNCPD_NMAX];
 };
 
 // -------------------------------------------------------------- helpers ----
@@ -162,7 +171,7 @@ cudaError_t launch_lead_contract(const LaunchCfg& c, const DevDesc* d_desc, cons
                                  const int64_t* d_red_prefix);
 int lead_cpt(int fp64, int RP);
 bool tma_rank_supported(int RP);
-cudaError_t launch_reduce_splits(const LaunchCfg& c, const DevDesc* d_desc, int fp64, const int64_t* d_red_prefix);
+cudaError_t launch_reduce_splits(const LaunchCfg& c, const DevDesc& h_desc, int fp64);
 cudaError_t launch_trailing_tma(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int RP);
 cudaError_t launch_lead_tma(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int RP);
 cudaError_t launch_level2(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int RP, int n);
@@ -177,10 +186,14 @@ cudaError_t launch_lipschitz(const LaunchCfg& c, const DevDesc* d_desc, const De
                              int prev);
 cudaError_t launch_update(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int RP, int n,
                           int use_w, double delta_w, int use_core);
-// commit = 1: write F/relerr/core term of the solver state; 0: only out_relk against xnorm2_orig
-cudaError_t launch_objective(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int RP, int commit);
+// commit = 1: write F/relerr/core term of the solver state; 0: only out_relk against xnorm2_orig.
+// reduce_last = 1: the Gram of the last mode is first summed from the chunk values the update left.
+cudaError_t launch_objective(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int RP, int commit,
+                             int reduce_last);
 cudaError_t launch_core_update(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int use_w, double delta_w);
-cudaError_t launch_iter_begin(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc);
+cudaError_t launch_iter_begin(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int use_core);
+// Rows per Gram chunk of a mode with at most imax rows (the rows of one update CTA).
+int gram_chunk_rows(int RP, int64_t imax);
 cudaError_t launch_redo_prepare(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc);
 // Quantise a rows x cols tensor (C order) into storage with row pitch `pitch` (padding zeroed).
 cudaError_t launch_quantize(cudaStream_t s, const void* src, int src_f64, void* dst, void* dst_lo, int st,

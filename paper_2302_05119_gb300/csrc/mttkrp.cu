@@ -318,34 +318,49 @@ k_lead_contract(const DevDesc* __restrict__ d) {
 // thread group g (of 8) adds splits g, g + 8, ... and the 8 group sums are
 // added in group order (fixed order: deterministic).
 template <typename T>
-__global__ void __launch_bounds__(256) k_reduce_splits(const DevDesc* __restrict__ d, const int64_t* __restrict__ prefix) {
+struct SplitArgs {
+  int K, pad;
+  int64_t prefix[CNCPD_KMAX + 1];  // first output element of each block
+  int64_t stride[CNCPD_KMAX];      // elements per split (trail_cols * R)
+  int nsplit[CNCPD_KMAX];
+  const T* part[CNCPD_KMAX];
+  T* out[CNCPD_KMAX];
+};
+
+// One CTA = 32 consecutive output elements x 8 split groups; group g adds
+// splits g, g+8, ... in order, then the 8 group sums are added in group order.
+template <typename T>
+__global__ void __launch_bounds__(256) k_reduce_splits(const __grid_constant__ SplitArgs<T> a) {
   __shared__ T red[8][32];
-  const int K = d->K;
-  const int64_t total = prefix[K];
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-  for (int64_t e0 = (int64_t)blockIdx.x * 32; e0 < total; e0 += (int64_t)gridDim.x * 32) {
-    const int64_t e = e0 + lane;
-    T s = T(0);
-    if (e < total) {
-      int k = 0;
-      while (prefix[k + 1] <= e) ++k;
-      const int64_t local = e - prefix[k];
-      const int64_t stride = d->trail_cols[k] * d->R[k];
-      const T* part = reinterpret_cast<const T*>(d->partial) + d->partial_off[k] + local;
-      const int ns = d->nsplit[k];
-#pragma unroll 4
-      for (int i = g; i < ns; i += 8) s += part[(int64_t)i * stride];
+  const int64_t e = (int64_t)blockIdx.x * 32 + lane;
+  const int64_t total = a.prefix[a.K];
+  int k = 0;
+  if (e < total)
+    while (a.prefix[k + 1] <= e) ++k;
+  T s = T(0);
+  if (e < total) {
+    const T* part = a.part[k] + (e - a.prefix[k]);
+    const int64_t stride = a.stride[k];
+    const int ns = a.nsplit[k];
+    int i = g;
+    for (; i + 24 < ns; i += 32) {
+      const T x0 = part[(int64_t)i * stride], x1 = part[(int64_t)(i + 8) * stride];
+      const T x2 = part[(int64_t)(i + 16) * stride], x3 = part[(int64_t)(i + 24) * stride];
+      s += x0;
+      s += x1;
+      s += x2;
+      s += x3;
     }
-    red[g][lane] = s;
-    __syncthreads();
-    if (g == 0 && e < total) {
-      T t = red[0][lane];
-      for (int q = 1; q < 8; ++q) t += red[q][lane];
-      int k = 0;
-      while (prefix[k + 1] <= e) ++k;
-      reinterpret_cast<T*>(d->Pt[k])[e - prefix[k]] = t;
-    }
-    __syncthreads();
+    for (; i < ns; i += 8) s += part[(int64_t)i * stride];
+  }
+  red[g][lane] = s;
+  __syncthreads();
+  if (g == 0 && e < total) {
+    T t = red[0][lane];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) t += red[q][lane];
+    a.out[k][e - a.prefix[k]] = t;
   }
 }
 
@@ -440,10 +455,26 @@ static cudaError_t trailing_impl(const LaunchCfg& c, const DevDesc* dd, const De
   return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_splits(const LaunchCfg& c, const DevDesc* dd, int fp64, const int64_t* d_red_prefix) {
-  if (fp64) k_reduce_splits<double><<<c.num_sms * 8, 256, 0, c.stream>>>(dd, d_red_prefix);
-  else k_reduce_splits<float><<<c.num_sms * 8, 256, 0, c.stream>>>(dd, d_red_prefix);
+template <typename T>
+static cudaError_t reduce_splits_impl(const LaunchCfg& c, const DevDesc& hd) {
+  SplitArgs<T> a{};
+  a.K = hd.K;
+  a.prefix[0] = 0;
+  for (int k = 0; k < hd.K; ++k) {
+    a.stride[k] = hd.trail_cols[k] * hd.R[k];
+    a.prefix[k + 1] = a.prefix[k] + a.stride[k];
+    a.nsplit[k] = hd.nsplit[k];
+    a.part[k] = reinterpret_cast<const T*>(hd.partial) + hd.partial_off[k];
+    a.out[k] = reinterpret_cast<T*>(hd.Pt[k]);
+  }
+  const int64_t blocks = (a.prefix[hd.K] + 31) / 32;
+  if (blocks == 0) return cudaSuccess;
+  k_reduce_splits<T><<<(unsigned)blocks, 256, 0, c.stream>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_splits(const LaunchCfg& c, const DevDesc& hd, int fp64) {
+  return fp64 ? reduce_splits_impl<double>(c, hd) : reduce_splits_impl<float>(c, hd);
 }
 
 template <int ST, typename T, int RP>
@@ -464,7 +495,8 @@ static cudaError_t lead_impl(const LaunchCfg& c, const DevDesc* dd, const DevDes
   kern<<<grid, 256, smem, c.stream>>>(dd);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return launch_reduce_splits(c, dd, sizeof(T) == 8, d_red_prefix);
+  (void)d_red_prefix;
+  return launch_reduce_splits(c, hd, sizeof(T) == 8);
 }
 
 int lead_cpt(int fp64, int RP) {
@@ -545,9 +577,8 @@ cudaError_t launch_lead_contract(const LaunchCfg& c, const DevDesc* dd, const De
 cudaError_t launch_level2(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int RP, int n) {
   (void)RP;
   const int gsize = (n < hd.h) ? hd.h : hd.N - hd.h;
-  int64_t imax = 0, omax = 0;
+  int64_t imax = 0;
   for (int k = 0; k < hd.K; ++k) imax = hd.dims[k][n] > imax ? hd.dims[k][n] : imax;
-  (void)omax;
   if (gsize == 2) return launch_mode_prep(c, dd, hd, fp64, n, 0, -1, 2);
   dim3 grid((unsigned)imax, hd.K);
   if (fp64) k_level2<double><<<grid, 256, 0, c.stream>>>(dd, n);

@@ -9,38 +9,91 @@
 namespace cncpd {
 
 // ---------------------------------------------------------------------------
-// Largest eigenvalue of a symmetric PSD R x R matrix (R <= 64), called by a
-// whole CTA.  ||H||_2 of Eqs. eqLipsLd / eqLipsLu.  Normalised repeated
-// squaring A <- A^2 / tr(A^2) in FP32 converges to the projector on the
-// leading eigenvector (ratios of eigenvalues are raised to the power 2^s).
-// The FP64 value is the Rayleigh quotient of H at a column of the limit.
-// Returns 0 for a zero matrix and propagates NaN/Inf.
+// Per-mode views passed to the small kernels by value.  Every pointer and size
+// a kernel needs is resolved on the host, so a kernel starts by issuing its
+// data loads instead of walking the device descriptor through dependent
+// global loads.
 // ---------------------------------------------------------------------------
-// Shared-memory layout of lmax_psd for an R x R problem (dynamic smem):
-// Hs (R*R doubles), v, w (R doubles each), A, B (R*R floats each), red (32 floats).
-__host__ __device__ inline size_t lmax_smem_bytes(int R) {
-  return (size_t)R * R * 8 + 2 * (size_t)R * 8 + 2 * (size_t)R * R * 4 + 32 * 4 + 16;
-}
-
-struct LmaxScratch {
-  double* Hs;
-  double* v;
-  double* w;
-  float* A;
-  float* B;
-  float* red;
-  __device__ void carve(unsigned char* base, int R) {
-    Hs = reinterpret_cast<double*>(base);
-    v = Hs + R * R;
-    w = v + R;
-    A = reinterpret_cast<float*>(w + R);
-    B = A + R * R;
-    red = B + R * R;
-  }
+template <typename T>
+struct LipArgs {            // H^(n,k) and L^(n,k) for every block
+  int K, N, n, prev;        // prev >= 0: first reduce the Gram partials of mode prev
+  int use_core, want_L, rr, gnc_prev;
+  int gr_prev, pad;
+  DevScalars* sc;
+  double* G;                // Gram arena: G^(m,k) at G + (k*N + m)*rr
+  T* H;                     // H arena: H^(k) at H + k*rr
+  const double* Gp_prev;    // partials of mode prev
+  int R[CNCPD_KMAX];
+  int Iprev[CNCPD_KMAX];
 };
 
-template <typename TT>
-__device__ double lmax_psd(const double* Hs, int R, LmaxScratch* s) {
+template <typename T>
+struct PairArgs {           // level 2 of a two-mode group
+  int K, first, ni, pad;
+  int In[CNCPD_KMAX], Io[CNCPD_KMAX], R[CNCPD_KMAX];
+  int cta0[CNCPD_KMAX + 1];  // first CTA of each block
+  const T* P[CNCPD_KMAX];
+  const T* W[CNCPD_KMAX];
+  T* M[CNCPD_KMAX];
+};
+
+template <typename T>
+struct UpdArgs {            // fused APG update of mode n
+  int K, n, Ln, nonneg;
+  int use_w, use_core, gr, gnc;
+  int rr, pad;
+  double delta_w;
+  DevScalars* sc;
+  double* Gp;               // Gram partials of mode n (written)
+  int R[CNCPD_KMAX];
+  int I[CNCPD_KMAX];
+  T* U1[CNCPD_KMAX];
+  T* U2[CNCPD_KMAX];
+  const T* M[CNCPD_KMAX];
+  const T* H[CNCPD_KMAX];
+};
+
+template <typename T>
+struct ObjArgs {            // objective with the last mode just updated
+  int K, N, rr, gnc;
+  int gr, commit, reduce_last, pad;
+  DevScalars* sc;
+  double* G;
+  const double* Gp_last;
+  int R[CNCPD_KMAX];
+  int I[CNCPD_KMAX];
+  const T* M[CNCPD_KMAX];
+  const T* U[CNCPD_KMAX];
+};
+
+// ---------------------------------------------------------------------------
+// Largest eigenvalue of a symmetric PSD R x R matrix (R <= RP), called by a
+// whole CTA: ||H||_2 of Eqs. eqLipsLd / eqLipsLu.  Normalised repeated
+// squaring A <- A^2 / tr(A^2) in FP32 on the zero-padded RP x RP matrix
+// converges to the projector on the leading eigenvector (eigenvalue ratios
+// are raised to the power 2^s); the value is the Rayleigh quotient of H at a
+// column of that limit, evaluated in TT (the factor precision), so its error
+// is quadratic in the FP32 accuracy of the eigenvector.  Returns 0 for a zero
+// matrix and propagates NaN/Inf.
+// ---------------------------------------------------------------------------
+template <int RP>
+struct LmaxSmem {
+  float A[RP * RP];
+  float B[RP * RP];
+  double v[RP];
+  double w[RP];
+  float red[32];
+};
+
+// Shared memory of one Lipschitz CTA: H in FP64, then the squaring scratch.
+template <int RP>
+__host__ __device__ constexpr size_t lip_smem_bytes() {
+  return (size_t)RP * RP * sizeof(double) + sizeof(LmaxSmem<RP>);
+}
+
+template <typename TT, int RP>
+__device__ double lmax_rp(const double* Hs, int R, LmaxSmem<RP>* s) {
+  constexpr int RR = RP * RP;
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
   const int nt = blockDim.x * blockDim.y;
   __syncthreads();
@@ -48,20 +101,24 @@ __device__ double lmax_psd(const double* Hs, int R, LmaxScratch* s) {
   for (int i = 0; i < R; ++i) tr += Hs[i * R + i];
   if (!isfinite(tr)) return tr;
   if (!(tr > 0.0)) return 0.0;
-  const int RR = R * R;
   const double itr = 1.0 / tr;
-  for (int e = tid; e < RR; e += nt) s->A[e] = (float)(Hs[e] * itr);
+  for (int e = tid; e < RR; e += nt) {
+    const int i = e / RP, j = e % RP;
+    s->A[e] = (i < R && j < R) ? (float)(Hs[i * R + j] * itr) : 0.f;
+  }
   __syncthreads();
   for (int it = 0; it < 32; ++it) {
     for (int e = tid; e < RR; e += nt) {
-      const int i = e / R, j = e % R;
+      const int i = e / RP, j = e % RP;
       float acc = 0.f;
-      for (int l = 0; l < R; ++l) acc = fmaf(s->A[i * R + l], s->A[l * R + j], acc);
+#pragma unroll
+      for (int l = 0; l < RP; ++l) acc = fmaf(s->A[i * RP + l], s->A[l * RP + j], acc);
       s->B[e] = acc;
     }
     __syncthreads();
     float trb = 0.f;
-    for (int i = 0; i < R; ++i) trb += s->B[i * R + i];
+#pragma unroll
+    for (int i = 0; i < RP; ++i) trb += s->B[i * RP + i];
     float dmax = 0.f;
     if (trb > 0.f) {
       for (int e = tid; e < RR; e += nt) {
@@ -70,7 +127,7 @@ __device__ double lmax_psd(const double* Hs, int R, LmaxScratch* s) {
         s->A[e] = nv;
       }
     }
-    if ((it & 3) != 3 && (trb > 0.f)) {
+    if ((it & 3) != 3 && trb > 0.f) {
       __syncthreads();
       continue;
     }
@@ -83,24 +140,17 @@ __device__ double lmax_psd(const double* Hs, int R, LmaxScratch* s) {
     __syncthreads();
     if (!(trb > 0.f) || m < 4e-6f) break;
   }
-  // v: column of the limit with the largest diagonal entry (FP32 accuracy in
-  // every non-leading direction).  One FP64 product y = H v and the Rayleigh
-  // quotient v^T y / v^T v, reduced by warp 0, give L with error quadratic in
-  // that accuracy.  (When the two largest eigenvalues agree to within FP32
-  // resolution the squaring still ends in a rank-one limit, and the error is
-  // bounded by their relative gap.)
+  // v: the column of the limit with the largest diagonal entry
   int jm = 0;
   float dm = -1.f;
   for (int i = 0; i < R; ++i)
-    if (s->A[i * R + i] > dm) { dm = s->A[i * R + i]; jm = i; }
-  // (TT = float on the FP32 path: L to FP32 accuracy is ample there and
-  // FP64 arithmetic is slow on this part; TT = double on the FP64 path.)
+    if (s->A[i * RP + i] > dm) { dm = s->A[i * RP + i]; jm = i; }
   for (int i = tid; i < R; i += nt) {
-    const TT vi = (TT)s->A[i * R + jm];
-    TT a = TT(0);
-    for (int l = 0; l < R; ++l) a = fma((TT)Hs[i * R + l], (TT)s->A[l * R + jm], a);
-    s->v[i] = (double)(vi * a);   // v_i (H v)_i
-    s->w[i] = (double)(vi * vi);  // v_i^2
+    const TT vi = (TT)s->A[i * RP + jm];
+    TT acc = TT(0);
+    for (int l = 0; l < R; ++l) acc = fma((TT)Hs[i * R + l], (TT)s->A[l * RP + jm], acc);
+    s->v[i] = (double)(vi * acc);  // v_i (H v)_i
+    s->w[i] = (double)(vi * vi);   // v_i^2
   }
   __syncthreads();
   if (tid < 32) {
@@ -137,28 +187,77 @@ __device__ __forceinline__ TT extrap_weight(double w_hat, int have_prev, double 
 }
 
 // ---------------------------------------------------------------------------
-// Gram G = U^T U (Table II operation 1) of one I x R factor, computed by a
-// whole CTA: U is staged through shared memory GT rows at a time; for every
-// (a, b) an FMA chain in the factor type runs over each tile and the tile
-// sums are added in FP64 in order.  Every kernel that forms a Gram calls
-// this routine, so all of them give bit-identical results.
+// Grams G = U^T U (Table II operation 1).  The rows of U^(n,k) are cut into
+// chunks of gr[n] rows.  For every chunk and every entry (a, b) an FMA chain
+// in the factor type runs over the chunk's rows in order and is stored in
+// FP64; the Gram is the sum of the chunk values in chunk order, in FP64.  The
+// update kernel writes the chunk values of the mode it has just updated, the
+// next kernel that needs the Gram adds them up; k_gram_chunks /
+// k_gram_reduce do both for whole factors.  Every path follows the same
+// order, so a Gram is bit-identical wherever it is formed.
 // ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T gram_chain(const T* U, int64_t row0, int rows, int R, int a, int b) {
+  // plain loads: the update kernel reads rows it has just written
+  T s = T(0);
+  for (int i = 0; i < rows; ++i) s = fma(U[(row0 + i) * R + a], U[(row0 + i) * R + b], s);
+  return s;
+}
+
+// Sum of the first nch chunk values of entry p (stride rr), in chunk order.
+__device__ __forceinline__ double gram_sum(const double* __restrict__ gp, int nch, int rr, int p) {
+  double s = 0.0;
+  int c = 0;
+  for (; c + 4 <= nch; c += 4) {
+    const double x0 = gp[(size_t)c * rr + p], x1 = gp[(size_t)(c + 1) * rr + p];
+    const double x2 = gp[(size_t)(c + 2) * rr + p], x3 = gp[(size_t)(c + 3) * rr + p];
+    s += x0;
+    s += x1;
+    s += x2;
+    s += x3;
+  }
+  for (; c < nch; ++c) s += gp[(size_t)c * rr + p];
+  return s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gram_chunks(const DevDesc* __restrict__ d, int n0, int n1) {
+  const int nm = n1 - n0;
+  const int k = blockIdx.y / nm, n = n0 + blockIdx.y % nm;
+  const int c = blockIdx.x;
+  const int gr = d->gr[n];
+  const int64_t I = d->dims[k][n];
+  const int64_t row0 = (int64_t)c * gr;
+  if (c >= d->gnc[n] || row0 >= I) return;
+  const int rows = (int)min((int64_t)gr, I - row0);
+  const int R = d->R[k];
+  const int rr = d->Rmax * d->Rmax;
+  const T* U = reinterpret_cast<const T*>(d->U1[k][n]);
+  double* out = d->Gp[n] + ((size_t)k * d->gnc[n] + c) * rr;
+  for (int p = threadIdx.x; p < R * R; p += blockDim.x) out[p] = (double)gram_chain<T>(U, row0, rows, R, p / R, p % R);
+}
+
+__global__ void __launch_bounds__(256) k_gram_reduce(const DevDesc* __restrict__ d, int n0, int n1) {
+  const int nm = n1 - n0;
+  const int k = blockIdx.x / nm, n = n0 + blockIdx.x % nm;
+  const int R = d->R[k];
+  const int rr = d->Rmax * d->Rmax;
+  const int nch = (int)((d->dims[k][n] + d->gr[n] - 1) / d->gr[n]);
+  const double* gp = d->Gp[n] + (size_t)k * d->gnc[n] * rr;
+  double* G = d->G[k][n];
+  for (int p = threadIdx.x; p < R * R; p += blockDim.x) G[p] = gram_sum(gp, nch, rr, p);
+}
+
+// Gram of one I x R factor by one CTA (factors without chunk partials: the
+// LRA factors and the ALS step): U staged through shared memory, FMA chains
+// in the factor type over tiles of GRAM_TILE rows, tile sums added in FP64.
 constexpr int GRAM_TILE = 64;
 
 template <typename T>
 __device__ void block_gram(const T* __restrict__ U, int64_t I, int R, double* __restrict__ G, T* buf, int cap_rows) {
-  // buf holds cap_rows rows (a multiple of GRAM_TILE); rows are staged in as
-  // few round trips as the buffer allows.  For small R each pair's rows are
-  // split into SL = max(1, 256 / R^2) interleaved slices (an FMA chain in the
-  // factor type each); per tile the slice sums are added in slice order in
-  // FP64, tiles in order.  The order depends only on R, so every kernel that
-  // calls this routine gets bit-identical Grams.
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
   const int nt = blockDim.x * blockDim.y;
   const int RR = R * R;
-  const int SL = max(1, 256 / RR);
-  const int items = RR * SL;  // <= 256 whenever SL > 1
-  __shared__ double slice_sum[256];
   double acc[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) acc[q] = 0.0;
@@ -170,38 +269,16 @@ __device__ void block_gram(const T* __restrict__ U, int64_t I, int R, double* __
     for (int t0 = 0; t0 < ns; t0 += GRAM_TILE) {
       const int n = min(GRAM_TILE, ns - t0);
       const T* tile = buf + t0 * R;
-      if (SL == 1) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int p = q * nt + tid;
-          if (p < RR) {
-            const int a = p / R, b = p % R;
-            T s = T(0);
-#pragma unroll 4
-            for (int i = 0; i < n; ++i) s = fma(tile[i * R + a], tile[i * R + b], s);
-            acc[q] += (double)s;
-          }
-        }
-      } else {
-        for (int wi = tid; wi < items; wi += nt) {
-          const int p = wi / SL, sl = wi % SL;
+      for (int q = 0; q < 16; ++q) {
+        const int p = q * nt + tid;
+        if (p < RR) {
           const int a = p / R, b = p % R;
           T s = T(0);
 #pragma unroll 4
-          for (int i = sl; i < n; i += SL) s = fma(tile[i * R + a], tile[i * R + b], s);
-          slice_sum[wi] = (double)s;
+          for (int i = 0; i < n; ++i) s = fma(tile[i * R + a], tile[i * R + b], s);
+          acc[q] += (double)s;
         }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int p = q * nt + tid;
-          if (p < RR) {
-            double t = 0.0;
-            for (int sl = 0; sl < SL; ++sl) t += slice_sum[p * SL + sl];
-            acc[q] += t;
-          }
-        }
-        __syncthreads();
       }
     }
   }
@@ -213,10 +290,8 @@ __device__ void block_gram(const T* __restrict__ U, int64_t I, int R, double* __
   __syncthreads();
 }
 
-// Grams of modes [n_begin, n_end) of every block; which = 0: the factors
-// U1, which = 1: the LRA factors U~.  One CTA per (block, mode).
 template <typename T>
-__global__ void __launch_bounds__(256) k_gram(const DevDesc* __restrict__ d, int n_begin, int n_end, int which) {
+__global__ void __launch_bounds__(256) k_gram_block(const DevDesc* __restrict__ d, int n_begin, int n_end, int which) {
   constexpr int CAP = (32768 / (int)sizeof(T)) / CNCPD_RMAX / GRAM_TILE * GRAM_TILE;
   __shared__ T tile[CAP * CNCPD_RMAX];
   const int nm = n_end - n_begin;
@@ -231,107 +306,158 @@ __global__ void __launch_bounds__(256) k_gram(const DevDesc* __restrict__ d, int
 cudaError_t launch_gram(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int n_begin, int n_end,
                         int which) {
   if (n_end <= n_begin) return cudaSuccess;
-  const int grid = hd.K * (n_end - n_begin);
-  if (fp64) k_gram<double><<<grid, 256, 0, c.stream>>>(dd, n_begin, n_end, which);
-  else k_gram<float><<<grid, 256, 0, c.stream>>>(dd, n_begin, n_end, which);
+  const int nm = n_end - n_begin;
+  if (which == 0 && hd.Gp[n_begin]) {
+    int cmax = 1;
+    for (int n = n_begin; n < n_end; ++n) cmax = std::max(cmax, hd.gnc[n]);
+    dim3 grid((unsigned)cmax, (unsigned)(hd.K * nm));
+    if (fp64) k_gram_chunks<double><<<grid, 256, 0, c.stream>>>(dd, n_begin, n_end);
+    else k_gram_chunks<float><<<grid, 256, 0, c.stream>>>(dd, n_begin, n_end);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_gram_reduce<<<hd.K * nm, 256, 0, c.stream>>>(dd, n_begin, n_end);
+    return cudaGetLastError();
+  }
+  const int grid = hd.K * nm;
+  if (fp64) k_gram_block<double><<<grid, 256, 0, c.stream>>>(dd, n_begin, n_end, which);
+  else k_gram_block<float><<<grid, 256, 0, c.stream>>>(dd, n_begin, n_end, which);
   return cudaGetLastError();
+}
+
+// Rows per Gram chunk of mode n: the rows one update CTA handles.
+int gram_chunk_rows(int RP, int64_t imax) {
+  const int ty = std::max(1, 128 / RP);
+  const int64_t passes = std::max<int64_t>(1, ((imax + ty - 1) / ty + 31) / 32);
+  return (int)(ty * passes);
 }
 
 // ---------------------------------------------------------------------------
 // H^(n,k) = D (*_{m != n} G^(m,k)) D (Eq. solapgU first term; Table II
-// operation 4) and L_u^(n,k) = ||H||_2 (Eq. eqLipsLu).  One CTA per block.
+// operation 4) and L_u^(n,k) = ||H||_2 (Eq. eqLipsLu).  One CTA per block;
+// the Gram of the mode updated just before is first summed from its chunks.
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ void lipschitz_body(const DevDesc* __restrict__ d, int k, int n, int use_core, int want_L, int prev,
-                               int gram_rows, unsigned char* smem_raw) {
-  const int R = d->R[k], N = d->N;
-  if (prev >= 0)  // Gram of the mode updated just before (Table II operation 1)
-    block_gram<T>(reinterpret_cast<const T*>(d->U1[k][prev]), d->dims[k][prev], R, d->G[k][prev],
-                  reinterpret_cast<T*>(smem_raw), gram_rows);
-  LmaxScratch scr;
-  scr.carve(smem_raw, R);
-  double* Hs = scr.Hs;
-  DevScalars* sc = d->sc;
-  T* Hout = reinterpret_cast<T*>(d->H[k]);
-  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+template <typename T, int RP>
+__device__ void lip_body(const LipArgs<T>& a, int k, unsigned char* smem) {
+  double* Hs = reinterpret_cast<double*>(smem);
+  LmaxSmem<RP>* ls = reinterpret_cast<LmaxSmem<RP>*>(smem + (size_t)RP * RP * sizeof(double));
+  const int R = a.R[k], N = a.N, rr = a.rr, n = a.n, prev = a.prev;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double* Gk = a.G + (size_t)k * N * rr;
+  DevScalars* sc = a.sc;
+  const int nch = prev >= 0 ? (a.Iprev[k] + a.gr_prev - 1) / a.gr_prev : 0;
+  const double* gp = prev >= 0 ? a.Gp_prev + (size_t)k * a.gnc_prev * rr : nullptr;
+  for (int p = tid; p < R * R; p += nt) {
+    double gm[CNCPD_NMAX];
+#pragma unroll
+    for (int m = 0; m < CNCPD_NMAX; ++m) gm[m] = (m < N && m != n && m != prev) ? Gk[(size_t)m * rr + p] : 1.0;
+    if (prev >= 0) {
+      const double g = gram_sum(gp, nch, rr, p);
+      Gk[(size_t)prev * rr + p] = g;
+#pragma unroll
+      for (int m = 0; m < CNCPD_NMAX; ++m)
+        if (m == prev && m != n) gm[m] = g;
+    }
     double h = 1.0;
-    for (int m = 0; m < N; ++m)
-      if (m != n) h *= d->G[k][m][e];
-    if (use_core) h *= sc->lam1[k][e / R] * sc->lam1[k][e % R];
-    Hs[e] = h;
-    Hout[e] = (T)h;
+#pragma unroll
+    for (int m = 0; m < CNCPD_NMAX; ++m)
+      if (m < N && m != n) h *= gm[m];
+    if (a.use_core) h *= sc->lam1[k][p / R] * sc->lam1[k][p % R];
+    Hs[p] = h;
+    a.H[(size_t)k * rr + p] = (T)h;
   }
-  if (!want_L) return;
-  const double L = lmax_psd<T>(Hs, R, &scr);
-  if (threadIdx.x == 0) {
+  if (!a.want_L) return;
+  const double L = lmax_rp<T, RP>(Hs, R, ls);
+  if (tid == 0) {
     sc->Lcur_u[n][k] = L;
     if (!isfinite(L)) atomicExch(&sc->nonfinite, 1);
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_lipschitz(const DevDesc* __restrict__ d, int n, int use_core, int want_L,
-                                                   int prev, int gram_rows) {
+template <typename T, int RP>
+__global__ void __launch_bounds__(256) k_lipschitz(const __grid_constant__ LipArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  lipschitz_body<T>(d, blockIdx.x, n, use_core, want_L, prev, gram_rows, smem_raw);
+  lip_body<T, RP>(a, blockIdx.x, smem_raw);
 }
 
-// Two-mode groups (third- and fourth-order tensors).  With n first in its
-// group, P[i_n][b][r] is contiguous per i_n:  M[i_n, r] = sum_b P W[b, r].
-// With n last, P[a][i_n][r]:  M[i_n, r] = sum_a P W[a, r], and ni
-// consecutive i_n of one a are contiguous.  W is the other mode's factor
-// (read through the read-only cache); a CTA produces ni rows of M.
+// Level 2 of a two-mode group (third- and fourth-order tensors).  With n
+// first in its group, P[i_n][b][r] is contiguous per i_n:
+//   M[i_n, r] = sum_b P[i_n, b, r] W[b, r];
+// thread t keeps r = t mod R and strides over (b, r) by a multiple of R; a
+// CTA produces ni rows.  With n last, P[a][i_n][r]:
+//   M[i_n, r] = sum_a P[a, i_n, r] W[a, r];
+// a CTA produces ni*R consecutive outputs, with the a range cut into slices.
+// Partial sums are added in a fixed order.
 template <typename T>
-__device__ void level2_pair_body(const DevDesc* __restrict__ d, int k, int bx, int n, int ni_max) {
-  __shared__ T red[256];
-  const int N = d->N, h = d->h;
-  const int m0 = (n < h) ? 0 : h;
-  const int other = (n == m0) ? n + 1 : m0;   // the group's other mode
-  const bool first = (n == m0);
-  const int In = (int)d->dims[k][n];
-  const int Io = (int)d->dims[k][other];
-  const int R = d->R[k];
-  const int i0 = bx * ni_max;
+__device__ void pair_body(const PairArgs<T>& a, int b, T* red) {
+  int k = 0;
+  while (k + 1 < a.K && a.cta0[k + 1] <= b) ++k;
+  const int bx = b - a.cta0[k];
+  const int In = a.In[k], Io = a.Io[k], R = a.R[k];
+  const int i0 = bx * a.ni;
   if (i0 >= In) return;
-  const int ni = min(ni_max, In - i0);
-  const T* P = reinterpret_cast<const T*>((n < h) ? d->Pl[k] : d->Pt[k]);
-  const T* W = reinterpret_cast<const T*>(d->U1[k][other]);
-  T* M = reinterpret_cast<T*>(d->M[k][n]);
+  const int ni = min(a.ni, In - i0);
+  const T* __restrict__ P = a.P[k];
+  const T* __restrict__ W = a.W[k];
+  T* M = a.M[k];
   const int t = threadIdx.x;
-  if (first) {
+  if (a.first) {
     const int BR = Io * R;
-    const int stride = (blockDim.x / R) * R;
+    const int stride = (256 / R) * R;
     T acc[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = T(0);
     if (t < stride) {
-#pragma unroll 2
-      for (int e = t; e < BR; e += stride) {
-        const T w = __ldg(W + e);
+      int e = t;
+      for (; e + 3 * stride < BR; e += 4 * stride) {
+        const T w0 = W[e], w1 = W[e + stride], w2 = W[e + 2 * stride], w3 = W[e + 3 * stride];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (q < ni) {
+            const T* Pq = P + (int64_t)(i0 + q) * BR + e;
+            const T p0 = Pq[0], p1 = Pq[stride], p2 = Pq[2 * stride], p3 = Pq[3 * stride];
+            acc[q] = fma(p0, w0, acc[q]);
+            acc[q] = fma(p1, w1, acc[q]);
+            acc[q] = fma(p2, w2, acc[q]);
+            acc[q] = fma(p3, w3, acc[q]);
+          }
+      }
+      for (; e < BR; e += stride) {
+        const T w = W[e];
 #pragma unroll
         for (int q = 0; q < 8; ++q)
           if (q < ni) acc[q] = fma(P[(int64_t)(i0 + q) * BR + e], w, acc[q]);
       }
     }
-    for (int q = 0; q < ni; ++q) {
-      red[t] = acc[q];
-      __syncthreads();
-      if (t < R) {
-        T s = T(0);
-        for (int u = t; u < stride; u += R) s += red[u];
-        M[(int64_t)(i0 + q) * R + t] = s;
-      }
-      __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (q < ni) red[q * 256 + t] = acc[q];
+    __syncthreads();
+    for (int o = t; o < ni * R; o += 256) {
+      const int q = o / R, r = o % R;
+      T s = T(0);
+      for (int u = r; u < stride; u += R) s += red[q * 256 + u];
+      M[(int64_t)(i0 + q) * R + r] = s;
     }
   } else {
     const int JR = ni * R;
-    const int nsl = max(1, (int)blockDim.x / JR);
+    const int nsl = max(1, 256 / JR);
     const int j = t % JR, sl = t / JR;
     T acc = T(0);
     if (sl < nsl && t < nsl * JR) {
       const int r = j % R;
-#pragma unroll 8
-      for (int a = sl; a < Io; a += nsl) acc = fma(P[((int64_t)a * In + i0) * R + j], __ldg(W + a * R + r), acc);
+      const T* Pj = P + (int64_t)i0 * R + j;
+      const int64_t ps = (int64_t)In * R;
+      int x = sl;
+      for (; x + 3 * nsl < Io; x += 4 * nsl) {
+        const T p0 = Pj[(int64_t)x * ps], p1 = Pj[(int64_t)(x + nsl) * ps];
+        const T p2 = Pj[(int64_t)(x + 2 * nsl) * ps], p3 = Pj[(int64_t)(x + 3 * nsl) * ps];
+        const T w0 = W[x * R + r], w1 = W[(x + nsl) * R + r], w2 = W[(x + 2 * nsl) * R + r], w3 = W[(x + 3 * nsl) * R + r];
+        acc = fma(p0, w0, acc);
+        acc = fma(p1, w1, acc);
+        acc = fma(p2, w2, acc);
+        acc = fma(p3, w3, acc);
+      }
+      for (; x < Io; x += nsl) acc = fma(Pj[(int64_t)x * ps], W[x * R + r], acc);
     }
     red[t] = acc;
     __syncthreads();
@@ -343,30 +469,19 @@ __device__ void level2_pair_body(const DevDesc* __restrict__ d, int k, int bx, i
   }
 }
 
-// CTAs [0, nlip): H and L of mode n for block blockIdx.x; the rest: level 2
-// of mode n, nx CTAs per block.
 template <typename T>
-__global__ void __launch_bounds__(256) k_mode_prep(const DevDesc* __restrict__ d, int n, int use_core, int prev,
-                                                   int gram_rows, int nlip, int nx, int ni) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  if ((int)blockIdx.x < nlip) {
-    lipschitz_body<T>(d, blockIdx.x, n, use_core, 1, prev, gram_rows, smem_raw);
-  } else {
-    const int b = blockIdx.x - nlip;
-    level2_pair_body<T>(d, b / nx, b % nx, n, ni);
-  }
+__global__ void __launch_bounds__(256) k_level2_pair(const __grid_constant__ PairArgs<T> a) {
+  __shared__ T red[8 * 256];
+  pair_body<T>(a, blockIdx.x, red);
 }
 
-static void lipschitz_smem(const DevDesc& hd, int fp64, int* gram_rows, size_t* sm) {
-  // Gram staging: up to 32 KiB of rows (whole factor when it fits)
-  int64_t imax = 0;
-  for (int k = 0; k < hd.K; ++k)
-    for (int m = 0; m < hd.N; ++m) imax = std::max<int64_t>(imax, hd.dims[k][m]);
-  const int es = fp64 ? 8 : 4;
-  int64_t rows = std::min<int64_t>((imax + GRAM_TILE - 1) / GRAM_TILE * GRAM_TILE,
-                                   std::max<int64_t>(GRAM_TILE, (32768 / es / std::max(1, hd.Rmax)) / GRAM_TILE * GRAM_TILE));
-  *gram_rows = (int)rows;
-  *sm = std::max(lmax_smem_bytes(hd.Rmax), (size_t)rows * hd.Rmax * es);
+// CTAs [0, K): H and L of mode n, block blockIdx.x; the rest: level 2.
+template <typename T, int RP>
+__global__ void __launch_bounds__(256) k_mode_prep(const __grid_constant__ LipArgs<T> la,
+                                                   const __grid_constant__ PairArgs<T> pa) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if ((int)blockIdx.x < la.K) lip_body<T, RP>(la, blockIdx.x, smem_raw);
+  else pair_body<T>(pa, blockIdx.x - la.K, reinterpret_cast<T*>(smem_raw));
 }
 
 bool level2_is_pair(const DevDesc& hd, int n) {
@@ -374,42 +489,128 @@ bool level2_is_pair(const DevDesc& hd, int n) {
   return gsize == 2;
 }
 
+template <typename T>
+static LipArgs<T> lip_args(const DevDesc& hd, int n, int use_core, int prev, int want_L) {
+  LipArgs<T> a{};
+  a.K = hd.K;
+  a.N = hd.N;
+  a.n = n;
+  a.prev = (prev >= 0 && hd.Gp[prev]) ? prev : -1;
+  a.use_core = use_core;
+  a.want_L = want_L;
+  a.rr = hd.Rmax * hd.Rmax;
+  a.sc = hd.sc;
+  a.G = hd.Gbase;
+  a.H = reinterpret_cast<T*>(hd.Hbase);
+  if (a.prev >= 0) {
+    a.Gp_prev = hd.Gp[prev];
+    a.gnc_prev = hd.gnc[prev];
+    a.gr_prev = hd.gr[prev];
+  }
+  for (int k = 0; k < hd.K; ++k) {
+    a.R[k] = hd.R[k];
+    a.Iprev[k] = a.prev >= 0 ? (int)hd.dims[k][prev] : 0;
+  }
+  return a;
+}
+
+template <typename T>
+static PairArgs<T> pair_args(const DevDesc& hd, int n, int num_sms, int* ctas) {
+  PairArgs<T> a{};
+  const int h = hd.h;
+  const int m0 = (n < h) ? 0 : h;
+  const int other = (n == m0) ? n + 1 : m0;
+  a.K = hd.K;
+  a.first = (n == m0);
+  int64_t imax = 0;
+  for (int k = 0; k < hd.K; ++k) imax = std::max<int64_t>(imax, hd.dims[k][n]);
+  int ni;
+  if (a.first) {
+    // rows per CTA: enough CTAs to fill the GPU about four times over
+    ni = std::max(1, std::min(8, 256 / std::max(1, hd.Rmax)));
+    while (ni > 1 && ((imax + ni - 1) / ni) * hd.K < 4LL * num_sms) ni /= 2;
+  } else {
+    ni = 1;  // R outputs per CTA; the a range is cut into 256/R slices
+  }
+  a.ni = ni;
+  int tot = 0;
+  for (int k = 0; k < hd.K; ++k) {
+    a.In[k] = (int)hd.dims[k][n];
+    a.Io[k] = (int)hd.dims[k][other];
+    a.R[k] = hd.R[k];
+    a.cta0[k] = tot;
+    tot += (int)((hd.dims[k][n] + ni - 1) / ni);
+    a.P[k] = reinterpret_cast<const T*>((n < h) ? hd.Pl[k] : hd.Pt[k]);
+    a.W[k] = reinterpret_cast<const T*>(hd.U1[k][other]);
+    a.M[k] = reinterpret_cast<T*>(hd.M[k][n]);
+  }
+  a.cta0[hd.K] = tot;
+  *ctas = tot;
+  return a;
+}
+
+template <typename T, int RP>
+static cudaError_t mode_prep_impl(const LaunchCfg& c, const DevDesc& hd, int n, int use_core, int prev,
+                                  int with_level2) {
+  // with_level2: 0 = Lipschitz only, 1 = Lipschitz + level 2, 2 = level 2 only
+  int ctas = 0;
+  PairArgs<T> pa{};
+  if (with_level2) pa = pair_args<T>(hd, n, c.num_sms, &ctas);
+  if (with_level2 == 2) {
+    if (ctas == 0) return cudaSuccess;
+    k_level2_pair<T><<<ctas, 256, 0, c.stream>>>(pa);
+    return cudaGetLastError();
+  }
+  LipArgs<T> la = lip_args<T>(hd, n, use_core, prev, 1);
+  const size_t sm = std::max(lip_smem_bytes<RP>(), with_level2 ? sizeof(T) * 8 * 256 : (size_t)0);
+  if (with_level2 == 0) {
+    cudaError_t e = allow_smem(k_lipschitz<T, RP>, sm);
+    if (e != cudaSuccess) return e;
+    k_lipschitz<T, RP><<<hd.K, RP <= 16 ? 128 : 256, sm, c.stream>>>(la);
+    return cudaGetLastError();
+  }
+  cudaError_t e = allow_smem(k_mode_prep<T, RP>, sm);
+  if (e != cudaSuccess) return e;
+  k_mode_prep<T, RP><<<hd.K + ctas, 256, sm, c.stream>>>(la, pa);
+  return cudaGetLastError();
+}
+
+static int rank_bucket_of(const DevDesc& hd) { return rank_bucket(hd.Rmax); }
+
 cudaError_t launch_mode_prep(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int n, int use_core,
                              int prev, int with_level2) {
-  // with_level2: 0 = Lipschitz only, 1 = Lipschitz + level 2, 2 = level 2 only
-  int gram_rows = GRAM_TILE;
-  size_t sm = 0;
-  const int nlip = (with_level2 == 2) ? 0 : hd.K;
-  if (nlip) lipschitz_smem(hd, fp64, &gram_rows, &sm);
-  int nx = 0, ni = 1;
-  if (with_level2) {
-    int64_t imax = 0;
-    for (int k = 0; k < hd.K; ++k) imax = std::max<int64_t>(imax, hd.dims[k][n]);
-    // rows per CTA: small enough for ~4 CTAs per SM over all blocks, ni*R <= 256
-    ni = std::max(1, std::min(8, 256 / std::max(1, hd.Rmax)));
-    while (ni > 1 && ((imax + ni - 1) / ni) * hd.K < 4LL * c.num_sms) ni /= 2;
-    nx = (int)((imax + ni - 1) / ni);
-  }
-  const int grid = nlip + nx * hd.K;
-  if (grid == 0) return cudaSuccess;
-  cudaError_t e = fp64 ? allow_smem(k_mode_prep<double>, sm) : allow_smem(k_mode_prep<float>, sm);
-  if (e != cudaSuccess) return e;
-  if (fp64) k_mode_prep<double><<<grid, 256, sm, c.stream>>>(dd, n, use_core, prev, gram_rows, nlip, nx, ni);
-  else k_mode_prep<float><<<grid, 256, sm, c.stream>>>(dd, n, use_core, prev, gram_rows, nlip, nx, ni);
-  return cudaGetLastError();
+  (void)dd;
+#define MCASE(V)                                                                                       \
+  case V:                                                                                              \
+    return fp64 ? mode_prep_impl<double, V>(c, hd, n, use_core, prev, with_level2)                     \
+                : mode_prep_impl<float, V>(c, hd, n, use_core, prev, with_level2);
+  switch (rank_bucket_of(hd)) { CNCPD_FOR_EACH_RP(MCASE) }
+#undef MCASE
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_lipschitz(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int n, int use_core,
                              int prev) {
-  int gram_rows;
-  size_t sm;
-  lipschitz_smem(hd, fp64, &gram_rows, &sm);
-  cudaError_t e = fp64 ? allow_smem(k_lipschitz<double>, sm) : allow_smem(k_lipschitz<float>, sm);
+  return launch_mode_prep(c, dd, hd, fp64, n, use_core, prev, 0);
+}
+
+// H of mode n for every block, without L (the gradient path).
+template <typename T, int RP>
+static cudaError_t hmat_impl(const LaunchCfg& c, const DevDesc& hd, int n, int use_core) {
+  LipArgs<T> la = lip_args<T>(hd, n, use_core, -1, 0);
+  const size_t sm = lip_smem_bytes<RP>();
+  cudaError_t e = allow_smem(k_lipschitz<T, RP>, sm);
   if (e != cudaSuccess) return e;
-  const int nt = hd.Rmax <= 16 ? 128 : 256;
-  if (fp64) k_lipschitz<double><<<hd.K, nt, sm, c.stream>>>(dd, n, use_core, 1, prev, gram_rows);
-  else k_lipschitz<float><<<hd.K, nt, sm, c.stream>>>(dd, n, use_core, 1, prev, gram_rows);
+  k_lipschitz<T, RP><<<hd.K, 256, sm, c.stream>>>(la);
   return cudaGetLastError();
+}
+
+static cudaError_t launch_hmat(const LaunchCfg& c, const DevDesc& hd, int fp64, int n, int use_core) {
+#define HCASE(V) \
+  case V: return fp64 ? hmat_impl<double, V>(c, hd, n, use_core) : hmat_impl<float, V>(c, hd, n, use_core);
+  switch (rank_bucket_of(hd)) { CNCPD_FOR_EACH_RP(HCASE) }
+#undef HCASE
+  return cudaErrorInvalidValue;
 }
 
 // ---------------------------------------------------------------------------
@@ -420,10 +621,10 @@ cudaError_t launch_lipschitz(const LaunchCfg& c, const DevDesc* dd, const DevDes
 //   individual columns: U1 <- P(U_hat - G_hat / L_u^(n,k))
 //   shared columns:     U1 <- P(U_hat_C - sum_k G_hat_C / sum_k L_u^(n,k)),
 //                       the same value written to every block
-//   U2 <- old U1.
-// (The Gram of the new factor is formed by the next kernel that needs it.)
-// Thread (c, y) owns column c of row blockIdx.x * ROWS + y and walks the
-// blocks in chunks of KC, keeping the shared-column gradient sum in a
+//   U2 <- old U1,
+// then the Gram chunk values of the new rows (one chunk per CTA).  Thread
+// (c, y) owns column c of row y of each pass over the CTA's rows and walks
+// the blocks in chunks of KC, keeping the shared-column gradient sum in a
 // register, so the coupled sum needs no cross-CTA communication.  Rows are
 // owned by exactly one CTA, so the in-place write is race free.
 // ---------------------------------------------------------------------------
@@ -435,128 +636,189 @@ struct UpdCfg {
 };
 
 template <typename T, int RP>
-__global__ void __launch_bounds__(128) k_update(const DevDesc* __restrict__ d, int n, int use_w, double delta_w,
-                                                int use_core) {
-  constexpr int ROWS = UpdCfg<T, RP>::ROWS;
+__global__ void __launch_bounds__(128) k_update(const __grid_constant__ UpdArgs<T> a) {
+  constexpr int TY = UpdCfg<T, RP>::ROWS;
   constexpr int KC = UpdCfg<T, RP>::KC;
+  constexpr int NT = RP * TY;
   __shared__ T Hs[KC][RP * RP];
-  __shared__ T uh[KC][ROWS][RP];
+  __shared__ T uh[KC][TY][RP];
+  __shared__ T wsh[CNCPD_KMAX + 1];
+  __shared__ T Lsh[CNCPD_KMAX];
+  __shared__ double LCs;
 
   const int c = threadIdx.x;
   const int y = threadIdx.y;
   const int tid = c + y * RP;
-  constexpr int NT = RP * ROWS;
-  const int64_t row0 = (int64_t)blockIdx.x * ROWS;
-  const int64_t i = row0 + y;
-  const int K = d->K;
-  const int Ln = d->L[n];
-  const int nonneg = d->nonneg[n];
-  DevScalars* sc = d->sc;
-  __shared__ T wsh[CNCPD_KMAX + 1];
-  __shared__ double LCs;
+  const int K = a.K, n = a.n, Ln = a.Ln;
+  DevScalars* sc = a.sc;
+  const int64_t row0 = (int64_t)blockIdx.x * a.gr;
+  const int nchunk = (K + KC - 1) / KC;
+
+  // H of the first chunk of blocks (all of them when K <= KC)
+  auto load_h = [&](int k0) {
+    for (int e = tid; e < KC * RP * RP; e += NT) {
+      const int kk = e / (RP * RP), q = e % (RP * RP);
+      const int k = k0 + kk;
+      const int ra = q / RP, rb = q % RP;
+      T v = T(0);
+      if (k < K) {
+        const int R = a.R[k];
+        if (ra < R && rb < R) v = a.H[k][ra * R + rb];
+      }
+      Hs[kk][q] = v;
+    }
+  };
+  load_h(0);
   {
-    // extrapolation weights (Eqs. eqextrawu and reading R3), one FP64
-    // evaluation per block instead of one per thread
-    const double w_hat = use_w ? sc->w_hat : 0.0;
+    // extrapolation weights (Eqs. eqextrawu and reading R3) and L, one
+    // evaluation per block
+    const double w_hat = a.use_w ? sc->w_hat : 0.0;
     const int have_prev = sc->have_prev;
-    if (tid < K) wsh[tid] = extrap_weight<T>(w_hat, have_prev, sc->Lprev_u[n][tid], sc->Lcur_u[n][tid], delta_w);
-    if (tid == K) {
+    for (int k = tid; k < K; k += NT) {
+      const double Lc = sc->Lcur_u[n][k];
+      wsh[k] = extrap_weight<T>(w_hat, have_prev, sc->Lprev_u[n][k], Lc, a.delta_w);
+      Lsh[k] = Lc > 0.0 ? (T)Lc : T(0);
+    }
+    if (tid == 0) {
       double LC = 0.0;
       for (int k = 0; k < K; ++k) LC += sc->Lcur_u[n][k];
       LCs = LC;
-      wsh[K] = extrap_weight<T>(w_hat, have_prev, sc->LCprev[n], LC, delta_w);
+      wsh[K] = extrap_weight<T>(w_hat, have_prev, sc->LCprev[n], LC, a.delta_w);
       if (blockIdx.x == 0) {
         sc->LCcur[n] = LC;
         sc->have_cur = 1;
       }
     }
-    __syncthreads();
   }
+  __syncthreads();
   const double LC = LCs;
   const T wC = wsh[K];
 
-  T sumC = T(0), uhC = T(0), u1C = T(0);
-  for (int k0 = 0; k0 < K; k0 += KC) {
-    const int kn = min(KC, K - k0);
-    __syncthreads();
-    T u1[KC], u2[KC], mv[KC];
-    for (int kk = 0; kk < kn; ++kk) {
-      const int k = k0 + kk;
-      const int R = d->R[k];
-      const T* Hk = reinterpret_cast<const T*>(d->H[k]);
-      for (int e = tid; e < RP * RP; e += NT) {
-        const int a = e / RP, b = e % RP;
-        Hs[kk][e] = (a < R && b < R) ? Hk[a * R + b] : T(0);
+  for (int p0 = 0; p0 < a.gr; p0 += TY) {
+    const int64_t i = row0 + p0 + y;
+    T sumC = T(0), uhC = T(0), u1C = T(0);
+    for (int k0 = 0; k0 < K; k0 += KC) {
+      if (nchunk > 1) {
+        __syncthreads();
+        load_h(k0);
       }
-      const bool valid = (i < d->dims[k][n]) && (c < R);
-      u1[kk] = u2[kk] = mv[kk] = T(0);
-      if (valid) {
-        u1[kk] = reinterpret_cast<const T*>(d->U1[k][n])[i * R + c];
-        u2[kk] = reinterpret_cast<const T*>(d->U2[k][n])[i * R + c];
-        mv[kk] = reinterpret_cast<const T*>(d->M[k][n])[i * R + c];
-      }
-      const T w = (c < Ln) ? wC : wsh[k];
-      uh[kk][y][c] = valid ? u1[kk] + w * (u1[kk] - u2[kk]) : T(0);
-    }
-    __syncthreads();
-    for (int kk = 0; kk < kn; ++kk) {
-      const int k = k0 + kk;
-      const int R = d->R[k];
-      if ((i < d->dims[k][n]) && (c < R)) {
-        const double Lk = sc->Lcur_u[n][k];
-        const T lam = use_core ? (T)sc->lam1[k][c] : T(1);
-        const T uhat = uh[kk][y][c];
-        T g = -mv[kk] * lam;
+      T u1[KC], mv[KC];
+      T lam[KC];
 #pragma unroll
-        for (int a = 0; a < RP; ++a) g = fma(uh[kk][y][a], Hs[kk][a * RP + c], g);
-        if (c >= Ln) {
-          T nv = u1[kk];
-          if (Lk > 0.0) {
-            nv = uhat - g / (T)Lk;
-            if (nonneg) nv = nv > T(0) ? nv : T(0);
+      for (int kk = 0; kk < KC; ++kk) {
+        const int k = k0 + kk;
+        u1[kk] = mv[kk] = T(0);
+        lam[kk] = T(1);
+        T u2 = T(0);
+        const bool valid = k < K && i < a.I[k] && c < a.R[k];
+        if (valid) {
+          const int R = a.R[k];
+          u1[kk] = a.U1[k][i * R + c];
+          u2 = a.U2[k][i * R + c];
+          mv[kk] = a.M[k][i * R + c];
+          if (a.use_core) lam[kk] = (T)sc->lam1[k][c];
+        }
+        const T w = (c < Ln) ? wC : (k < K ? wsh[k] : T(0));
+        uh[kk][y][c] = valid ? u1[kk] + w * (u1[kk] - u2) : T(0);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < KC; ++kk) {
+        const int k = k0 + kk;
+        if (k < K && i < a.I[k] && c < a.R[k]) {
+          const int R = a.R[k];
+          const T uhat = uh[kk][y][c];
+          T g = -mv[kk] * lam[kk];
+#pragma unroll
+          for (int q = 0; q < RP; ++q) g = fma(uh[kk][y][q], Hs[kk][q * RP + c], g);
+          if (c >= Ln) {
+            T nv = u1[kk];
+            const T Lk = Lsh[k];
+            if (Lk > T(0)) {
+              nv = uhat - g / Lk;
+              if (a.nonneg) nv = nv > T(0) ? nv : T(0);
+            }
+            a.U2[k][i * R + c] = u1[kk];
+            a.U1[k][i * R + c] = nv;
+          } else {
+            sumC += g;
+            uhC = uhat;
+            u1C = u1[kk];
           }
-          reinterpret_cast<T*>(d->U2[k][n])[i * R + c] = u1[kk];
-          reinterpret_cast<T*>(d->U1[k][n])[i * R + c] = nv;
-        } else {
-          sumC += g;
-          uhC = uhat;
-          u1C = u1[kk];
         }
       }
+      __syncthreads();
+    }
+    if (c < Ln && i < a.I[0]) {
+      T nv = u1C;
+      if (LC > 0.0) {
+        nv = uhC - sumC / (T)LC;
+        if (a.nonneg) nv = nv > T(0) ? nv : T(0);
+      }
+      for (int k = 0; k < K; ++k) {
+        const int R = a.R[k];
+        a.U2[k][i * R + c] = u1C;
+        a.U1[k][i * R + c] = nv;
+      }
     }
   }
-  if (c < Ln && i < d->dims[0][n]) {
-    T nv = u1C;
-    if (LC > 0.0) {
-      nv = uhC - sumC / (T)LC;
-      if (nonneg) nv = nv > T(0) ? nv : T(0);
-    }
-    for (int k = 0; k < K; ++k) {
-      const int R = d->R[k];
-      reinterpret_cast<T*>(d->U2[k][n])[i * R + c] = u1C;
-      reinterpret_cast<T*>(d->U1[k][n])[i * R + c] = nv;
+  if (!a.Gp) return;
+  __syncthreads();  // the CTA's new rows are visible to the whole CTA
+  for (int e = tid; e < K * RP * RP; e += NT) {
+    const int k = e / (RP * RP), q = e % (RP * RP);
+    const int ra = q / RP, rb = q % RP;
+    const int R = a.R[k];
+    const int64_t I = a.I[k];
+    if (ra < R && rb < R && row0 < I) {
+      const int rows = (int)min((int64_t)a.gr, I - row0);
+      a.Gp[((size_t)k * a.gnc + blockIdx.x) * a.rr + ra * R + rb] =
+          (double)gram_chain<T>(a.U1[k], row0, rows, R, ra, rb);
     }
   }
-
 }
 
 template <typename T, int RP>
-static cudaError_t update_impl(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int n, int use_w,
-                               double delta_w, int use_core) {
-  constexpr int ROWS = UpdCfg<T, RP>::ROWS;
+static cudaError_t update_impl(const LaunchCfg& c, const DevDesc& hd, int n, int use_w, double delta_w,
+                               int use_core) {
+  UpdArgs<T> a{};
+  a.K = hd.K;
+  a.n = n;
+  a.Ln = hd.L[n];
+  a.nonneg = hd.nonneg[n];
+  a.use_w = use_w;
+  a.use_core = use_core;
+  a.delta_w = delta_w;
+  a.sc = hd.sc;
+  a.rr = hd.Rmax * hd.Rmax;
   int64_t imax = 0;
-  for (int k = 0; k < hd.K; ++k) imax = hd.dims[k][n] > imax ? hd.dims[k][n] : imax;
-  const unsigned grid = (unsigned)((imax + ROWS - 1) / ROWS);
-  k_update<T, RP><<<grid, dim3(RP, ROWS), 0, c.stream>>>(dd, n, use_w, delta_w, use_core);
+  for (int k = 0; k < hd.K; ++k) imax = std::max<int64_t>(imax, hd.dims[k][n]);
+  if (hd.Gp[n]) {
+    a.Gp = hd.Gp[n];
+    a.gr = hd.gr[n];
+    a.gnc = hd.gnc[n];
+  } else {
+    a.gr = gram_chunk_rows(RP, imax);
+  }
+  for (int k = 0; k < hd.K; ++k) {
+    a.R[k] = hd.R[k];
+    a.I[k] = (int)hd.dims[k][n];
+    a.U1[k] = reinterpret_cast<T*>(hd.U1[k][n]);
+    a.U2[k] = reinterpret_cast<T*>(hd.U2[k][n]);
+    a.M[k] = reinterpret_cast<const T*>(hd.M[k][n]);
+    a.H[k] = reinterpret_cast<const T*>(hd.Hbase) + (size_t)k * a.rr;
+  }
+  const unsigned grid = (unsigned)((imax + a.gr - 1) / a.gr);
+  k_update<T, RP><<<grid, dim3(RP, UpdCfg<T, RP>::ROWS), 0, c.stream>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_update(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int RP, int n,
                           int use_w, double delta_w, int use_core) {
-#define UCASE(V)                                                                       \
-  case V:                                                                              \
-    return fp64 ? update_impl<double, V>(c, dd, hd, n, use_w, delta_w, use_core)       \
-                : update_impl<float, V>(c, dd, hd, n, use_w, delta_w, use_core);
+  (void)dd;
+#define UCASE(V)                                                                  \
+  case V:                                                                         \
+    return fp64 ? update_impl<double, V>(c, hd, n, use_w, delta_w, use_core)      \
+                : update_impl<float, V>(c, hd, n, use_w, delta_w, use_core);
   switch (RP) { CNCPD_FOR_EACH_RP(UCASE) }
 #undef UCASE
   return cudaErrorInvalidValue;
@@ -570,66 +832,90 @@ cudaError_t launch_update(const LaunchCfg& c, const DevDesc* dd, const DevDesc& 
 // with M^(N-1) the MTTKRP of the last mode (computed before its update) and
 // U^(N-1) the updated factor: together they give <X, [[U]]> at the new point.
 // The per-r sums are the core term (U^{odot})^T vec(X) of Eq. solapgG for the
-// next core update.  RelErr per Section III-C.  One CTA, threads (r, y).
+// next core update.  RelErr per Section III-C.  One CTA per block, threads
+// (r, y); the last CTA to finish adds the blocks up in order.
 // ---------------------------------------------------------------------------
 template <typename T, int RP>
-__global__ void __launch_bounds__(256) k_objective(const DevDesc* __restrict__ d, int commit) {
-  const int r = threadIdx.x, y = threadIdx.y, Y = blockDim.y;
-  const int tid = r + y * RP;
-  const int NT = RP * Y;
-  const int N = d->N, n = N - 1;
+__global__ void __launch_bounds__(256) k_objective(const __grid_constant__ ObjArgs<T> a) {
+  constexpr int Y = 256 / RP;
+  constexpr int NT = RP * Y;
+  const int tid = threadIdx.x;
+  const int r = tid % RP, y = tid / RP;  // threads >= NT only join the reductions
+  const int N = a.N, n = N - 1;
   const int k = blockIdx.x;
-  DevScalars* sc = d->sc;
+  DevScalars* sc = a.sc;
   __shared__ double red[256];
   __shared__ double cr[RP];
   __shared__ int is_last;
-  constexpr int CAP = (16384 / (int)sizeof(T)) / RP / GRAM_TILE * GRAM_TILE > 0
-                          ? (16384 / (int)sizeof(T)) / RP / GRAM_TILE * GRAM_TILE : GRAM_TILE;
-  __shared__ T tile[CAP * RP];
-  const int R = d->R[k];
-  if (commit)  // Gram of the last mode, just updated
-    block_gram<T>(reinterpret_cast<const T*>(d->U1[k][n]), d->dims[k][n], R, d->G[k][n], tile, CAP);
-  const int64_t I = d->dims[k][n];
-  const T* M = reinterpret_cast<const T*>(d->M[k][n]);
-  const T* U = reinterpret_cast<const T*>(d->U1[k][n]);
+  const int R = a.R[k];
+  const int64_t I = a.I[k];
+  const T* __restrict__ M = a.M[k];
+  const T* __restrict__ U = a.U[k];
+  const int rr = a.rr;
+  double* Gk = a.G + (size_t)k * N * rr;
+  // <M, U> per column, FP64
   double acc = 0.0;
-  if (r < R)
-    for (int64_t i = y; i < I; i += Y) acc = fma((double)M[i * R + r], (double)U[i * R + r], acc);
-  red[tid] = acc;
+  if (r < R && y < Y) {
+    int64_t i = y;
+    for (; i + 3 * Y < I; i += 4 * Y) {
+      const T m0 = M[i * R + r], m1 = M[(i + Y) * R + r], m2 = M[(i + 2 * Y) * R + r], m3 = M[(i + 3 * Y) * R + r];
+      const T u0 = U[i * R + r], u1 = U[(i + Y) * R + r], u2 = U[(i + 2 * Y) * R + r], u3 = U[(i + 3 * Y) * R + r];
+      acc = fma((double)m0, (double)u0, acc);
+      acc = fma((double)m1, (double)u1, acc);
+      acc = fma((double)m2, (double)u2, acc);
+      acc = fma((double)m3, (double)u3, acc);
+    }
+    for (; i < I; i += Y) acc = fma((double)M[i * R + r], (double)U[i * R + r], acc);
+  }
+  // ||X_hat||^2 terms; the Gram of the last mode is summed from its chunks
+  double xx = 0.0;
+  const int nch = a.reduce_last ? (int)((I + a.gr - 1) / a.gr) : 0;
+  const double* gp = a.reduce_last ? a.Gp_last + (size_t)k * a.gnc * rr : nullptr;
+  for (int p = tid; p < R * R; p += 256) {
+    double gm[CNCPD_NMAX];
+#pragma unroll
+    for (int m = 0; m < CNCPD_NMAX; ++m) gm[m] = (m < N && !(a.reduce_last && m == n)) ? Gk[(size_t)m * rr + p] : 1.0;
+    if (a.reduce_last) {
+      const double g = gram_sum(gp, nch, rr, p);
+      Gk[(size_t)n * rr + p] = g;
+#pragma unroll
+      for (int m = 0; m < CNCPD_NMAX; ++m)
+        if (m == n) gm[m] = g;
+    }
+    double g = sc->lam1[k][p / R] * sc->lam1[k][p % R];
+#pragma unroll
+    for (int m = 0; m < CNCPD_NMAX; ++m)
+      if (m < N) g *= gm[m];
+    xx += g;
+  }
+  if (tid < NT) red[tid] = acc;
   __syncthreads();
   if (y == 0) {
     double s = 0.0;
     for (int yy = 0; yy < Y; ++yy) s += red[yy * RP + r];
     cr[r] = s;
-    if (r < R && commit) sc->cterm[k][r] = s;
+    if (r < R && a.commit) sc->cterm[k][r] = s;
   }
   __syncthreads();
-  // ||X_hat||^2 = lambda^T (*_m G^(m)) lambda and <X, X_hat> = lambda^T c
-  double xx = 0.0;
-  for (int p = tid; p < R * R; p += NT) {
-    const int a = p / R, b = p % R;
-    double g = sc->lam1[k][a] * sc->lam1[k][b];
-    for (int m = 0; m < N; ++m) g *= d->G[k][m][p];
-    xx += g;
-  }
   if (tid < R) xx -= 2.0 * sc->lam1[k][tid] * cr[tid];
   for (int o = 16; o > 0; o >>= 1) xx += __shfl_xor_sync(0xffffffffu, xx, o);
+  __syncthreads();
   if ((tid & 31) == 0) red[tid >> 5] = xx;
   __syncthreads();
   if (tid == 0) {
     double t = 0.0;
-    for (int q = 0; q < (NT + 31) / 32; ++q) t += red[q];
-    const double x2 = commit ? sc->xnorm2[k] : sc->xnorm2_orig[k];
+    for (int q = 0; q < 8; ++q) t += red[q];
+    const double x2 = a.commit ? sc->xnorm2[k] : sc->xnorm2_orig[k];
     const double Fk = 0.5 * (x2 + t);
     const double rel = x2 > 0.0 ? sqrt(fmax(2.0 * Fk, 0.0) / x2) : 0.0;
-    if (commit) {
+    if (a.commit) {
       sc->Fk[k] = Fk;
       sc->relk[k] = rel;
     } else {
       sc->out_relk[k] = rel;
     }
   }
-  if (!commit) return;
+  if (!a.commit) return;
   __threadfence();
   __syncthreads();
   if (tid == 0) is_last = (atomicAdd(&sc->done_counter[1], 1) == (int)gridDim.x - 1);
@@ -648,12 +934,39 @@ __global__ void __launch_bounds__(256) k_objective(const DevDesc* __restrict__ d
   }
 }
 
-cudaError_t launch_objective(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int RP, int commit) {
-#define OCASE(V)                                                                                  \
-  case V:                                                                                         \
-    if (fp64) k_objective<double, V><<<hd.K, dim3(V, 256 / V), 0, c.stream>>>(dd, commit);        \
-    else k_objective<float, V><<<hd.K, dim3(V, 256 / V), 0, c.stream>>>(dd, commit);              \
-    return cudaGetLastError();
+template <typename T, int RP>
+static cudaError_t objective_impl(const LaunchCfg& c, const DevDesc& hd, int commit, int reduce_last) {
+  ObjArgs<T> a{};
+  const int n = hd.N - 1;
+  a.K = hd.K;
+  a.N = hd.N;
+  a.rr = hd.Rmax * hd.Rmax;
+  a.commit = commit;
+  a.reduce_last = (reduce_last && hd.Gp[n]) ? 1 : 0;
+  a.sc = hd.sc;
+  a.G = hd.Gbase;
+  if (a.reduce_last) {
+    a.Gp_last = hd.Gp[n];
+    a.gnc = hd.gnc[n];
+    a.gr = hd.gr[n];
+  }
+  for (int k = 0; k < hd.K; ++k) {
+    a.R[k] = hd.R[k];
+    a.I[k] = (int)hd.dims[k][n];
+    a.M[k] = reinterpret_cast<const T*>(hd.M[k][n]);
+    a.U[k] = reinterpret_cast<const T*>(hd.U1[k][n]);
+  }
+  k_objective<T, RP><<<hd.K, 256, 0, c.stream>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_objective(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int RP, int commit,
+                             int reduce_last) {
+  (void)dd;
+#define OCASE(V)                                                                 \
+  case V:                                                                        \
+    return fp64 ? objective_impl<double, V>(c, hd, commit, reduce_last)          \
+                : objective_impl<float, V>(c, hd, commit, reduce_last);
   switch (RP) { CNCPD_FOR_EACH_RP(OCASE) }
 #undef OCASE
   return cudaErrorInvalidValue;
@@ -663,21 +976,21 @@ cudaError_t launch_objective(const LaunchCfg& c, const DevDesc* dd, const DevDes
 // Core update of Eqs. solD / solapgG / eqextraPG with L_d = ||(U^T U)^*||_2
 // (Eq. eqLipsLd) and the weight of Eq. eqextrawd.  One CTA per block, FP64.
 // ---------------------------------------------------------------------------
+template <int RP>
 __global__ void __launch_bounds__(256) k_core_update(const DevDesc* __restrict__ d, int use_w, double delta_w) {
   const int k = blockIdx.x;
   const int R = d->R[k], N = d->N;
   DevScalars* sc = d->sc;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  LmaxScratch scr;
-  scr.carve(smem_raw, R);
-  double* Hs = scr.Hs;
+  double* Hs = reinterpret_cast<double*>(smem_raw);
+  LmaxSmem<RP>* ls = reinterpret_cast<LmaxSmem<RP>*>(smem_raw + (size_t)RP * RP * sizeof(double));
   __shared__ double lh[CNCPD_RMAX];
   for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
     double h = 1.0;
     for (int m = 0; m < N; ++m) h *= d->G[k][m][e];
     Hs[e] = h;
   }
-  const double Ld = lmax_psd<double>(Hs, R, &scr);
+  const double Ld = lmax_rp<double, RP>(Hs, R, ls);
   const double w = extrap_weight<double>(use_w ? sc->w_hat : 0.0, sc->have_prev, sc->Ldprev[k], Ld, delta_w);
   for (int a = threadIdx.x; a < R; a += blockDim.x) lh[a] = sc->lam1[k][a] + w * (sc->lam1[k][a] - sc->lam2[k][a]);
   __syncthreads();
@@ -698,12 +1011,21 @@ __global__ void __launch_bounds__(256) k_core_update(const DevDesc* __restrict__
   }
 }
 
-cudaError_t launch_core_update(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int use_w, double delta_w) {
-  const size_t sm = lmax_smem_bytes(hd.Rmax);
-  cudaError_t e = allow_smem(k_core_update, sm);
+template <int RP>
+static cudaError_t core_impl(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int use_w, double delta_w) {
+  const size_t sm = lip_smem_bytes<RP>();
+  cudaError_t e = allow_smem(k_core_update<RP>, sm);
   if (e != cudaSuccess) return e;
-  k_core_update<<<hd.K, 256, sm, c.stream>>>(dd, use_w, delta_w);
+  k_core_update<RP><<<hd.K, 256, sm, c.stream>>>(dd, use_w, delta_w);
   return cudaGetLastError();
+}
+
+cudaError_t launch_core_update(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int use_w, double delta_w) {
+#define CCASE(V) \
+  case V: return core_impl<V>(c, dd, hd, use_w, delta_w);
+  switch (rank_bucket_of(hd)) { CNCPD_FOR_EACH_RP(CCASE) }
+#undef CCASE
+  return cudaErrorInvalidValue;
 }
 
 // ---------------------------------------------------------------------------
@@ -711,34 +1033,43 @@ cudaError_t launch_core_update(const LaunchCfg& c, const DevDesc* dd, const DevD
 // Lipschitz constants of the last accepted sweep as L_{k-2}, snapshot the
 // core term and lambda_2 (the factor snapshot is a device memcpy).
 // Redo: restore lambda and the core term for the w = 0 re-update.
+// One element per thread, so every load is issued at once.
 // ---------------------------------------------------------------------------
-__global__ void k_iter_begin(const DevDesc* __restrict__ d) {
-  DevScalars* sc = d->sc;
-  const int K = d->K, N = d->N;
+struct IterArgs {
+  int K, N, use_core, pad;
+  DevScalars* sc;
+};
+
+__global__ void __launch_bounds__(1024) k_iter_begin(const __grid_constant__ IterArgs a) {
+  DevScalars* sc = a.sc;
+  const int K = a.K, N = a.N;
   const int tid = threadIdx.x;
   const int have_cur = sc->have_cur;
-  __syncthreads();
-  if (tid == 0) {
+  if (tid < N * K) {
+    const int n = tid / K, k = tid % K;
+    const double L = sc->Lcur_u[n][k];
+    if (have_cur) sc->Lprev_u[n][k] = L;
+  } else if (tid < N * K + N) {
+    const int n = tid - N * K;
+    const double L = sc->LCcur[n];
+    if (have_cur) sc->LCprev[n] = L;
+  } else if (tid < N * K + N + K) {
+    const int k = tid - N * K - N;
+    const double L = sc->Ldcur[k];
+    if (have_cur) sc->Ldprev[k] = L;
+  } else if (tid == N * K + N + K) {
     const double t = sc->t;
     const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
     sc->w_hat = (t - 1.0) / tn;
     sc->t = tn;
+    if (have_cur) sc->have_prev = 1;
   }
-  if (have_cur) {
-    for (int e = tid; e < N * CNCPD_KMAX; e += blockDim.x) {
-      const int n = e / CNCPD_KMAX, k = e % CNCPD_KMAX;
-      sc->Lprev_u[n][k] = sc->Lcur_u[n][k];
+  if (a.use_core)
+    for (int e = tid; e < K * CNCPD_RMAX; e += blockDim.x) {
+      const int k = e / CNCPD_RMAX, r = e % CNCPD_RMAX;
+      sc->cterm_save[k][r] = sc->cterm[k][r];
+      sc->lamS[k][r] = sc->lam2[k][r];
     }
-    for (int n = tid; n < N; n += blockDim.x) sc->LCprev[n] = sc->LCcur[n];
-    for (int k = tid; k < K; k += blockDim.x) sc->Ldprev[k] = sc->Ldcur[k];
-  }
-  for (int e = tid; e < K * CNCPD_RMAX; e += blockDim.x) {
-    const int k = e / CNCPD_RMAX, r = e % CNCPD_RMAX;
-    sc->cterm_save[k][r] = sc->cterm[k][r];
-    sc->lamS[k][r] = sc->lam2[k][r];
-  }
-  __syncthreads();
-  if (tid == 0 && have_cur) sc->have_prev = 1;
 }
 
 __global__ void k_redo_prepare(const DevDesc* __restrict__ d) {
@@ -752,8 +1083,13 @@ __global__ void k_redo_prepare(const DevDesc* __restrict__ d) {
   }
 }
 
-cudaError_t launch_iter_begin(const LaunchCfg& c, const DevDesc* dd, const DevDesc&) {
-  k_iter_begin<<<1, 256, 0, c.stream>>>(dd);
+cudaError_t launch_iter_begin(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int use_core) {
+  (void)dd;
+  IterArgs a{hd.K, hd.N, use_core, 0, hd.sc};
+  const int need = hd.N * hd.K + hd.N + hd.K + 1;
+  int nt = 256;
+  while (nt < need && nt < 1024) nt *= 2;
+  k_iter_begin<<<1, nt, 0, c.stream>>>(a);
   return cudaGetLastError();
 }
 
@@ -802,11 +1138,8 @@ cudaError_t launch_grad(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd
   int64_t imax = 0;
   for (int k = 0; k < hd.K; ++k) imax = hd.dims[k][n] > imax ? hd.dims[k][n] : imax;
   {
-    const size_t sm = lmax_smem_bytes(hd.Rmax);
-    cudaError_t e = fp64 ? allow_smem(k_lipschitz<double>, sm) : allow_smem(k_lipschitz<float>, sm);
+    cudaError_t e = launch_hmat(c, hd, fp64, n, use_core);
     if (e != cudaSuccess) return e;
-    if (fp64) k_lipschitz<double><<<hd.K, 256, sm, c.stream>>>(dd, n, use_core, 0, -1, GRAM_TILE);
-    else k_lipschitz<float><<<hd.K, 256, sm, c.stream>>>(dd, n, use_core, 0, -1, GRAM_TILE);
   }
 #define GCASE(V)                                                                        \
   case V: {                                                                             \
@@ -929,22 +1262,31 @@ cudaError_t launch_uniform_init(cudaStream_t s, void* dst, int fp64, int64_t n, 
   return cudaGetLastError();
 }
 
+template <int RP>
 __global__ void k_lmax_one(const double* H, int R, double* out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  LmaxScratch scr;
-  scr.carve(smem_raw, R);
-  double* Hs = scr.Hs;
+  double* Hs = reinterpret_cast<double*>(smem_raw);
+  LmaxSmem<RP>* ls = reinterpret_cast<LmaxSmem<RP>*>(smem_raw + (size_t)RP * RP * sizeof(double));
   for (int e = threadIdx.x; e < R * R; e += blockDim.x) Hs[e] = H[e];
-  const double L = lmax_psd<double>(Hs, R, &scr);
+  const double L = lmax_rp<double, RP>(Hs, R, ls);
   if (threadIdx.x == 0) *out = L;
 }
 
-cudaError_t launch_lmax_host(const double* d_H, int R, double* d_out, cudaStream_t s) {
-  const size_t sm = lmax_smem_bytes(R);
-  cudaError_t e = allow_smem(k_lmax_one, sm);
+template <int RP>
+static cudaError_t lmax_one_impl(const double* d_H, int R, double* d_out, cudaStream_t s) {
+  const size_t sm = lip_smem_bytes<RP>();
+  cudaError_t e = allow_smem(k_lmax_one<RP>, sm);
   if (e != cudaSuccess) return e;
-  k_lmax_one<<<1, 256, sm, s>>>(d_H, R, d_out);
+  k_lmax_one<RP><<<1, 256, sm, s>>>(d_H, R, d_out);
   return cudaGetLastError();
+}
+
+cudaError_t launch_lmax_host(const double* d_H, int R, double* d_out, cudaStream_t s) {
+#define LCASE(V) \
+  case V: return lmax_one_impl<V>(d_H, R, d_out, s);
+  switch (rank_bucket(R)) { CNCPD_FOR_EACH_RP(LCASE) }
+#undef LCASE
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace cncpd
