@@ -788,7 +788,7 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
   for (int n = 0; n < N; ++n) {
     int64_t imax = 0;
     for (int k = 0; k < K; ++k) imax = std::max<int64_t>(imax, c->dim(k, n));
-    d.gr[n] = gram_chunk_rows(c->RP, imax);
+    d.gr[n] = gram_chunk_rows(c->RP, K, imax, c->fp64);
     d.gnc[n] = (int)((imax + d.gr[n] - 1) / d.gr[n]);
     CTRY(dalloc(c, (void**)&d.Gp[n], (size_t)K * d.gnc[n] * rr * sizeof(double)));
   }

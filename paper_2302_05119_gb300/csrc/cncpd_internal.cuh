@@ -19,6 +19,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #define CNCPD_KMAX 64
 #define CNCPD_NMAX 8
 #define CNCPD_RMAX 64
@@ -153,6 +155,26 @@ inline int rank_bucket(int R) {
   return -1;
 }
 
+// Every kernel of the sweep asks for the largest shared-memory carveout, so
+// consecutive kernels (the TMA passes need almost all of it) run with one
+// L1 / shared split and the SMs are not reconfigured between launches.  Set
+// once per kernel and device, before the kernel's first launch.
+template <auto Kernel>
+inline void carve() {
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return;
+  }
+  const unsigned long long bit = 1ull << dev;
+  if (done.load(std::memory_order_relaxed) & bit) return;
+  if (cudaFuncSetAttribute(Kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+    cudaGetLastError();
+  done.fetch_or(bit);
+}
+
 // ----------------------------------------------------- launch wrappers ----
 // Implemented in mttkrp.cu / update.cu / lra.cu.  `fp64` selects the FP64
 // factor path (storage ST_F64); otherwise factors are FP32.
@@ -193,7 +215,7 @@ cudaError_t launch_objective(const LaunchCfg& c, const DevDesc* d_desc, const De
 cudaError_t launch_core_update(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int use_w, double delta_w);
 cudaError_t launch_iter_begin(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int use_core);
 // Rows per Gram chunk of a mode with at most imax rows (the rows of one update CTA).
-int gram_chunk_rows(int RP, int64_t imax);
+int gram_chunk_rows(int RP, int K, int64_t imax, int fp64);
 cudaError_t launch_redo_prepare(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc);
 // Quantise a rows x cols tensor (C order) into storage with row pitch `pitch` (padding zeroed).
 cudaError_t launch_quantize(cudaStream_t s, const void* src, int src_f64, void* dst, void* dst_lo, int st,

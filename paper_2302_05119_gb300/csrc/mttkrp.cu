@@ -343,16 +343,14 @@ __global__ void __launch_bounds__(256) k_reduce_splits(const __grid_constant__ S
     const T* part = a.part[k] + (e - a.prefix[k]);
     const int64_t stride = a.stride[k];
     const int ns = a.nsplit[k];
-    int i = g;
-    for (; i + 24 < ns; i += 32) {
-      const T x0 = part[(int64_t)i * stride], x1 = part[(int64_t)(i + 8) * stride];
-      const T x2 = part[(int64_t)(i + 16) * stride], x3 = part[(int64_t)(i + 24) * stride];
-      s += x0;
-      s += x1;
-      s += x2;
-      s += x3;
+    for (int i0 = g; i0 < ns; i0 += 64) {
+      T x[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) x[j] = part[(int64_t)min(i0 + 8 * j, ns - 1) * stride];  // clamped
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (i0 + 8 * j < ns) s += x[j];
     }
-    for (; i < ns; i += 8) s += part[(int64_t)i * stride];
   }
   red[g][lane] = s;
   __syncthreads();
@@ -469,6 +467,7 @@ static cudaError_t reduce_splits_impl(const LaunchCfg& c, const DevDesc& hd) {
   }
   const int64_t blocks = (a.prefix[hd.K] + 31) / 32;
   if (blocks == 0) return cudaSuccess;
+  carve<k_reduce_splits<T>>();
   k_reduce_splits<T><<<(unsigned)blocks, 256, 0, c.stream>>>(a);
   return cudaGetLastError();
 }

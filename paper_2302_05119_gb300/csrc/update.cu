@@ -41,7 +41,7 @@ template <typename T>
 struct UpdArgs {            // fused APG update of mode n
   int K, n, Ln, nonneg;
   int use_w, use_core, gr, gnc;
-  int rr, pad;
+  int rr, stage_rows;       // stage_rows: the CTA keeps its new rows in shared memory
   double delta_w;
   DevScalars* sc;
   double* Gp;               // Gram partials of mode n (written)
@@ -82,6 +82,7 @@ struct LmaxSmem {
   float B[RP * RP];
   double v[RP];
   double w[RP];
+  double scal[2];
   float red[32];
 };
 
@@ -97,11 +98,17 @@ __device__ double lmax_rp(const double* Hs, int R, LmaxSmem<RP>* s) {
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
   const int nt = blockDim.x * blockDim.y;
   __syncthreads();
-  double tr = 0.0;
-  for (int i = 0; i < R; ++i) tr += Hs[i * R + i];
+  if (tid == 0) {  // FP64 is slow on this part: one thread forms the trace and its inverse
+    double t = 0.0;
+    for (int i = 0; i < R; ++i) t += Hs[i * R + i];
+    s->scal[0] = t;
+    s->scal[1] = (t > 0.0 && isfinite(t)) ? 1.0 / t : 0.0;
+  }
+  __syncthreads();
+  const double tr = s->scal[0];
   if (!isfinite(tr)) return tr;
   if (!(tr > 0.0)) return 0.0;
-  const double itr = 1.0 / tr;
+  const double itr = s->scal[1];
   for (int e = tid; e < RR; e += nt) {
     const int i = e / RP, j = e % RP;
     s->A[e] = (i < R && j < R) ? (float)(Hs[i * R + j] * itr) : 0.f;
@@ -204,19 +211,18 @@ __device__ __forceinline__ T gram_chain(const T* U, int64_t row0, int rows, int 
   return s;
 }
 
-// Sum of the first nch chunk values of entry p (stride rr), in chunk order.
+// Sum of the first nch chunk values of entry p (stride rr), in chunk order;
+// the loads of up to 32 chunks are issued before any of them is added.
 __device__ __forceinline__ double gram_sum(const double* __restrict__ gp, int nch, int rr, int p) {
   double s = 0.0;
-  int c = 0;
-  for (; c + 4 <= nch; c += 4) {
-    const double x0 = gp[(size_t)c * rr + p], x1 = gp[(size_t)(c + 1) * rr + p];
-    const double x2 = gp[(size_t)(c + 2) * rr + p], x3 = gp[(size_t)(c + 3) * rr + p];
-    s += x0;
-    s += x1;
-    s += x2;
-    s += x3;
+  for (int c0 = 0; c0 < nch; c0 += 32) {
+    double x[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) x[j] = gp[(size_t)min(c0 + j, nch - 1) * rr + p];  // clamped: no predicate
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (c0 + j < nch) s += x[j];
   }
-  for (; c < nch; ++c) s += gp[(size_t)c * rr + p];
   return s;
 }
 
@@ -311,10 +317,16 @@ cudaError_t launch_gram(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd
     int cmax = 1;
     for (int n = n_begin; n < n_end; ++n) cmax = std::max(cmax, hd.gnc[n]);
     dim3 grid((unsigned)cmax, (unsigned)(hd.K * nm));
-    if (fp64) k_gram_chunks<double><<<grid, 256, 0, c.stream>>>(dd, n_begin, n_end);
-    else k_gram_chunks<float><<<grid, 256, 0, c.stream>>>(dd, n_begin, n_end);
+    if (fp64) {
+      carve<k_gram_chunks<double>>();
+      k_gram_chunks<double><<<grid, 256, 0, c.stream>>>(dd, n_begin, n_end);
+    } else {
+      carve<k_gram_chunks<float>>();
+      k_gram_chunks<float><<<grid, 256, 0, c.stream>>>(dd, n_begin, n_end);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    carve<k_gram_reduce>();
     k_gram_reduce<<<hd.K * nm, 256, 0, c.stream>>>(dd, n_begin, n_end);
     return cudaGetLastError();
   }
@@ -324,11 +336,40 @@ cudaError_t launch_gram(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd
   return cudaGetLastError();
 }
 
-// Rows per Gram chunk of mode n: the rows one update CTA handles.
-int gram_chunk_rows(int RP, int64_t imax) {
-  const int ty = std::max(1, 128 / RP);
-  const int64_t passes = std::max<int64_t>(1, ((imax + ty - 1) / ty + 31) / 32);
-  return (int)(ty * passes);
+// Update kernel geometry of one mode.  When K * RP <= 512 and the shared
+// memory fits, one CTA covers (column, block, row) with RP * K * TY threads
+// (k_update_kp); otherwise RP * (128 / RP) threads walk the blocks
+// (k_update).  A CTA handles gr = TY * passes rows -- enough passes that no
+// block has more than 32 Gram chunks -- and gr is also the Gram chunk size.
+struct UpdGeom {
+  int kp, ty, gr;
+  size_t smem;
+};
+
+static UpdGeom update_geometry(int RP, int K, int64_t imax, size_t es) {
+  UpdGeom g{};
+  auto rows = [&](int ty) {
+    const int64_t passes = std::max<int64_t>(1, ((imax + ty - 1) / ty + 31) / 32);
+    return (int)(ty * passes);
+  };
+  if (RP * K <= 512) {
+    g.ty = std::min(64, std::max(1, 512 / (RP * K)));
+    g.gr = rows(g.ty);
+    g.smem = ((size_t)K * RP * RP + 2 * (size_t)g.ty * K * RP + (size_t)K * g.gr * RP) * es;
+    if (g.smem <= 200 * 1024) {
+      g.kp = 1;
+      return g;
+    }
+  }
+  g.kp = 0;
+  g.ty = std::max(1, 128 / RP);
+  g.gr = rows(g.ty);
+  g.smem = 0;
+  return g;
+}
+
+int gram_chunk_rows(int RP, int K, int64_t imax, int fp64) {
+  return update_geometry(RP, K, imax, fp64 ? 8 : 4).gr;
 }
 
 // ---------------------------------------------------------------------------
@@ -401,69 +442,65 @@ __device__ void pair_body(const PairArgs<T>& a, int b, T* red) {
   T* M = a.M[k];
   const int t = threadIdx.x;
   if (a.first) {
+    // ni <= 2 rows; 12 columns e of the (b, r) range per batch, all loads first
     const int BR = Io * R;
     const int stride = (256 / R) * R;
-    T acc[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = T(0);
+    T acc0 = T(0), acc1 = T(0);
     if (t < stride) {
-      int e = t;
-      for (; e + 3 * stride < BR; e += 4 * stride) {
-        const T w0 = W[e], w1 = W[e + stride], w2 = W[e + 2 * stride], w3 = W[e + 3 * stride];
+      const T* P0 = P + (int64_t)i0 * BR;
+      const T* P1 = ni > 1 ? P0 + BR : P0;
+      for (int e0 = t; e0 < BR; e0 += 12 * stride) {
+        T wv[12], p0v[12], p1v[12];
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if (q < ni) {
-            const T* Pq = P + (int64_t)(i0 + q) * BR + e;
-            const T p0 = Pq[0], p1 = Pq[stride], p2 = Pq[2 * stride], p3 = Pq[3 * stride];
-            acc[q] = fma(p0, w0, acc[q]);
-            acc[q] = fma(p1, w1, acc[q]);
-            acc[q] = fma(p2, w2, acc[q]);
-            acc[q] = fma(p3, w3, acc[q]);
+        for (int j = 0; j < 12; ++j) {
+          const int e = min(e0 + j * stride, BR - 1);  // clamped: every load issues at once
+          wv[j] = W[e];
+          p0v[j] = P0[e];
+          p1v[j] = P1[e];
+        }
+#pragma unroll
+        for (int j = 0; j < 12; ++j)
+          if (e0 + j * stride < BR) {
+            acc0 = fma(p0v[j], wv[j], acc0);
+            acc1 = fma(p1v[j], wv[j], acc1);
           }
       }
-      for (; e < BR; e += stride) {
-        const T w = W[e];
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if (q < ni) acc[q] = fma(P[(int64_t)(i0 + q) * BR + e], w, acc[q]);
-      }
     }
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-      if (q < ni) red[q * 256 + t] = acc[q];
+    red[t] = acc0;
+    red[256 + t] = acc1;
     __syncthreads();
-    for (int o = t; o < ni * R; o += 256) {
-      const int q = o / R, r = o % R;
+    if (t < ni * R) {
+      const int q = t / R, r = t % R;
       T s = T(0);
       for (int u = r; u < stride; u += R) s += red[q * 256 + u];
       M[(int64_t)(i0 + q) * R + r] = s;
     }
   } else {
-    const int JR = ni * R;
-    const int nsl = max(1, 256 / JR);
-    const int j = t % JR, sl = t / JR;
+    // ni == 1: R outputs, the a range cut into 256 / R slices; 12 a per batch
+    const int nsl = max(1, 256 / R);
+    const int j = t % R, sl = t / R;
     T acc = T(0);
-    if (sl < nsl && t < nsl * JR) {
-      const int r = j % R;
+    if (sl < nsl) {
       const T* Pj = P + (int64_t)i0 * R + j;
       const int64_t ps = (int64_t)In * R;
-      int x = sl;
-      for (; x + 3 * nsl < Io; x += 4 * nsl) {
-        const T p0 = Pj[(int64_t)x * ps], p1 = Pj[(int64_t)(x + nsl) * ps];
-        const T p2 = Pj[(int64_t)(x + 2 * nsl) * ps], p3 = Pj[(int64_t)(x + 3 * nsl) * ps];
-        const T w0 = W[x * R + r], w1 = W[(x + nsl) * R + r], w2 = W[(x + 2 * nsl) * R + r], w3 = W[(x + 3 * nsl) * R + r];
-        acc = fma(p0, w0, acc);
-        acc = fma(p1, w1, acc);
-        acc = fma(p2, w2, acc);
-        acc = fma(p3, w3, acc);
+      for (int x0 = sl; x0 < Io; x0 += 12 * nsl) {
+        T pv[12], wv[12];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+          const int x = min(x0 + q * nsl, Io - 1);  // clamped: every load issues at once
+          pv[q] = Pj[(int64_t)x * ps];
+          wv[q] = W[x * R + j];
+        }
+#pragma unroll
+        for (int q = 0; q < 12; ++q)
+          if (x0 + q * nsl < Io) acc = fma(pv[q], wv[q], acc);
       }
-      for (; x < Io; x += nsl) acc = fma(Pj[(int64_t)x * ps], W[x * R + r], acc);
     }
     red[t] = acc;
     __syncthreads();
-    if (t < JR) {
+    if (t < R) {
       T s = T(0);
-      for (int u = 0; u < nsl; ++u) s += red[u * JR + t];
+      for (int u = 0; u < nsl; ++u) s += red[u * R + t];
       M[(int64_t)i0 * R + t] = s;
     }
   }
@@ -526,9 +563,8 @@ static PairArgs<T> pair_args(const DevDesc& hd, int n, int num_sms, int* ctas) {
   for (int k = 0; k < hd.K; ++k) imax = std::max<int64_t>(imax, hd.dims[k][n]);
   int ni;
   if (a.first) {
-    // rows per CTA: enough CTAs to fill the GPU about four times over
-    ni = std::max(1, std::min(8, 256 / std::max(1, hd.Rmax)));
-    while (ni > 1 && ((imax + ni - 1) / ni) * hd.K < 4LL * num_sms) ni /= 2;
+    // one or two rows per CTA: two unless that leaves fewer than ~4 CTAs per SM
+    ni = ((imax + 1) / 2) * hd.K >= 4LL * num_sms ? 2 : 1;
   } else {
     ni = 1;  // R outputs per CTA; the a range is cut into 256/R slices
   }
@@ -558,6 +594,7 @@ static cudaError_t mode_prep_impl(const LaunchCfg& c, const DevDesc& hd, int n, 
   if (with_level2) pa = pair_args<T>(hd, n, c.num_sms, &ctas);
   if (with_level2 == 2) {
     if (ctas == 0) return cudaSuccess;
+    carve<k_level2_pair<T>>();
     k_level2_pair<T><<<ctas, 256, 0, c.stream>>>(pa);
     return cudaGetLastError();
   }
@@ -566,11 +603,13 @@ static cudaError_t mode_prep_impl(const LaunchCfg& c, const DevDesc& hd, int n, 
   if (with_level2 == 0) {
     cudaError_t e = allow_smem(k_lipschitz<T, RP>, sm);
     if (e != cudaSuccess) return e;
+    carve<k_lipschitz<T, RP>>();
     k_lipschitz<T, RP><<<hd.K, RP <= 16 ? 128 : 256, sm, c.stream>>>(la);
     return cudaGetLastError();
   }
   cudaError_t e = allow_smem(k_mode_prep<T, RP>, sm);
   if (e != cudaSuccess) return e;
+  carve<k_mode_prep<T, RP>>();
   k_mode_prep<T, RP><<<hd.K + ctas, 256, sm, c.stream>>>(la, pa);
   return cudaGetLastError();
 }
@@ -601,6 +640,7 @@ static cudaError_t hmat_impl(const LaunchCfg& c, const DevDesc& hd, int n, int u
   const size_t sm = lip_smem_bytes<RP>();
   cudaError_t e = allow_smem(k_lipschitz<T, RP>, sm);
   if (e != cudaSuccess) return e;
+  carve<k_lipschitz<T, RP>>();
   k_lipschitz<T, RP><<<hd.K, 256, sm, c.stream>>>(la);
   return cudaGetLastError();
 }
@@ -645,6 +685,10 @@ __global__ void __launch_bounds__(128) k_update(const __grid_constant__ UpdArgs<
   __shared__ T wsh[CNCPD_KMAX + 1];
   __shared__ T Lsh[CNCPD_KMAX];
   __shared__ double LCs;
+  // new rows of the CTA for the Gram chunk values (all blocks in one chunk
+  // of KC; otherwise null and the rows are read back from global memory)
+  extern __shared__ __align__(16) unsigned char nv_raw[];
+  T* nvs = a.stage_rows ? reinterpret_cast<T*>(nv_raw) : nullptr;
 
   const int c = threadIdx.x;
   const int y = threadIdx.y;
@@ -695,7 +739,7 @@ __global__ void __launch_bounds__(128) k_update(const __grid_constant__ UpdArgs<
   const T wC = wsh[K];
 
   for (int p0 = 0; p0 < a.gr; p0 += TY) {
-    const int64_t i = row0 + p0 + y;
+    const int64_t i = (p0 + y < a.gr) ? row0 + p0 + y : INT64_MAX;  // rows past the chunk belong to the next CTA
     T sumC = T(0), uhC = T(0), u1C = T(0);
     for (int k0 = 0; k0 < K; k0 += KC) {
       if (nchunk > 1) {
@@ -740,6 +784,7 @@ __global__ void __launch_bounds__(128) k_update(const __grid_constant__ UpdArgs<
             }
             a.U2[k][i * R + c] = u1[kk];
             a.U1[k][i * R + c] = nv;
+            if (nvs) nvs[((size_t)kk * a.gr + p0 + y) * RP + c] = nv;
           } else {
             sumC += g;
             uhC = uhat;
@@ -759,6 +804,7 @@ __global__ void __launch_bounds__(128) k_update(const __grid_constant__ UpdArgs<
         const int R = a.R[k];
         a.U2[k][i * R + c] = u1C;
         a.U1[k][i * R + c] = nv;
+        if (nvs) nvs[((size_t)k * a.gr + p0 + y) * RP + c] = nv;
       }
     }
   }
@@ -771,8 +817,136 @@ __global__ void __launch_bounds__(128) k_update(const __grid_constant__ UpdArgs<
     const int64_t I = a.I[k];
     if (ra < R && rb < R && row0 < I) {
       const int rows = (int)min((int64_t)a.gr, I - row0);
-      a.Gp[((size_t)k * a.gnc + blockIdx.x) * a.rr + ra * R + rb] =
-          (double)gram_chain<T>(a.U1[k], row0, rows, R, ra, rb);
+      T gv;
+      if (nvs) {
+        const T* Uk = nvs + (size_t)k * a.gr * RP;
+        gv = T(0);
+        for (int ii = 0; ii < rows; ++ii) gv = fma(Uk[ii * RP + ra], Uk[ii * RP + rb], gv);
+      } else {
+        gv = gram_chain<T>(a.U1[k], row0, rows, R, ra, rb);
+      }
+      a.Gp[((size_t)k * a.gnc + blockIdx.x) * a.rr + ra * R + rb] = (double)gv;
+    }
+  }
+}
+
+// The same update with one thread per (column c, block k, row y): the loads
+// of a pass are issued together, the shared-column gradient sum is formed in
+// shared memory in block order, and the CTA's new rows stay in shared memory
+// for the Gram chunk values.
+template <typename T, int RP>
+__global__ void __launch_bounds__(512) k_update_kp(const __grid_constant__ UpdArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int K = a.K, Ln = a.Ln, n = a.n;
+  const int c = threadIdx.x, k = threadIdx.y, y = threadIdx.z, TY = blockDim.z;
+  const int tid = c + RP * (k + K * y);
+  const int NT = RP * K * TY;
+  T* Hs = reinterpret_cast<T*>(sm_raw);       // [K][RP][RP]
+  T* uh = Hs + (size_t)K * RP * RP;           // [TY][K][RP]
+  T* gC = uh + (size_t)TY * K * RP;           // [TY][K][RP]
+  T* nvs = gC + (size_t)TY * K * RP;          // [K][gr][RP]
+  __shared__ T wsh[CNCPD_KMAX + 1];
+  __shared__ T Lsh[CNCPD_KMAX];
+  __shared__ T LCsh;
+  DevScalars* sc = a.sc;
+  const int64_t row0 = (int64_t)blockIdx.x * a.gr;
+  const int R = a.R[k];
+  const int64_t I = a.I[k];
+
+  // H of every block (zero-padded to RP x RP)
+#pragma unroll 4
+  for (int e = tid; e < K * RP * RP; e += NT) {
+    const int kk = e / (RP * RP), q = e % (RP * RP);
+    const int ra = q / RP, rb = q % RP;
+    const int Rk = a.R[kk];
+    Hs[e] = (ra < Rk && rb < Rk) ? a.H[kk][ra * Rk + rb] : T(0);
+  }
+  // extrapolation weights (Eqs. eqextrawu and reading R3), one per block
+  if (tid <= K) {
+    const double w_hat = a.use_w ? sc->w_hat : 0.0;
+    const int have_prev = sc->have_prev;
+    if (tid < K) {
+      const double Lc = sc->Lcur_u[n][tid];
+      wsh[tid] = extrap_weight<T>(w_hat, have_prev, sc->Lprev_u[n][tid], Lc, a.delta_w);
+      Lsh[tid] = Lc > 0.0 ? (T)Lc : T(0);
+    } else {
+      double LC = 0.0;
+#pragma unroll 8
+      for (int kk = 0; kk < K; ++kk) LC += sc->Lcur_u[n][kk];
+      wsh[K] = extrap_weight<T>(w_hat, have_prev, sc->LCprev[n], LC, a.delta_w);
+      LCsh = LC > 0.0 ? (T)LC : T(0);
+      if (blockIdx.x == 0) {
+        sc->LCcur[n] = LC;
+        sc->have_cur = 1;
+      }
+    }
+  }
+  const T lam = (a.use_core && c < R) ? (T)sc->lam1[k][c] : T(1);
+  for (int p0 = 0; p0 < a.gr; p0 += TY) {
+    const bool inchunk = p0 + y < a.gr;
+    const int64_t i = row0 + p0 + y;
+    const bool valid = inchunk && i < I && c < R;
+    const size_t off = valid ? (size_t)i * R + c : 0;
+    const T u1 = valid ? a.U1[k][off] : T(0);
+    const T u2 = valid ? a.U2[k][off] : T(0);
+    const T mv = valid ? a.M[k][off] : T(0);
+    __syncthreads();  // weights and H staged; the previous pass is done with uh / gC
+    const T w = (c < Ln) ? wsh[K] : wsh[k];
+    const T uhat = u1 + w * (u1 - u2);
+    uh[((size_t)y * K + k) * RP + c] = valid ? uhat : T(0);
+    __syncthreads();
+    if (valid) {
+      const T* uy = uh + ((size_t)y * K + k) * RP;
+      const T* Hk = Hs + (size_t)k * RP * RP + c;
+      T g = -mv * lam;
+#pragma unroll
+      for (int q = 0; q < RP; ++q) g = fma(uy[q], Hk[q * RP], g);
+      if (c >= Ln) {
+        T nv = u1;
+        const T Lk = Lsh[k];
+        if (Lk > T(0)) {
+          nv = uhat - g / Lk;
+          if (a.nonneg) nv = nv > T(0) ? nv : T(0);
+        }
+        a.U2[k][off] = u1;
+        a.U1[k][off] = nv;
+        nvs[((size_t)k * a.gr + p0 + y) * RP + c] = nv;
+      } else {
+        gC[((size_t)y * K + k) * RP + c] = g;
+      }
+    }
+    __syncthreads();
+    if (k == 0 && valid && c < Ln) {
+      // shared columns: one step from the sum of every block's gradient
+      T s = T(0);
+      for (int kk = 0; kk < K; ++kk) s += gC[((size_t)y * K + kk) * RP + c];
+      T nv = u1;
+      const T LC = LCsh;
+      if (LC > T(0)) {
+        nv = uhat - s / LC;
+        if (a.nonneg) nv = nv > T(0) ? nv : T(0);
+      }
+      for (int kk = 0; kk < K; ++kk) {
+        const size_t o = (size_t)i * a.R[kk] + c;
+        a.U2[kk][o] = u1;
+        a.U1[kk][o] = nv;
+        nvs[((size_t)kk * a.gr + p0 + y) * RP + c] = nv;
+      }
+    }
+  }
+  if (!a.Gp) return;
+  __syncthreads();
+  for (int e = tid; e < K * RP * RP; e += NT) {
+    const int kk = e / (RP * RP), q = e % (RP * RP);
+    const int ra = q / RP, rb = q % RP;
+    const int Rk = a.R[kk];
+    const int64_t Ik = a.I[kk];
+    if (ra < Rk && rb < Rk && row0 < Ik) {
+      const int rows = (int)min((int64_t)a.gr, Ik - row0);
+      const T* Uk = nvs + (size_t)kk * a.gr * RP;
+      T gv = T(0);
+      for (int ii = 0; ii < rows; ++ii) gv = fma(Uk[ii * RP + ra], Uk[ii * RP + rb], gv);
+      a.Gp[((size_t)kk * a.gnc + blockIdx.x) * a.rr + ra * Rk + rb] = (double)gv;
     }
   }
 }
@@ -792,12 +966,12 @@ static cudaError_t update_impl(const LaunchCfg& c, const DevDesc& hd, int n, int
   a.rr = hd.Rmax * hd.Rmax;
   int64_t imax = 0;
   for (int k = 0; k < hd.K; ++k) imax = std::max<int64_t>(imax, hd.dims[k][n]);
+  const UpdGeom geo = update_geometry(RP, hd.K, imax, sizeof(T));
+  a.gr = geo.gr;
   if (hd.Gp[n]) {
     a.Gp = hd.Gp[n];
-    a.gr = hd.gr[n];
     a.gnc = hd.gnc[n];
-  } else {
-    a.gr = gram_chunk_rows(RP, imax);
+    if (hd.gr[n] != geo.gr) return cudaErrorInvalidValue;  // chunking must match the partial buffers
   }
   for (int k = 0; k < hd.K; ++k) {
     a.R[k] = hd.R[k];
@@ -808,7 +982,24 @@ static cudaError_t update_impl(const LaunchCfg& c, const DevDesc& hd, int n, int
     a.H[k] = reinterpret_cast<const T*>(hd.Hbase) + (size_t)k * a.rr;
   }
   const unsigned grid = (unsigned)((imax + a.gr - 1) / a.gr);
-  k_update<T, RP><<<grid, dim3(RP, UpdCfg<T, RP>::ROWS), 0, c.stream>>>(a);
+  if (geo.kp) {
+    a.stage_rows = 1;
+    cudaError_t e = allow_smem(k_update_kp<T, RP>, geo.smem);
+    if (e != cudaSuccess) return e;
+    carve<k_update_kp<T, RP>>();
+    k_update_kp<T, RP><<<grid, dim3(RP, hd.K, geo.ty), geo.smem, c.stream>>>(a);
+    return cudaGetLastError();
+  }
+  size_t dyn = 0;
+  if (a.Gp && hd.K <= UpdCfg<T, RP>::KC) {
+    dyn = (size_t)hd.K * a.gr * RP * sizeof(T);
+    if (dyn <= 96 * 1024) a.stage_rows = 1;
+    else dyn = 0;
+  }
+  cudaError_t e = allow_smem(k_update<T, RP>, dyn);
+  if (e != cudaSuccess) return e;
+  carve<k_update<T, RP>>();
+  k_update<T, RP><<<grid, dim3(RP, UpdCfg<T, RP>::ROWS), dyn, c.stream>>>(a);
   return cudaGetLastError();
 }
 
@@ -854,19 +1045,23 @@ __global__ void __launch_bounds__(256) k_objective(const __grid_constant__ ObjAr
   const int rr = a.rr;
   double* Gk = a.G + (size_t)k * N * rr;
   // <M, U> per column, FP64
-  double acc = 0.0;
+  // (an FMA chain in the factor type per thread, the chains added in FP64)
+  T acc_t = T(0);
   if (r < R && y < Y) {
-    int64_t i = y;
-    for (; i + 3 * Y < I; i += 4 * Y) {
-      const T m0 = M[i * R + r], m1 = M[(i + Y) * R + r], m2 = M[(i + 2 * Y) * R + r], m3 = M[(i + 3 * Y) * R + r];
-      const T u0 = U[i * R + r], u1 = U[(i + Y) * R + r], u2 = U[(i + 2 * Y) * R + r], u3 = U[(i + 3 * Y) * R + r];
-      acc = fma((double)m0, (double)u0, acc);
-      acc = fma((double)m1, (double)u1, acc);
-      acc = fma((double)m2, (double)u2, acc);
-      acc = fma((double)m3, (double)u3, acc);
+    for (int64_t i0 = y; i0 < I; i0 += 16 * Y) {
+      T mv[16], uv[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int64_t i = min(i0 + (int64_t)j * Y, I - 1);  // clamped: every load issues at once
+        mv[j] = M[i * R + r];
+        uv[j] = U[i * R + r];
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (i0 + (int64_t)j * Y < I) acc_t = fma(mv[j], uv[j], acc_t);
     }
-    for (; i < I; i += Y) acc = fma((double)M[i * R + r], (double)U[i * R + r], acc);
   }
+  const double acc = (double)acc_t;
   // ||X_hat||^2 terms; the Gram of the last mode is summed from its chunks
   double xx = 0.0;
   const int nch = a.reduce_last ? (int)((I + a.gr - 1) / a.gr) : 0;
@@ -956,6 +1151,7 @@ static cudaError_t objective_impl(const LaunchCfg& c, const DevDesc& hd, int com
     a.M[k] = reinterpret_cast<const T*>(hd.M[k][n]);
     a.U[k] = reinterpret_cast<const T*>(hd.U1[k][n]);
   }
+  carve<k_objective<T, RP>>();
   k_objective<T, RP><<<hd.K, 256, 0, c.stream>>>(a);
   return cudaGetLastError();
 }
@@ -1016,6 +1212,7 @@ static cudaError_t core_impl(const LaunchCfg& c, const DevDesc* dd, const DevDes
   const size_t sm = lip_smem_bytes<RP>();
   cudaError_t e = allow_smem(k_core_update<RP>, sm);
   if (e != cudaSuccess) return e;
+  carve<k_core_update<RP>>();
   k_core_update<RP><<<hd.K, 256, sm, c.stream>>>(dd, use_w, delta_w);
   return cudaGetLastError();
 }
@@ -1089,11 +1286,13 @@ cudaError_t launch_iter_begin(const LaunchCfg& c, const DevDesc* dd, const DevDe
   const int need = hd.N * hd.K + hd.N + hd.K + 1;
   int nt = 256;
   while (nt < need && nt < 1024) nt *= 2;
+  carve<k_iter_begin>();
   k_iter_begin<<<1, nt, 0, c.stream>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_redo_prepare(const LaunchCfg& c, const DevDesc* dd, const DevDesc&) {
+  carve<k_redo_prepare>();
   k_redo_prepare<<<1, 256, 0, c.stream>>>(dd);
   return cudaGetLastError();
 }
