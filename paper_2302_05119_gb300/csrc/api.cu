@@ -426,6 +426,10 @@ int initialise(cncpd_ctx* c) {
     TRY(sync(c));
     for (int k = 0; k < c->K; ++k) s->xnorm2[k] = xt[k];
   }
+  for (int k = 0; k < c->K; ++k) {
+    s->inv_xnorm2[k] = s->xnorm2[k] > 0.0 ? 1.0 / s->xnorm2[k] : 0.0;
+    s->inv_xnorm2_orig[k] = s->xnorm2_orig[k] > 0.0 ? 1.0 / s->xnorm2_orig[k] : 0.0;
+  }
   CU(cudaMemcpyAsync(c->sc, buf.data(), sizeof(DevScalars), cudaMemcpyHostToDevice, c->stream));
   CU(launch_gram(lc, c->dd, c->hd, c->fp64, 0, c->N, 0));
   const int n = c->N - 1;
@@ -790,7 +794,7 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
     for (int k = 0; k < K; ++k) imax = std::max<int64_t>(imax, c->dim(k, n));
     d.gr[n] = gram_chunk_rows(c->RP, K, imax, c->fp64);
     d.gnc[n] = (int)((imax + d.gr[n] - 1) / d.gr[n]);
-    CTRY(dalloc(c, (void**)&d.Gp[n], (size_t)K * d.gnc[n] * rr * sizeof(double)));
+    CTRY(dalloc(c, &d.Gp[n], (size_t)K * d.gnc[n] * rr * c->fsz));
   }
   for (int k = 0; k < K; ++k)
     for (int n = 0; n < N; ++n) {

@@ -55,6 +55,8 @@ struct DevScalars {
   double lam2[CNCPD_KMAX][CNCPD_RMAX];
   double lamS[CNCPD_KMAX][CNCPD_RMAX];
   double xnorm2_orig[CNCPD_KMAX];          // ||X^(k)||^2 of the stored tensors (global fit)
+  double inv_xnorm2[CNCPD_KMAX];           // 1 / xnorm2 and 1 / xnorm2_orig (0 for a zero tensor)
+  double inv_xnorm2_orig[CNCPD_KMAX];
   double out_relk[CNCPD_KMAX];             // per-block relative error of an uncommitted evaluation
   int done_counter[CNCPD_NMAX + 2];        // arrival counters of last-CTA reductions (reset by the last CTA)
 };
@@ -109,8 +111,8 @@ struct DevDesc {
   void* Hbase;
   // Gram partials of each mode (null: Grams are formed by one CTA per factor).
   // Rows of U^(n,k) are cut into chunks of gr[n] rows; chunk c of block k
-  // holds the FP64-stored partial sums at Gp[n] + (k*gnc[n] + c)*Rmax^2.
-  double* Gp[CNCPD_NMAX];
+  // holds its partial sums, in the factor type, at Gp[n] + (k*gnc[n] + c)*Rmax^2.
+  void* Gp[CNCPD_NMAX];
   int gr[CNCPD_NMAX];
   int gnc[CNCPD_NMAX];
 };

@@ -22,7 +22,7 @@ struct LipArgs {            // H^(n,k) and L^(n,k) for every block
   DevScalars* sc;
   double* G;                // Gram arena: G^(m,k) at G + (k*N + m)*rr
   T* H;                     // H arena: H^(k) at H + k*rr
-  const double* Gp_prev;    // partials of mode prev
+  const T* Gp_prev;         // partials of mode prev
   int R[CNCPD_KMAX];
   int Iprev[CNCPD_KMAX];
 };
@@ -44,7 +44,7 @@ struct UpdArgs {            // fused APG update of mode n
   int rr, stage_rows;       // stage_rows: the CTA keeps its new rows in shared memory
   double delta_w;
   DevScalars* sc;
-  double* Gp;               // Gram partials of mode n (written)
+  T* Gp;                    // Gram partials of mode n (written)
   int R[CNCPD_KMAX];
   int I[CNCPD_KMAX];
   T* U1[CNCPD_KMAX];
@@ -59,7 +59,7 @@ struct ObjArgs {            // objective with the last mode just updated
   int gr, commit, reduce_last, pad;
   DevScalars* sc;
   double* G;
-  const double* Gp_last;
+  const T* Gp_last;
   int R[CNCPD_KMAX];
   int I[CNCPD_KMAX];
   const T* M[CNCPD_KMAX];
@@ -78,6 +78,7 @@ struct ObjArgs {            // objective with the last mode just updated
 // ---------------------------------------------------------------------------
 template <int RP>
 struct LmaxSmem {
+  float Hf[RP * RP];  // H in FP32 (R x R, row stride R), written by the caller
   float A[RP * RP];
   float B[RP * RP];
   double v[RP];
@@ -94,24 +95,25 @@ __host__ __device__ constexpr size_t lip_smem_bytes() {
 
 template <typename TT, int RP>
 __device__ double lmax_rp(const double* Hs, int R, LmaxSmem<RP>* s) {
+  // Hs: H in FP64 (read only when TT is double); s->Hf: H in FP32
   constexpr int RR = RP * RP;
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
   const int nt = blockDim.x * blockDim.y;
   __syncthreads();
-  if (tid == 0) {  // FP64 is slow on this part: one thread forms the trace and its inverse
-    double t = 0.0;
-    for (int i = 0; i < R; ++i) t += Hs[i * R + i];
-    s->scal[0] = t;
-    s->scal[1] = (t > 0.0 && isfinite(t)) ? 1.0 / t : 0.0;
+  if (tid == 0) {  // one thread forms the trace and its inverse
+    float t = 0.f;
+    for (int i = 0; i < R; ++i) t += s->Hf[i * R + i];
+    s->red[0] = t;
+    s->red[1] = (t > 0.f && isfinite(t)) ? 1.f / t : 0.f;
   }
   __syncthreads();
-  const double tr = s->scal[0];
-  if (!isfinite(tr)) return tr;
-  if (!(tr > 0.0)) return 0.0;
-  const double itr = s->scal[1];
+  const float tr = s->red[0];
+  if (!isfinite(tr)) return (double)tr;
+  if (!(tr > 0.f)) return 0.0;
+  const float itr = s->red[1];
   for (int e = tid; e < RR; e += nt) {
     const int i = e / RP, j = e % RP;
-    s->A[e] = (i < R && j < R) ? (float)(Hs[i * R + j] * itr) : 0.f;
+    s->A[e] = (i < R && j < R) ? s->Hf[i * R + j] * itr : 0.f;
   }
   __syncthreads();
   for (int it = 0; it < 32; ++it) {
@@ -147,24 +149,24 @@ __device__ double lmax_rp(const double* Hs, int R, LmaxSmem<RP>* s) {
     __syncthreads();
     if (!(trb > 0.f) || m < 4e-6f) break;
   }
-  // v: the column of the limit with the largest diagonal entry
+  // v: the column of the limit with the largest diagonal entry; warp 0 forms
+  // the Rayleigh quotient v^T H v / v^T v
   int jm = 0;
   float dm = -1.f;
   for (int i = 0; i < R; ++i)
     if (s->A[i * RP + i] > dm) { dm = s->A[i * RP + i]; jm = i; }
-  for (int i = tid; i < R; i += nt) {
-    const TT vi = (TT)s->A[i * RP + jm];
-    TT acc = TT(0);
-    for (int l = 0; l < R; ++l) acc = fma((TT)Hs[i * R + l], (TT)s->A[l * RP + jm], acc);
-    s->v[i] = (double)(vi * acc);  // v_i (H v)_i
-    s->w[i] = (double)(vi * vi);   // v_i^2
-  }
-  __syncthreads();
   if (tid < 32) {
     TT num = TT(0), den = TT(0);
     for (int i = tid; i < R; i += 32) {
-      num += (TT)s->v[i];
-      den += (TT)s->w[i];
+      const TT vi = (TT)s->A[i * RP + jm];
+      TT acc = TT(0);
+      if constexpr (sizeof(TT) == 4) {
+        for (int l = 0; l < R; ++l) acc = fma(s->Hf[i * R + l], s->A[l * RP + jm], acc);
+      } else {
+        for (int l = 0; l < R; ++l) acc = fma(Hs[i * R + l], (TT)s->A[l * RP + jm], acc);
+      }
+      num = fma(vi, acc, num);
+      den = fma(vi, vi, den);
     }
     for (int o = 16; o > 0; o >>= 1) {
       num += __shfl_xor_sync(0xffffffffu, num, o);
@@ -211,19 +213,43 @@ __device__ __forceinline__ T gram_chain(const T* U, int64_t row0, int rows, int 
   return s;
 }
 
-// Sum of the first nch chunk values of entry p (stride rr), in chunk order;
-// the loads of up to 32 chunks are issued before any of them is added.
-__device__ __forceinline__ double gram_sum(const double* __restrict__ gp, int nch, int rr, int p) {
-  double s = 0.0;
-  for (int c0 = 0; c0 < nch; c0 += 32) {
-    double x[32];
+// Compensated FP32 addition (hi, lo) += x (Knuth's TwoSum); FP64 is slow on
+// this part, and a pair of FP32 values carries about 48 bits.
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  lo += (hi - (s - bp)) + (x - bp);
+  hi = s;
+}
+
+// Sum of the first nch chunk values of entry p (stride rr), in chunk order
+// (compensated FP32 for FP32 factors, FP64 otherwise); the loads of up to 32
+// chunks are issued before any of them is added.
+template <typename T>
+__device__ __forceinline__ double gram_sum(const T* __restrict__ gp, int nch, int rr, int p) {
+  if constexpr (sizeof(T) == 4) {
+    float hi = 0.f, lo = 0.f;
+    for (int c0 = 0; c0 < nch; c0 += 32) {
+      float x[32];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) x[j] = gp[(size_t)min(c0 + j, nch - 1) * rr + p];  // clamped: no predicate
+      for (int j = 0; j < 32; ++j) x[j] = gp[(size_t)min(c0 + j, nch - 1) * rr + p];  // clamped: no predicate
 #pragma unroll
-    for (int j = 0; j < 32; ++j)
-      if (c0 + j < nch) s += x[j];
+      for (int j = 0; j < 32; ++j)
+        if (c0 + j < nch) ff_add(hi, lo, x[j]);
+    }
+    return (double)hi + (double)lo;
+  } else {
+    double s = 0.0;
+    for (int c0 = 0; c0 < nch; c0 += 32) {
+      double x[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) x[j] = gp[(size_t)min(c0 + j, nch - 1) * rr + p];
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (c0 + j < nch) s += x[j];
+    }
+    return s;
   }
-  return s;
 }
 
 template <typename T>
@@ -239,19 +265,20 @@ __global__ void __launch_bounds__(256) k_gram_chunks(const DevDesc* __restrict__
   const int R = d->R[k];
   const int rr = d->Rmax * d->Rmax;
   const T* U = reinterpret_cast<const T*>(d->U1[k][n]);
-  double* out = d->Gp[n] + ((size_t)k * d->gnc[n] + c) * rr;
-  for (int p = threadIdx.x; p < R * R; p += blockDim.x) out[p] = (double)gram_chain<T>(U, row0, rows, R, p / R, p % R);
+  T* out = reinterpret_cast<T*>(d->Gp[n]) + ((size_t)k * d->gnc[n] + c) * rr;
+  for (int p = threadIdx.x; p < R * R; p += blockDim.x) out[p] = gram_chain<T>(U, row0, rows, R, p / R, p % R);
 }
 
+template <typename T>
 __global__ void __launch_bounds__(256) k_gram_reduce(const DevDesc* __restrict__ d, int n0, int n1) {
   const int nm = n1 - n0;
   const int k = blockIdx.x / nm, n = n0 + blockIdx.x % nm;
   const int R = d->R[k];
   const int rr = d->Rmax * d->Rmax;
   const int nch = (int)((d->dims[k][n] + d->gr[n] - 1) / d->gr[n]);
-  const double* gp = d->Gp[n] + (size_t)k * d->gnc[n] * rr;
+  const T* gp = reinterpret_cast<const T*>(d->Gp[n]) + (size_t)k * d->gnc[n] * rr;
   double* G = d->G[k][n];
-  for (int p = threadIdx.x; p < R * R; p += blockDim.x) G[p] = gram_sum(gp, nch, rr, p);
+  for (int p = threadIdx.x; p < R * R; p += blockDim.x) G[p] = gram_sum<T>(gp, nch, rr, p);
 }
 
 // Gram of one I x R factor by one CTA (factors without chunk partials: the
@@ -326,8 +353,13 @@ cudaError_t launch_gram(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    carve<k_gram_reduce>();
-    k_gram_reduce<<<hd.K * nm, 256, 0, c.stream>>>(dd, n_begin, n_end);
+    if (fp64) {
+      carve<k_gram_reduce<double>>();
+      k_gram_reduce<double><<<hd.K * nm, 256, 0, c.stream>>>(dd, n_begin, n_end);
+    } else {
+      carve<k_gram_reduce<float>>();
+      k_gram_reduce<float><<<hd.K * nm, 256, 0, c.stream>>>(dd, n_begin, n_end);
+    }
     return cudaGetLastError();
   }
   const int grid = hd.K * nm;
@@ -386,13 +418,13 @@ __device__ void lip_body(const LipArgs<T>& a, int k, unsigned char* smem) {
   double* Gk = a.G + (size_t)k * N * rr;
   DevScalars* sc = a.sc;
   const int nch = prev >= 0 ? (a.Iprev[k] + a.gr_prev - 1) / a.gr_prev : 0;
-  const double* gp = prev >= 0 ? a.Gp_prev + (size_t)k * a.gnc_prev * rr : nullptr;
+  const T* gp = prev >= 0 ? a.Gp_prev + (size_t)k * a.gnc_prev * rr : nullptr;
   for (int p = tid; p < R * R; p += nt) {
     double gm[CNCPD_NMAX];
 #pragma unroll
     for (int m = 0; m < CNCPD_NMAX; ++m) gm[m] = (m < N && m != n && m != prev) ? Gk[(size_t)m * rr + p] : 1.0;
     if (prev >= 0) {
-      const double g = gram_sum(gp, nch, rr, p);
+      const double g = gram_sum<T>(gp, nch, rr, p);
       Gk[(size_t)prev * rr + p] = g;
 #pragma unroll
       for (int m = 0; m < CNCPD_NMAX; ++m)
@@ -403,7 +435,8 @@ __device__ void lip_body(const LipArgs<T>& a, int k, unsigned char* smem) {
     for (int m = 0; m < CNCPD_NMAX; ++m)
       if (m < N && m != n) h *= gm[m];
     if (a.use_core) h *= sc->lam1[k][p / R] * sc->lam1[k][p % R];
-    Hs[p] = h;
+    if constexpr (sizeof(T) == 8) Hs[p] = h;
+    ls->Hf[p] = (float)h;
     a.H[(size_t)k * rr + p] = (T)h;
   }
   if (!a.want_L) return;
@@ -540,7 +573,7 @@ static LipArgs<T> lip_args(const DevDesc& hd, int n, int use_core, int prev, int
   a.G = hd.Gbase;
   a.H = reinterpret_cast<T*>(hd.Hbase);
   if (a.prev >= 0) {
-    a.Gp_prev = hd.Gp[prev];
+    a.Gp_prev = reinterpret_cast<const T*>(hd.Gp[prev]);
     a.gnc_prev = hd.gnc[prev];
     a.gr_prev = hd.gr[prev];
   }
@@ -825,7 +858,7 @@ __global__ void __launch_bounds__(128) k_update(const __grid_constant__ UpdArgs<
       } else {
         gv = gram_chain<T>(a.U1[k], row0, rows, R, ra, rb);
       }
-      a.Gp[((size_t)k * a.gnc + blockIdx.x) * a.rr + ra * R + rb] = (double)gv;
+      a.Gp[((size_t)k * a.gnc + blockIdx.x) * a.rr + ra * R + rb] = gv;
     }
   }
 }
@@ -946,7 +979,7 @@ __global__ void __launch_bounds__(512) k_update_kp(const __grid_constant__ UpdAr
       const T* Uk = nvs + (size_t)kk * a.gr * RP;
       T gv = T(0);
       for (int ii = 0; ii < rows; ++ii) gv = fma(Uk[ii * RP + ra], Uk[ii * RP + rb], gv);
-      a.Gp[((size_t)kk * a.gnc + blockIdx.x) * a.rr + ra * Rk + rb] = (double)gv;
+      a.Gp[((size_t)kk * a.gnc + blockIdx.x) * a.rr + ra * Rk + rb] = gv;
     }
   }
 }
@@ -969,7 +1002,7 @@ static cudaError_t update_impl(const LaunchCfg& c, const DevDesc& hd, int n, int
   const UpdGeom geo = update_geometry(RP, hd.K, imax, sizeof(T));
   a.gr = geo.gr;
   if (hd.Gp[n]) {
-    a.Gp = hd.Gp[n];
+    a.Gp = reinterpret_cast<T*>(hd.Gp[n]);
     a.gnc = hd.gnc[n];
     if (hd.gr[n] != geo.gr) return cudaErrorInvalidValue;  // chunking must match the partial buffers
   }
@@ -1035,8 +1068,9 @@ __global__ void __launch_bounds__(256) k_objective(const __grid_constant__ ObjAr
   const int N = a.N, n = N - 1;
   const int k = blockIdx.x;
   DevScalars* sc = a.sc;
-  __shared__ double red[256];
+  __shared__ T red[256];
   __shared__ double cr[RP];
+  __shared__ double wsum[2][8];
   __shared__ int is_last;
   const int R = a.R[k];
   const int64_t I = a.I[k];
@@ -1044,8 +1078,7 @@ __global__ void __launch_bounds__(256) k_objective(const __grid_constant__ ObjAr
   const T* __restrict__ U = a.U[k];
   const int rr = a.rr;
   double* Gk = a.G + (size_t)k * N * rr;
-  // <M, U> per column, FP64
-  // (an FMA chain in the factor type per thread, the chains added in FP64)
+  // <M, U> per column: an FMA chain in the factor type per thread
   T acc_t = T(0);
   if (r < R && y < Y) {
     for (int64_t i0 = y; i0 < I; i0 += 16 * Y) {
@@ -1061,17 +1094,16 @@ __global__ void __launch_bounds__(256) k_objective(const __grid_constant__ ObjAr
         if (i0 + (int64_t)j * Y < I) acc_t = fma(mv[j], uv[j], acc_t);
     }
   }
-  const double acc = (double)acc_t;
-  // ||X_hat||^2 terms; the Gram of the last mode is summed from its chunks
+  // ||X_hat||^2 terms in FP64; the Gram of the last mode is summed from its chunks
   double xx = 0.0;
   const int nch = a.reduce_last ? (int)((I + a.gr - 1) / a.gr) : 0;
-  const double* gp = a.reduce_last ? a.Gp_last + (size_t)k * a.gnc * rr : nullptr;
+  const T* gp = a.reduce_last ? a.Gp_last + (size_t)k * a.gnc * rr : nullptr;
   for (int p = tid; p < R * R; p += 256) {
     double gm[CNCPD_NMAX];
 #pragma unroll
     for (int m = 0; m < CNCPD_NMAX; ++m) gm[m] = (m < N && !(a.reduce_last && m == n)) ? Gk[(size_t)m * rr + p] : 1.0;
     if (a.reduce_last) {
-      const double g = gram_sum(gp, nch, rr, p);
+      const double g = gram_sum<T>(gp, nch, rr, p);
       Gk[(size_t)n * rr + p] = g;
 #pragma unroll
       for (int m = 0; m < CNCPD_NMAX; ++m)
@@ -1083,26 +1115,54 @@ __global__ void __launch_bounds__(256) k_objective(const __grid_constant__ ObjAr
       if (m < N) g *= gm[m];
     xx += g;
   }
-  if (tid < NT) red[tid] = acc;
+  if (tid < NT) red[tid] = acc_t;
   __syncthreads();
-  if (y == 0) {
-    double s = 0.0;
-    for (int yy = 0; yy < Y; ++yy) s += red[yy * RP + r];
+  if (y == 0 && r < R) {
+    // the Y chains of column r, added in order
+    double s;
+    if constexpr (sizeof(T) == 4) {
+      float hi = 0.f, lo = 0.f;
+      for (int yy = 0; yy < Y; ++yy) ff_add(hi, lo, red[yy * RP + r]);
+      s = (double)hi + (double)lo;
+    } else {
+      s = 0.0;
+      for (int yy = 0; yy < Y; ++yy) s += red[yy * RP + r];
+    }
     cr[r] = s;
-    if (r < R && a.commit) sc->cterm[k][r] = s;
+    if (a.commit) sc->cterm[k][r] = s;
   }
   __syncthreads();
+  // ||X_hat||^2 - 2 <X, X_hat> over the CTA: for FP32 factors in compensated
+  // FP32 pairs (FP64 adds are slow here), FP64 only for the last additions
   if (tid < R) xx -= 2.0 * sc->lam1[k][tid] * cr[tid];
-  for (int o = 16; o > 0; o >>= 1) xx += __shfl_xor_sync(0xffffffffu, xx, o);
-  __syncthreads();
-  if ((tid & 31) == 0) red[tid >> 5] = xx;
+  if constexpr (sizeof(T) == 4) {
+    float hi = (float)xx;
+    float lo = (float)(xx - (double)hi);
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
+      const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
+      ff_add(hi, lo, oh);
+      lo += ol;
+    }
+    if ((tid & 31) == 0) {
+      wsum[0][tid >> 5] = (double)hi;
+      wsum[1][tid >> 5] = (double)lo;
+    }
+  } else {
+    for (int o = 16; o > 0; o >>= 1) xx += __shfl_xor_sync(0xffffffffu, xx, o);
+    if ((tid & 31) == 0) {
+      wsum[0][tid >> 5] = xx;
+      wsum[1][tid >> 5] = 0.0;
+    }
+  }
   __syncthreads();
   if (tid == 0) {
     double t = 0.0;
-    for (int q = 0; q < 8; ++q) t += red[q];
+    for (int q = 0; q < 8; ++q) t += wsum[0][q] + wsum[1][q];
     const double x2 = a.commit ? sc->xnorm2[k] : sc->xnorm2_orig[k];
+    const double ix2 = a.commit ? sc->inv_xnorm2[k] : sc->inv_xnorm2_orig[k];
     const double Fk = 0.5 * (x2 + t);
-    const double rel = x2 > 0.0 ? sqrt(fmax(2.0 * Fk, 0.0) / x2) : 0.0;
+    const double rel = sqrt(fmax(2.0 * Fk, 0.0) * ix2);
     if (a.commit) {
       sc->Fk[k] = Fk;
       sc->relk[k] = rel;
@@ -1141,7 +1201,7 @@ static cudaError_t objective_impl(const LaunchCfg& c, const DevDesc& hd, int com
   a.sc = hd.sc;
   a.G = hd.Gbase;
   if (a.reduce_last) {
-    a.Gp_last = hd.Gp[n];
+    a.Gp_last = reinterpret_cast<const T*>(hd.Gp[n]);
     a.gnc = hd.gnc[n];
     a.gr = hd.gr[n];
   }
@@ -1185,6 +1245,7 @@ __global__ void __launch_bounds__(256) k_core_update(const DevDesc* __restrict__
     double h = 1.0;
     for (int m = 0; m < N; ++m) h *= d->G[k][m][e];
     Hs[e] = h;
+    ls->Hf[e] = (float)h;
   }
   const double Ld = lmax_rp<double, RP>(Hs, R, ls);
   const double w = extrap_weight<double>(use_w ? sc->w_hat : 0.0, sc->have_prev, sc->Ldprev[k], Ld, delta_w);
@@ -1466,7 +1527,10 @@ __global__ void k_lmax_one(const double* H, int R, double* out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* Hs = reinterpret_cast<double*>(smem_raw);
   LmaxSmem<RP>* ls = reinterpret_cast<LmaxSmem<RP>*>(smem_raw + (size_t)RP * RP * sizeof(double));
-  for (int e = threadIdx.x; e < R * R; e += blockDim.x) Hs[e] = H[e];
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+    Hs[e] = H[e];
+    ls->Hf[e] = (float)H[e];
+  }
   const double L = lmax_rp<double, RP>(Hs, R, ls);
   if (threadIdx.x == 0) *out = L;
 }
