@@ -64,6 +64,7 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int* err = &d->sc->timeout;
   const CUtensorMap* maps = d->tmap_trail;
+  const uint64_t pol = l2_evict_first_policy();
   if (threadIdx.x == 0) {
     for (int s = 0; s < TST; ++s) {
       mbar_init(smem_u32(&full[s]), 2);  // TMA issuer (with the byte count) + Khatri-Rao warp
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
         const uint32_t ph = (it / TST) & 1;
         if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, err)) { ok = false; break; }
         mbar_arrive_expect_tx(smem_u32(&full[s]), S::X_BYTES);
-        tma_load_2d(smem_u32(xs + s * S::X_BYTES), &maps[k], smem_u32(&full[s]), c * TT_BC, row0);
+        tma_load_2d_hint(smem_u32(xs + s * S::X_BYTES), &maps[k], smem_u32(&full[s]), c * TT_BC, row0, pol);
       }
     }
     // copies still in flight land before the CTA leaves
@@ -275,6 +276,7 @@ __global__ void __launch_bounds__((LT_CONS + NKR + 1) * 32, 1) k_lead_tma(const 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int* err = &d->sc->timeout;
   const CUtensorMap* maps = d->tmap_lead;
+  const uint64_t pol = l2_evict_first_policy();
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
       mbar_init(smem_u32(&full[s]), 2);  // TMA issuer (with the byte count) + Khatri-Rao warp
@@ -306,7 +308,7 @@ __global__ void __launch_bounds__((LT_CONS + NKR + 1) * 32, 1) k_lead_tma(const 
         const uint32_t ph = (it / ST) & 1;
         if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, err)) { ok = false; break; }
         mbar_arrive_expect_tx(smem_u32(&full[s]), S::X_BYTES);
-        tma_load_2d(smem_u32(xs + s * S::X_BYTES), &maps[k], smem_u32(&full[s]), ctile * LT_COLS, r0);
+        tma_load_2d_hint(smem_u32(xs + s * S::X_BYTES), &maps[k], smem_u32(&full[s]), ctile * LT_COLS, r0, pol);
       }
     }
     for (uint32_t i = it > (uint32_t)ST ? it - ST : 0; i < it; ++i)
