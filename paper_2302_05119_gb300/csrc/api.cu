@@ -95,9 +95,15 @@ struct cncpd_ctx {
   double F_prev = 0.0, rel_prev = 0.0;
   int total_iters = 0;
 
-  cudaGraphExec_t g_main = nullptr, g_redo = nullptr;
+  // two main graphs used alternately (each records its own profile events, so
+  // one iteration's pass times are read while the next one runs) and the
+  // re-update graph (event set 2)
+  cudaGraphExec_t g_main[2] = {nullptr, nullptr}, g_redo = nullptr;
   int main_runs = 0, redo_runs = 0;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[3][4] = {};
+  int ev_set = 0;
+  HostMirror* hm = nullptr;      // pinned, mapped; written by the objective kernel
+  HostMirror* hm_dev = nullptr;
   cudaStream_t side = nullptr;                // branch for work independent of a tensor pass
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
@@ -212,9 +218,12 @@ int sync(cncpd_ctx* c) {
 }
 
 void destroy_graphs(cncpd_ctx* c) {
-  if (c->g_main) cudaGraphExecDestroy(c->g_main);
+  for (auto& g : c->g_main) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+  }
   if (c->g_redo) cudaGraphExecDestroy(c->g_redo);
-  c->g_main = c->g_redo = nullptr;
+  c->g_redo = nullptr;
   c->main_runs = c->redo_runs = 0;
 }
 
@@ -239,7 +248,7 @@ int record(cncpd_ctx* c, int which_ev) {
   if (!c->opts.profile) return CNCPD_OK;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   CU(cudaStreamIsCapturing(c->stream, &cs));
-  CU(cudaEventRecordWithFlags(c->ev[which_ev], c->stream,
+  CU(cudaEventRecordWithFlags(c->ev[c->ev_set][which_ev], c->stream,
                               cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault));
   return CNCPD_OK;
 }
@@ -345,12 +354,14 @@ int timeout_error(cncpd_ctx* c) {
   return set_err(CNCPD_ETIMEOUT, "a bounded device-side wait expired (pipeline stalled); iteration state discarded");
 }
 
+// The objective at the end of a sweep publishes F to the host mirror; the
+// LRA objective does not, so that path reads the scalars back.
 int enqueue_main(cncpd_ctx* c) {
   LaunchCfg lc{c->stream, c->num_sms};
   CU(launch_iter_begin(lc, c->dd, c->hd, c->opts.use_core));
   CU(cudaMemcpyAsync(c->AS, c->A2, arena_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
   TRY(enqueue_sweep(c, 1));
-  return enqueue_readback(c);
+  return c->lra ? enqueue_readback(c) : CNCPD_OK;
 }
 
 int enqueue_redo(cncpd_ctx* c) {
@@ -361,7 +372,7 @@ int enqueue_redo(cncpd_ctx* c) {
   CU(launch_gram(lc, c->dd, c->hd, c->fp64, 0, c->N, 0));
   if (c->lra) CU(launch_cross_gram(lc, c->dd, c->hd, c->fp64, 0, c->N));
   TRY(enqueue_sweep(c, 0));
-  return enqueue_readback(c);
+  return c->lra ? enqueue_readback(c) : CNCPD_OK;
 }
 
 int capture(cncpd_ctx* c, int (*fn)(cncpd_ctx*), cudaGraphExec_t* out) {
@@ -382,22 +393,51 @@ int capture(cncpd_ctx* c, int (*fn)(cncpd_ctx*), cudaGraphExec_t* out) {
 
 // The first replay of each kind runs eagerly (so that every kernel's
 // attributes are set outside stream capture); later ones replay the graph.
-int run_main(cncpd_ctx* c) {
+// Main replays alternate between event sets 0 and 1; returns the set used.
+int run_main(cncpd_ctx* c, int* set_used) {
+  const int set = c->main_runs & 1;
+  *set_used = set;
+  c->ev_set = set;
   if (c->opts.use_graph && c->main_runs++ > 0) {
-    if (!c->g_main) TRY(capture(c, enqueue_main, &c->g_main));
-    CU(cudaGraphLaunch(c->g_main, c->stream));
+    if (!c->g_main[set]) TRY(capture(c, enqueue_main, &c->g_main[set]));
+    CU(cudaGraphLaunch(c->g_main[set], c->stream));
     return CNCPD_OK;
   }
   return enqueue_main(c);
 }
 
 int run_redo(cncpd_ctx* c) {
+  c->ev_set = 2;
   if (c->opts.use_graph && c->redo_runs++ > 0) {
     if (!c->g_redo) TRY(capture(c, enqueue_redo, &c->g_redo));
     CU(cudaGraphLaunch(c->g_redo, c->stream));
     return CNCPD_OK;
   }
   return enqueue_redo(c);
+}
+
+// Wait until the objective kernel has published a sequence number other than
+// s0 to the host mirror (or, on the LRA path, until the stream is idle).  The
+// stream is queried now and then, so that a failed launch or a fault ends the
+// wait; a bounded time limit guards against anything else.
+int wait_published(cncpd_ctx* c, unsigned int s0) {
+  if (c->lra) return sync(c);
+  const double t0 = now_s();
+  for (unsigned long n = 1;; ++n) {
+    if (c->hm->seq != s0) {
+      std::atomic_thread_fence(std::memory_order_acquire);
+      return CNCPD_OK;
+    }
+    if ((n & 255) == 0) {
+      const cudaError_t e = cudaStreamQuery(c->stream);
+      if (e == cudaSuccess) {
+        if (c->hm->seq != s0) continue;
+        return set_err(CNCPD_ECUDA, "the sweep finished without publishing its objective");
+      }
+      if (e != cudaErrorNotReady) return set_err(CNCPD_ECUDA, "sweep failed: %s", cudaGetErrorString(e));
+      if (now_s() - t0 > 60.0) return set_err(CNCPD_ETIMEOUT, "a sweep did not finish within 60 s");
+    }
+  }
 }
 
 // Reset the iteration history (first iteration of Algorithm 1) and evaluate
@@ -479,11 +519,12 @@ long long kernels_per_replay(cncpd_ctx* c, int redo) {
   return n;
 }
 
-int read_profile(cncpd_ctx* c, cncpd_stats* st) {
+int read_profile(cncpd_ctx* c, cncpd_stats* st, int set) {
   if (!c->opts.profile || c->lra) return CNCPD_OK;
   float a = 0, b = 0;
-  CU(cudaEventElapsedTime(&a, c->ev[0], c->ev[1]));
-  CU(cudaEventElapsedTime(&b, c->ev[2], c->ev[3]));
+  CU(cudaEventSynchronize(c->ev[set][3]));
+  CU(cudaEventElapsedTime(&a, c->ev[set][0], c->ev[set][1]));
+  CU(cudaEventElapsedTime(&b, c->ev[set][2], c->ev[set][3]));
   st->stream_ms += a + b;
   st->trail_ms += a;
   st->lead_ms += b;
@@ -496,28 +537,41 @@ int run_iterations(cncpd_ctx* c, int n_iters, bool use_eps, cncpd_stats* out) {
   const double t0 = now_s();
   if (c->dirty) TRY(initialise(c));
   const double pb = c->lra ? 0.0 : 2.0 * pass_bytes(c);
+  int pending = -1;  // event set of a main replay whose pass times are not read yet
   for (int it = 0; it < n_iters; ++it) {
-    TRY(run_main(c));
-    TRY(sync(c));
-    TRY(read_profile(c, &st));
+    const unsigned int s0 = c->hm->seq;
+    int set = 0;
+    TRY(run_main(c, &set));
+    // the previous iteration's pass times, read while this one runs
+    if (pending >= 0) TRY(read_profile(c, &st, pending));
+    pending = set;
+    TRY(wait_published(c, s0));
     st.x_bytes += pb;
     st.launches += kernels_per_replay(c, 0);
-    double F = c->hs->F;
+    double F = c->lra ? c->hs->F : c->hm->F;
     const bool redo = c->opts.reupdate && (F - c->F_prev) > 1e-13 * std::fabs(c->F_prev);
     if (redo) {
+      const unsigned int s1 = c->hm->seq;
       TRY(run_redo(c));
-      TRY(sync(c));
-      TRY(read_profile(c, &st));
+      TRY(wait_published(c, s1));
+      TRY(read_profile(c, &st, 2));
       st.x_bytes += pb;
       st.launches += kernels_per_replay(c, 1);
-      F = c->hs->F;
+      F = c->lra ? c->hs->F : c->hm->F;
       st.reupdates++;
     }
-    if (c->hs->timeout) return timeout_error(c);
-    if (c->hs->nonfinite || !std::isfinite(F))
+    const int timeout = c->lra ? c->hs->timeout : c->hm->timeout;
+    const int nonfinite = c->lra ? c->hs->nonfinite : c->hm->nonfinite;
+    if (timeout) {
+      TRY(sync(c));
+      return timeout_error(c);
+    }
+    if (nonfinite || !std::isfinite(F)) {
+      TRY(sync(c));
       return set_err(CNCPD_ENONFINITE, "objective or Lipschitz constant not finite at iteration %d",
                      c->total_iters + 1);
-    const double rel = c->hs->relerr;
+    }
+    const double rel = c->lra ? c->hs->relerr : c->hm->relerr;
     c->total_iters++;
     st.iters++;
     c->F_prev = F;
@@ -528,6 +582,8 @@ int run_iterations(cncpd_ctx* c, int n_iters, bool use_eps, cncpd_stats* out) {
       break;
     }
   }
+  TRY(sync(c));
+  if (pending >= 0) TRY(read_profile(c, &st, pending));
   st.total_iters = c->total_iters;
   st.F = c->F_prev;
   st.relerr = c->rel_prev;
@@ -603,8 +659,10 @@ void cncpd_destroy(cncpd_t h) {
   destroy_graphs(h);
   for (void* p : h->allocs) cudaFree(p);
   if (h->hs) cudaFreeHost(h->hs);
-  for (auto& e : h->ev)
-    if (e) cudaEventDestroy(e);
+  if (h->hm) cudaFreeHost(h->hm);
+  for (auto& set : h->ev)
+    for (auto& e : set)
+      if (e) cudaEventDestroy(e);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->side) cudaStreamDestroy(h->side);
@@ -691,7 +749,11 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
   CCU(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
   CCU(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
   CCU(cudaMallocHost((void**)&c->hs, sizeof(HostScalars)));
-  for (auto& e : c->ev) CCU(cudaEventCreate(&e));
+  CCU(cudaHostAlloc((void**)&c->hm, sizeof(HostMirror), cudaHostAllocMapped));
+  std::memset((void*)c->hm, 0, sizeof(HostMirror));
+  CCU(cudaHostGetDevicePointer((void**)&c->hm_dev, c->hm, 0));
+  for (auto& set : c->ev)
+    for (auto& e : set) CCU(cudaEventCreate(&e));
   // order after the caller's stream
   if (stream) {
     cudaEvent_t ev;
@@ -852,6 +914,7 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
   CTRY(dalloc(c, (void**)&d.err, sizeof(int)));
   CCU(cudaMemsetAsync(d.err, 0, sizeof(int), c->stream));
   d.sc = c->sc;
+  d.hm = c->hm_dev;
   CTRY(dalloc(c, (void**)&c->dd, sizeof(DevDesc)));
   CTRY(upload_desc(c));
 

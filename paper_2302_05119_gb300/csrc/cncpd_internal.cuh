@@ -59,6 +59,17 @@ struct DevScalars {
   double inv_xnorm2_orig[CNCPD_KMAX];
   double out_relk[CNCPD_KMAX];             // per-block relative error of an uncommitted evaluation
   int done_counter[CNCPD_NMAX + 2];        // arrival counters of last-CTA reductions (reset by the last CTA)
+  unsigned int seq;                        // objectives published to the host mirror
+};
+
+// Pinned, mapped host memory that the objective's last CTA writes directly,
+// so the host learns an iteration's F without a copy or a stream sync: the
+// fields first, then (after a system-scope fence) the sequence number.
+struct HostMirror {
+  double F, relerr;
+  int nonfinite, timeout;
+  volatile unsigned int seq;
+  int pad;
 };
 
 struct DevDesc {
@@ -106,6 +117,7 @@ struct DevDesc {
   int pad1;
   DevScalars* sc;
   int* err;                            // device error word (bounded waits, bad state)
+  HostMirror* hm;                      // device address of the host mirror (null: none)
   // Grams and H live in arenas: G^(m,k) = Gbase + (k*N + m)*Rmax^2, H^(k) = Hbase + k*Rmax^2
   double* Gbase;
   void* Hbase;

@@ -58,6 +58,7 @@ struct ObjArgs {            // objective with the last mode just updated
   int K, N, rr, gnc;
   int gr, commit, reduce_last, pad;
   DevScalars* sc;
+  HostMirror* hm;
   double* G;
   const T* Gp_last;
   int R[CNCPD_KMAX];
@@ -1182,10 +1183,22 @@ __global__ void __launch_bounds__(256) k_objective(const __grid_constant__ ObjAr
       F += __ldcg(&sc->Fk[q]);
       rel += __ldcg(&sc->relk[q]);
     }
+    const double relerr = rel / gridDim.x;
     sc->F = F;
-    sc->relerr = rel / gridDim.x;
+    sc->relerr = relerr;
     if (!isfinite(F)) sc->nonfinite = 1;
     sc->done_counter[1] = 0;
+    if (a.hm) {
+      HostMirror* hm = a.hm;
+      hm->F = F;
+      hm->relerr = relerr;
+      hm->nonfinite = *((volatile int*)&sc->nonfinite);
+      hm->timeout = *((volatile int*)&sc->timeout);
+      const unsigned int q = sc->seq + 1;
+      sc->seq = q;
+      __threadfence_system();
+      hm->seq = q;
+    }
   }
 }
 
@@ -1199,6 +1212,7 @@ static cudaError_t objective_impl(const LaunchCfg& c, const DevDesc& hd, int com
   a.commit = commit;
   a.reduce_last = (reduce_last && hd.Gp[n]) ? 1 : 0;
   a.sc = hd.sc;
+  a.hm = commit ? hd.hm : nullptr;
   a.G = hd.Gbase;
   if (a.reduce_last) {
     a.Gp_last = reinterpret_cast<const T*>(hd.Gp[n]);
