@@ -275,48 +275,68 @@ int enqueue_trailing(cncpd_ctx* c, const DevDesc* dd, const DevDesc& hd, int RP)
   return CNCPD_OK;
 }
 
-int enqueue_lead(cncpd_ctx* c, const DevDesc* dd, const DevDesc& hd, int RP, const int64_t* red_prefix) {
+// with_reduce = 0: the split-K partials are left for the consumer to sum
+// (the update of the last mode when the trailing group is that mode alone).
+int enqueue_lead(cncpd_ctx* c, const DevDesc* dd, const DevDesc& hd, int RP, const int64_t* red_prefix,
+                 int with_reduce = 1) {
   LaunchCfg lc{c->stream, c->num_sms};
   TRY(record(c, 2));
   if (hd.use_tma) {
     CU(launch_lead_tma(lc, dd, hd, RP));
     TRY(record(c, 3));
-    CU(launch_reduce_splits(lc, hd, c->fp64));
+    if (with_reduce) CU(launch_reduce_splits(lc, hd, c->fp64));
   } else {
-    CU(launch_lead_contract(lc, dd, hd, c->st, RP, red_prefix));
+    CU(launch_lead_contract(lc, dd, hd, c->st, RP, red_prefix, with_reduce));
     TRY(record(c, 3));
   }
   return CNCPD_OK;
 }
 
+// The sweep does the iteration bookkeeping inside its first Lipschitz launch
+// (no separate k_iter_begin) on the tensor-pass path without a core tensor.
+bool begin_in_sweep(const cncpd_ctx* c) { return !c->lra && !c->opts.use_core; }
+
+// The lead pass of a third-order problem is the last mode's MTTKRP; the
+// update of that mode sums its split-K partials itself.
+bool fused_last_reduce(const cncpd_ctx* c) { return !c->lra && c->N - c->h == 1; }
+
 // Launch H / L of mode n (with the Gram of mode n-1) on the side stream so
 // that it runs concurrently with the tensor pass enqueued next on the main
 // stream; the main stream joins before the update of mode n.
-int fork_lipschitz(cncpd_ctx* c, int n, int core) {
+int fork_lipschitz(cncpd_ctx* c, int n, int core, int begin) {
   LaunchCfg ls{c->side, c->num_sms};
   CU(cudaEventRecord(c->ev_fork, c->stream));
   CU(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-  CU(launch_lipschitz(ls, c->dd, c->hd, c->fp64, n, core, n - 1));
+  CU(launch_lipschitz(ls, c->dd, c->hd, c->fp64, n, core, n - 1, begin));
   CU(cudaEventRecord(c->ev_join, c->side));
   return CNCPD_OK;
 }
 
-int enqueue_sweep(cncpd_ctx* c, int use_w) {
+// begin = 1: a main (not re-update) sweep, whose first Lipschitz launch
+// also does the iteration bookkeeping when begin_in_sweep holds.
+int enqueue_sweep(cncpd_ctx* c, int use_w, int begin) {
   LaunchCfg lc{c->stream, c->num_sms};
   const double dw = c->opts.delta_w;
   const int core = c->opts.use_core;
+  const int fuse_reduce = fused_last_reduce(c);
   if (core) CU(launch_core_update(lc, c->dd, c->hd, use_w, dw));
   for (int n = 0; n < c->N; ++n) {
-    bool forked = false;
-    if (!c->lra && (n == 0 || n == c->h)) {
-      // the pass needs the factors updated so far; H / L of mode n only needs
-      // the Grams, which are final as well: run them side by side
-      TRY(fork_lipschitz(c, n, core));
-      forked = true;
-      if (n == 0) TRY(enqueue_trailing(c, c->dd, c->hd, c->RP));
-      else TRY(enqueue_lead(c, c->dd, c->hd, c->RP, c->d_red_prefix));
-    }
-    if (forked) {
+    const int beg = (n == 0 && begin && begin_in_sweep(c)) ? 1 : 0;
+    if (!c->lra && n == 0) {
+      // trailing pass alone on the GPU, then level 2 and H / L of mode 0 (with
+      // the iteration bookkeeping) in one launch
+      TRY(enqueue_trailing(c, c->dd, c->hd, c->RP));
+      if (level2_is_pair(c->hd, n)) {
+        CU(launch_mode_prep(lc, c->dd, c->hd, c->fp64, n, core, -1, 1, beg));
+      } else {
+        TRY(enqueue_mode_m(c, n));
+        CU(launch_lipschitz(lc, c->dd, c->hd, c->fp64, n, core, -1, beg));
+      }
+    } else if (!c->lra && n == c->h) {
+      // the lead pass needs the factors updated so far; H / L of mode h only
+      // needs the Grams, which are final as well: run them side by side
+      TRY(fork_lipschitz(c, n, core, 0));
+      TRY(enqueue_lead(c, c->dd, c->hd, c->RP, c->d_red_prefix, fuse_reduce ? 0 : 1));
       if (level2_is_pair(c->hd, n)) CU(launch_mode_prep(lc, c->dd, c->hd, c->fp64, n, core, -1, 2));
       else TRY(enqueue_mode_m(c, n));
       CU(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
@@ -325,9 +345,9 @@ int enqueue_sweep(cncpd_ctx* c, int use_w) {
       CU(launch_mode_prep(lc, c->dd, c->hd, c->fp64, n, core, n - 1, 1));
     } else {
       TRY(enqueue_mode_m(c, n));
-      CU(launch_lipschitz(lc, c->dd, c->hd, c->fp64, n, core, n - 1));  // also the Gram of mode n-1
+      CU(launch_lipschitz(lc, c->dd, c->hd, c->fp64, n, core, n - 1, beg));  // also the Gram of mode n-1
     }
-    CU(launch_update(lc, c->dd, c->hd, c->fp64, c->RP, n, use_w, dw, core));
+    CU(launch_update(lc, c->dd, c->hd, c->fp64, c->RP, n, use_w, dw, core, (fuse_reduce && n == c->N - 1) ? 1 : 0));
     if (c->lra) CU(launch_cross_gram(lc, c->dd, c->hd, c->fp64, n, n + 1));
   }
   if (c->lra) {
@@ -356,11 +376,11 @@ int timeout_error(cncpd_ctx* c) {
 
 // The objective at the end of a sweep publishes F to the host mirror; the
 // LRA objective does not, so that path reads the scalars back.
+// (The snapshot S of U2 taken for a re-update is written by the update kernels.)
 int enqueue_main(cncpd_ctx* c) {
   LaunchCfg lc{c->stream, c->num_sms};
-  CU(launch_iter_begin(lc, c->dd, c->hd, c->opts.use_core));
-  CU(cudaMemcpyAsync(c->AS, c->A2, arena_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
-  TRY(enqueue_sweep(c, 1));
+  if (!begin_in_sweep(c)) CU(launch_iter_begin(lc, c->dd, c->hd, c->opts.use_core));
+  TRY(enqueue_sweep(c, 1, 1));
   return c->lra ? enqueue_readback(c) : CNCPD_OK;
 }
 
@@ -371,7 +391,7 @@ int enqueue_redo(cncpd_ctx* c) {
   CU(cudaMemcpyAsync(c->A2, c->AS, arena_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
   CU(launch_gram(lc, c->dd, c->hd, c->fp64, 0, c->N, 0));
   if (c->lra) CU(launch_cross_gram(lc, c->dd, c->hd, c->fp64, 0, c->N));
-  TRY(enqueue_sweep(c, 0));
+  TRY(enqueue_sweep(c, 0, 0));
   return c->lra ? enqueue_readback(c) : CNCPD_OK;
 }
 
@@ -506,16 +526,21 @@ double pass_bytes(cncpd_ctx* c) {
 
 // Kernels launched by one main (redo = 0) or re-update (redo = 1) replay.
 long long kernels_per_replay(cncpd_ctx* c, int redo) {
-  long long n = c->opts.use_core ? 1 : 0;
-  if (!c->lra) n += 1 + 2;  // trailing contraction; lead contraction + split reduction
+  long long n = c->opts.use_core ? 1 : 0;                 // core update
+  if (!redo && !begin_in_sweep(c)) n += 1;                // iteration bookkeeping
+  if (redo) n += 1 + 2 + (c->lra ? 1 : 0);                // restore, Grams (chunks + sums), cross Grams
+  if (!c->lra) n += 2 + (fused_last_reduce(c) ? 0 : 1);  // both tensor passes (+ split reduction)
   for (int m = 0; m < c->N; ++m) {
-    const int gsize = (m < c->h) ? c->h : c->N - c->h;
-    if (c->lra) n += 2;     // collapsed M, cross Gram
-    else if (gsize > 2) n += 1;  // generic level 2 (pairs share the Lipschitz launch)
-    n += 2;                 // Lipschitz (+ level 2, + the previous mode's Gram), update
+    n += 2;                                               // Lipschitz (alone or with level 2), update
+    if (c->lra) {
+      n += 2;                                             // collapsed M, cross Gram
+    } else {
+      const int gsize = (m < c->h) ? c->h : c->N - c->h;
+      const bool forked = (m == c->h);
+      if (gsize > 2 || (gsize == 2 && forked)) n += 1;   // level 2 in its own launch
+    }
   }
-  n += c->lra ? 2 : 1;      // (last Gram +) objective
-  n += redo ? (c->lra ? 3 : 2) : 1;
+  n += c->lra ? 3 : 1;                                    // (last Gram: chunks + sums) + objective
   return n;
 }
 
@@ -915,6 +940,8 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
   CCU(cudaMemsetAsync(d.err, 0, sizeof(int), c->stream));
   d.sc = c->sc;
   d.hm = c->hm_dev;
+  d.A1base = c->A1;
+  d.ASbase = c->AS;
   CTRY(dalloc(c, (void**)&c->dd, sizeof(DevDesc)));
   CTRY(upload_desc(c));
 

@@ -118,6 +118,10 @@ struct DevDesc {
   DevScalars* sc;
   int* err;                            // device error word (bounded waits, bad state)
   HostMirror* hm;                      // device address of the host mirror (null: none)
+  // factor arenas U1 and S (snapshot of U2 at the start of an iteration); the
+  // snapshot of U^(n,k) sits at the same offset in S as U1[k][n] in U1
+  char* A1base;
+  char* ASbase;
   // Grams and H live in arenas: G^(m,k) = Gbase + (k*N + m)*Rmax^2, H^(k) = Hbase + k*Rmax^2
   double* Gbase;
   void* Hbase;
@@ -147,6 +151,23 @@ __device__ __forceinline__ T load_x(const void* __restrict__ x, const void* __re
     return (T)(__bfloat162float(reinterpret_cast<const __nv_bfloat16*>(x)[i]) +
                __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(xlo)[i]));
   }
+}
+
+// One entry of the lead-mode contraction from its split-K partial sums
+// (ns splits, stride elements apart), the splits added in order; the loads of
+// up to 32 splits are issued before any of them is added.
+template <typename T>
+__device__ __forceinline__ T sum_splits(const T* __restrict__ p, int ns, int64_t stride) {
+  T s = T(0);
+  for (int i0 = 0; i0 < ns; i0 += 32) {
+    T x[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) x[j] = p[(int64_t)min(i0 + j, ns - 1) * stride];  // clamped: no predicate
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (i0 + j < ns) s += x[j];
+  }
+  return s;
 }
 
 // Mixed-radix decode of a flat C-order index over modes [m0, m1) of block k.
@@ -204,7 +225,7 @@ struct LaunchCfg {
 // trailing-mode contraction -> Pl ; lead-mode contraction (split-K + fixed-order reduction) -> Pt
 cudaError_t launch_trailing_contract(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int st, int RP);
 cudaError_t launch_lead_contract(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int st, int RP,
-                                 const int64_t* d_red_prefix);
+                                 const int64_t* d_red_prefix, int with_reduce = 1);
 int lead_cpt(int fp64, int RP);
 bool tma_rank_supported(int RP);
 cudaError_t launch_reduce_splits(const LaunchCfg& c, const DevDesc& h_desc, int fp64);
@@ -215,13 +236,17 @@ cudaError_t launch_gram(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc
 // Level-2 of mode n (two-mode groups) and H / L of mode n in one launch
 // (CTAs 0..K-1: Lipschitz; the rest: level 2).  with_level2 = 0: Lipschitz only.
 cudaError_t launch_mode_prep(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int n,
-                             int use_core, int prev, int with_level2);
+                             int use_core, int prev, int with_level2, int begin = 0);
 bool level2_is_pair(const DevDesc& h_desc, int n);
 // prev >= 0: first form the Gram of mode `prev` (updated just before)
+// begin = 1: the launch also does the iteration bookkeeping of k_iter_begin
+// (no core tensor).
 cudaError_t launch_lipschitz(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int n, int use_core,
-                             int prev);
+                             int prev, int begin = 0);
+// msplit = 1: M of mode n (the last mode, a one-mode trailing group) is summed
+// here from the lead contraction's split-K partials (and stored).
 cudaError_t launch_update(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int RP, int n,
-                          int use_w, double delta_w, int use_core);
+                          int use_w, double delta_w, int use_core, int msplit);
 // commit = 1: write F/relerr/core term of the solver state; 0: only out_relk against xnorm2_orig.
 // reduce_last = 1: the Gram of the last mode is first summed from the chunk values the update left.
 cudaError_t launch_objective(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int RP, int commit,

@@ -327,39 +327,16 @@ struct SplitArgs {
   T* out[CNCPD_KMAX];
 };
 
-// One CTA = 32 consecutive output elements x 8 split groups; group g adds
-// splits g, g+8, ... in order, then the 8 group sums are added in group order.
+// One thread per output element, the splits added in order (sum_splits).
 template <typename T>
 __global__ void __launch_bounds__(256) k_reduce_splits(const __grid_constant__ SplitArgs<T> a) {
-  __shared__ T red[8][32];
-  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-  const int64_t e = (int64_t)blockIdx.x * 32 + lane;
+  const int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x;
   const int64_t total = a.prefix[a.K];
+  if (e >= total) return;
   int k = 0;
-  if (e < total)
-    while (a.prefix[k + 1] <= e) ++k;
-  T s = T(0);
-  if (e < total) {
-    const T* part = a.part[k] + (e - a.prefix[k]);
-    const int64_t stride = a.stride[k];
-    const int ns = a.nsplit[k];
-    for (int i0 = g; i0 < ns; i0 += 64) {
-      T x[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) x[j] = part[(int64_t)min(i0 + 8 * j, ns - 1) * stride];  // clamped
-#pragma unroll
-      for (int j = 0; j < 8; ++j)
-        if (i0 + 8 * j < ns) s += x[j];
-    }
-  }
-  red[g][lane] = s;
-  __syncthreads();
-  if (g == 0 && e < total) {
-    T t = red[0][lane];
-#pragma unroll
-    for (int q = 1; q < 8; ++q) t += red[q][lane];
-    a.out[k][e - a.prefix[k]] = t;
-  }
+  while (a.prefix[k + 1] <= e) ++k;
+  const int64_t local = e - a.prefix[k];
+  a.out[k][local] = sum_splits<T>(a.part[k] + local, a.nsplit[k], a.stride[k]);
 }
 
 // ---------------------------------------------------------------------------
@@ -465,7 +442,7 @@ static cudaError_t reduce_splits_impl(const LaunchCfg& c, const DevDesc& hd) {
     a.part[k] = reinterpret_cast<const T*>(hd.partial) + hd.partial_off[k];
     a.out[k] = reinterpret_cast<T*>(hd.Pt[k]);
   }
-  const int64_t blocks = (a.prefix[hd.K] + 31) / 32;
+  const int64_t blocks = (a.prefix[hd.K] + 255) / 256;
   if (blocks == 0) return cudaSuccess;
   carve<k_reduce_splits<T>>();
   k_reduce_splits<T><<<(unsigned)blocks, 256, 0, c.stream>>>(a);
@@ -477,7 +454,8 @@ cudaError_t launch_reduce_splits(const LaunchCfg& c, const DevDesc& hd, int fp64
 }
 
 template <int ST, typename T, int RP>
-static cudaError_t lead_impl(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, const int64_t* d_red_prefix) {
+static cudaError_t lead_impl(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, const int64_t* d_red_prefix,
+                             int with_reduce) {
   const int total = hd.tt_prefix[hd.K];
   if (total == 0) return cudaSuccess;
   constexpr int CPT = (sizeof(T) == 8) ? (RP <= 16 ? 2 : 1) : (RP <= 20 ? 4 : (RP <= 32 ? 2 : 1));
@@ -495,6 +473,7 @@ static cudaError_t lead_impl(const LaunchCfg& c, const DevDesc* dd, const DevDes
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   (void)d_red_prefix;
+  if (!with_reduce) return cudaSuccess;
   return launch_reduce_splits(c, hd, sizeof(T) == 8);
 }
 
@@ -569,8 +548,8 @@ cudaError_t launch_trailing_contract(const LaunchCfg& c, const DevDesc* dd, cons
 }
 
 cudaError_t launch_lead_contract(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int st, int RP,
-                                  const int64_t* d_red_prefix) {
-  CNCPD_DISPATCH_ST_RP(lead_impl, c, dd, hd, d_red_prefix)
+                                  const int64_t* d_red_prefix, int with_reduce) {
+  CNCPD_DISPATCH_ST_RP(lead_impl, c, dd, hd, d_red_prefix, with_reduce)
 }
 
 cudaError_t launch_level2(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int RP, int n) {

@@ -18,7 +18,7 @@ template <typename T>
 struct LipArgs {            // H^(n,k) and L^(n,k) for every block
   int K, N, n, prev;        // prev >= 0: first reduce the Gram partials of mode prev
   int use_core, want_L, rr, gnc_prev;
-  int gr_prev, pad;
+  int gr_prev, begin;       // begin: also the iteration bookkeeping (no core tensor)
   DevScalars* sc;
   double* G;                // Gram arena: G^(m,k) at G + (k*N + m)*rr
   T* H;                     // H arena: H^(k) at H + k*rr
@@ -49,8 +49,11 @@ struct UpdArgs {            // fused APG update of mode n
   int I[CNCPD_KMAX];
   T* U1[CNCPD_KMAX];
   T* U2[CNCPD_KMAX];
-  const T* M[CNCPD_KMAX];
+  T* S[CNCPD_KMAX];          // snapshot of U2 at the start of the iteration (written here)
+  T* M[CNCPD_KMAX];
   const T* H[CNCPD_KMAX];
+  const T* part[CNCPD_KMAX];  // non-null: M is summed from these split-K partials
+  int nsplit[CNCPD_KMAX];
 };
 
 template <typename T>
@@ -420,6 +423,30 @@ __device__ void lip_body(const LipArgs<T>& a, int k, unsigned char* smem) {
   DevScalars* sc = a.sc;
   const int nch = prev >= 0 ? (a.Iprev[k] + a.gr_prev - 1) / a.gr_prev : 0;
   const T* gp = prev >= 0 ? a.Gp_prev + (size_t)k * a.gnc_prev * rr : nullptr;
+  if (a.begin) {
+    // Iteration bookkeeping (Appendix A): t_k, hat w, and the Lipschitz
+    // constants of the last accepted sweep become L_{k-2}.  This CTA's own
+    // L^(n,k) is copied by the thread that overwrites it below; CTA 0 does
+    // the rest.  Every reader of these values runs after this kernel.
+    const int have_cur = sc->have_cur;
+    if (tid == 0 && have_cur) sc->Lprev_u[n][k] = sc->Lcur_u[n][k];
+    if (k == 0) {
+      const int K = a.K;
+      for (int e = tid; e < N * K; e += nt) {
+        const int m = e / K, kk = e % K;
+        if (m != n && have_cur) sc->Lprev_u[m][kk] = sc->Lcur_u[m][kk];
+      }
+      for (int m = tid; m < N; m += nt)
+        if (have_cur) sc->LCprev[m] = sc->LCcur[m];
+      if (tid == 0) {
+        const double t = sc->t;
+        const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+        sc->w_hat = (t - 1.0) / tn;
+        sc->t = tn;
+        if (have_cur) sc->have_prev = 1;
+      }
+    }
+  }
   for (int p = tid; p < R * R; p += nt) {
     double gm[CNCPD_NMAX];
 #pragma unroll
@@ -561,8 +588,9 @@ bool level2_is_pair(const DevDesc& hd, int n) {
 }
 
 template <typename T>
-static LipArgs<T> lip_args(const DevDesc& hd, int n, int use_core, int prev, int want_L) {
+static LipArgs<T> lip_args(const DevDesc& hd, int n, int use_core, int prev, int want_L, int begin = 0) {
   LipArgs<T> a{};
+  a.begin = begin;
   a.K = hd.K;
   a.N = hd.N;
   a.n = n;
@@ -621,7 +649,7 @@ static PairArgs<T> pair_args(const DevDesc& hd, int n, int num_sms, int* ctas) {
 
 template <typename T, int RP>
 static cudaError_t mode_prep_impl(const LaunchCfg& c, const DevDesc& hd, int n, int use_core, int prev,
-                                  int with_level2) {
+                                  int with_level2, int begin) {
   // with_level2: 0 = Lipschitz only, 1 = Lipschitz + level 2, 2 = level 2 only
   int ctas = 0;
   PairArgs<T> pa{};
@@ -632,7 +660,7 @@ static cudaError_t mode_prep_impl(const LaunchCfg& c, const DevDesc& hd, int n, 
     k_level2_pair<T><<<ctas, 256, 0, c.stream>>>(pa);
     return cudaGetLastError();
   }
-  LipArgs<T> la = lip_args<T>(hd, n, use_core, prev, 1);
+  LipArgs<T> la = lip_args<T>(hd, n, use_core, prev, 1, begin);
   const size_t sm = std::max(lip_smem_bytes<RP>(), with_level2 ? sizeof(T) * 8 * 256 : (size_t)0);
   if (with_level2 == 0) {
     cudaError_t e = allow_smem(k_lipschitz<T, RP>, sm);
@@ -650,21 +678,27 @@ static cudaError_t mode_prep_impl(const LaunchCfg& c, const DevDesc& hd, int n, 
 
 static int rank_bucket_of(const DevDesc& hd) { return rank_bucket(hd.Rmax); }
 
-cudaError_t launch_mode_prep(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int n, int use_core,
-                             int prev, int with_level2) {
-  (void)dd;
+static cudaError_t mode_prep_any(const LaunchCfg& c, const DevDesc& hd, int fp64, int n, int use_core, int prev,
+                                 int with_level2, int begin) {
 #define MCASE(V)                                                                                       \
   case V:                                                                                              \
-    return fp64 ? mode_prep_impl<double, V>(c, hd, n, use_core, prev, with_level2)                     \
-                : mode_prep_impl<float, V>(c, hd, n, use_core, prev, with_level2);
+    return fp64 ? mode_prep_impl<double, V>(c, hd, n, use_core, prev, with_level2, begin)              \
+                : mode_prep_impl<float, V>(c, hd, n, use_core, prev, with_level2, begin);
   switch (rank_bucket_of(hd)) { CNCPD_FOR_EACH_RP(MCASE) }
 #undef MCASE
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_mode_prep(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int n, int use_core,
+                             int prev, int with_level2, int begin) {
+  (void)dd;
+  return mode_prep_any(c, hd, fp64, n, use_core, prev, with_level2, begin);
+}
+
 cudaError_t launch_lipschitz(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int n, int use_core,
-                             int prev) {
-  return launch_mode_prep(c, dd, hd, fp64, n, use_core, prev, 0);
+                             int prev, int begin) {
+  (void)dd;
+  return mode_prep_any(c, hd, fp64, n, use_core, prev, 0, begin);
 }
 
 // H of mode n for every block, without L (the gradient path).
@@ -774,30 +808,34 @@ __global__ void __launch_bounds__(128) k_update(const __grid_constant__ UpdArgs<
 
   for (int p0 = 0; p0 < a.gr; p0 += TY) {
     const int64_t i = (p0 + y < a.gr) ? row0 + p0 + y : INT64_MAX;  // rows past the chunk belong to the next CTA
-    T sumC = T(0), uhC = T(0), u1C = T(0);
+    T sumC = T(0), uhC = T(0), u1C = T(0), u2C = T(0);
     for (int k0 = 0; k0 < K; k0 += KC) {
       if (nchunk > 1) {
         __syncthreads();
         load_h(k0);
       }
-      T u1[KC], mv[KC];
+      T u1[KC], u2[KC], mv[KC];
       T lam[KC];
 #pragma unroll
       for (int kk = 0; kk < KC; ++kk) {
         const int k = k0 + kk;
-        u1[kk] = mv[kk] = T(0);
+        u1[kk] = u2[kk] = mv[kk] = T(0);
         lam[kk] = T(1);
-        T u2 = T(0);
         const bool valid = k < K && i < a.I[k] && c < a.R[k];
         if (valid) {
           const int R = a.R[k];
           u1[kk] = a.U1[k][i * R + c];
-          u2 = a.U2[k][i * R + c];
-          mv[kk] = a.M[k][i * R + c];
+          u2[kk] = a.U2[k][i * R + c];
+          if (a.part[0]) {
+            mv[kk] = sum_splits<T>(a.part[k] + i * R + c, a.nsplit[k], (int64_t)a.I[k] * R);
+            a.M[k][i * R + c] = mv[kk];
+          } else {
+            mv[kk] = a.M[k][i * R + c];
+          }
           if (a.use_core) lam[kk] = (T)sc->lam1[k][c];
         }
         const T w = (c < Ln) ? wC : (k < K ? wsh[k] : T(0));
-        uh[kk][y][c] = valid ? u1[kk] + w * (u1[kk] - u2) : T(0);
+        uh[kk][y][c] = valid ? u1[kk] + w * (u1[kk] - u2[kk]) : T(0);
       }
       __syncthreads();
 #pragma unroll
@@ -816,6 +854,7 @@ __global__ void __launch_bounds__(128) k_update(const __grid_constant__ UpdArgs<
               nv = uhat - g / Lk;
               if (a.nonneg) nv = nv > T(0) ? nv : T(0);
             }
+            a.S[k][i * R + c] = u2[kk];
             a.U2[k][i * R + c] = u1[kk];
             a.U1[k][i * R + c] = nv;
             if (nvs) nvs[((size_t)kk * a.gr + p0 + y) * RP + c] = nv;
@@ -823,6 +862,7 @@ __global__ void __launch_bounds__(128) k_update(const __grid_constant__ UpdArgs<
             sumC += g;
             uhC = uhat;
             u1C = u1[kk];
+            u2C = u2[kk];
           }
         }
       }
@@ -836,6 +876,7 @@ __global__ void __launch_bounds__(128) k_update(const __grid_constant__ UpdArgs<
       }
       for (int k = 0; k < K; ++k) {
         const int R = a.R[k];
+        a.S[k][i * R + c] = u2C;
         a.U2[k][i * R + c] = u1C;
         a.U1[k][i * R + c] = nv;
         if (nvs) nvs[((size_t)k * a.gr + p0 + y) * RP + c] = nv;
@@ -923,7 +964,15 @@ __global__ void __launch_bounds__(512) k_update_kp(const __grid_constant__ UpdAr
     const size_t off = valid ? (size_t)i * R + c : 0;
     const T u1 = valid ? a.U1[k][off] : T(0);
     const T u2 = valid ? a.U2[k][off] : T(0);
-    const T mv = valid ? a.M[k][off] : T(0);
+    T mv = T(0);
+    if (a.part[0]) {
+      if (valid) {
+        mv = sum_splits<T>(a.part[k] + off, a.nsplit[k], I * R);
+        a.M[k][off] = mv;
+      }
+    } else {
+      mv = valid ? a.M[k][off] : T(0);
+    }
     __syncthreads();  // weights and H staged; the previous pass is done with uh / gC
     const T w = (c < Ln) ? wsh[K] : wsh[k];
     const T uhat = u1 + w * (u1 - u2);
@@ -942,6 +991,7 @@ __global__ void __launch_bounds__(512) k_update_kp(const __grid_constant__ UpdAr
           nv = uhat - g / Lk;
           if (a.nonneg) nv = nv > T(0) ? nv : T(0);
         }
+        a.S[k][off] = u2;
         a.U2[k][off] = u1;
         a.U1[k][off] = nv;
         nvs[((size_t)k * a.gr + p0 + y) * RP + c] = nv;
@@ -962,6 +1012,7 @@ __global__ void __launch_bounds__(512) k_update_kp(const __grid_constant__ UpdAr
       }
       for (int kk = 0; kk < K; ++kk) {
         const size_t o = (size_t)i * a.R[kk] + c;
+        a.S[kk][o] = u2;
         a.U2[kk][o] = u1;
         a.U1[kk][o] = nv;
         nvs[((size_t)kk * a.gr + p0 + y) * RP + c] = nv;
@@ -987,7 +1038,7 @@ __global__ void __launch_bounds__(512) k_update_kp(const __grid_constant__ UpdAr
 
 template <typename T, int RP>
 static cudaError_t update_impl(const LaunchCfg& c, const DevDesc& hd, int n, int use_w, double delta_w,
-                               int use_core) {
+                               int use_core, int msplit) {
   UpdArgs<T> a{};
   a.K = hd.K;
   a.n = n;
@@ -1012,8 +1063,13 @@ static cudaError_t update_impl(const LaunchCfg& c, const DevDesc& hd, int n, int
     a.I[k] = (int)hd.dims[k][n];
     a.U1[k] = reinterpret_cast<T*>(hd.U1[k][n]);
     a.U2[k] = reinterpret_cast<T*>(hd.U2[k][n]);
-    a.M[k] = reinterpret_cast<const T*>(hd.M[k][n]);
+    a.S[k] = reinterpret_cast<T*>(hd.ASbase + (static_cast<const char*>(hd.U1[k][n]) - hd.A1base));
+    a.M[k] = reinterpret_cast<T*>(hd.M[k][n]);
     a.H[k] = reinterpret_cast<const T*>(hd.Hbase) + (size_t)k * a.rr;
+    if (msplit) {
+      a.part[k] = reinterpret_cast<const T*>(hd.partial) + hd.partial_off[k];
+      a.nsplit[k] = hd.nsplit[k];
+    }
   }
   const unsigned grid = (unsigned)((imax + a.gr - 1) / a.gr);
   if (geo.kp) {
@@ -1038,12 +1094,12 @@ static cudaError_t update_impl(const LaunchCfg& c, const DevDesc& hd, int n, int
 }
 
 cudaError_t launch_update(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int RP, int n,
-                          int use_w, double delta_w, int use_core) {
+                          int use_w, double delta_w, int use_core, int msplit) {
   (void)dd;
 #define UCASE(V)                                                                  \
   case V:                                                                         \
-    return fp64 ? update_impl<double, V>(c, hd, n, use_w, delta_w, use_core)      \
-                : update_impl<float, V>(c, hd, n, use_w, delta_w, use_core);
+    return fp64 ? update_impl<double, V>(c, hd, n, use_w, delta_w, use_core, msplit)      \
+                : update_impl<float, V>(c, hd, n, use_w, delta_w, use_core, msplit);
   switch (RP) { CNCPD_FOR_EACH_RP(UCASE) }
 #undef UCASE
   return cudaErrorInvalidValue;
