@@ -68,7 +68,9 @@ typedef struct {
   int lra_max_it;    /* ALS sweep cap; 200 (Sec. III-C) */
   double delta_w;    /* delta_w of Eqs. eqextrawd/eqextrawu; 0.9999 (App. A) */
   int use_core;      /* 1: update the super-diagonal cores D^(k) (Eq. solD); 0: D = I */
-  int reupdate;      /* 1: non-monotone safeguard of Algorithm 1 (redo with w = 0) */
+  int reupdate;      /* 1: non-monotone safeguard of Algorithm 1 (redo with w = 0) when
+                        F(k) - F(k-1) > tol * F(k-1); tol = 1e-13 for FP64 storage and
+                        1e-6 otherwise (the FP32 objective is accurate to a few 1e-7) */
   int storage;       /* cncpd_dtype of X on the device, or -1 = same as the input
                         (F64 input -> F64 path; anything else -> F32 factors) */
   int use_graph;     /* 1: replay each sweep as a CUDA graph */

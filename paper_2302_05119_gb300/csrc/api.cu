@@ -92,6 +92,10 @@ struct cncpd_ctx {
 
   // solver state on the host
   bool dirty = true;             // factors/cores changed: re-initialise history
+  // "F did not increase" (Algorithm 1 safeguard) when F - F_prev <= tie_tol * |F_prev|:
+  // 1e-13 with FP64 factors; 1e-6 with FP32 factors, whose objective is only
+  // accurate to a few 1e-7 relative (cancellation in the Gram expansion)
+  double tie_tol = 1e-13;
   double F_prev = 0.0, rel_prev = 0.0;
   int total_iters = 0;
 
@@ -574,7 +578,7 @@ int run_iterations(cncpd_ctx* c, int n_iters, bool use_eps, cncpd_stats* out) {
     st.x_bytes += pb;
     st.launches += kernels_per_replay(c, 0);
     double F = c->lra ? c->hs->F : c->hm->F;
-    const bool redo = c->opts.reupdate && (F - c->F_prev) > 1e-13 * std::fabs(c->F_prev);
+    const bool redo = c->opts.reupdate && (F - c->F_prev) > c->tie_tol * std::fabs(c->F_prev);
     if (redo) {
       const unsigned int s1 = c->hm->seq;
       TRY(run_redo(c));
@@ -747,6 +751,7 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
   c->opts = o;
   c->st = st;
   c->fp64 = (st == ST_F64);
+  c->tie_tol = c->fp64 ? 1e-13 : 1e-6;
   c->fsz = c->fp64 ? 8 : 4;
   c->lam_init.assign((size_t)K * CNCPD_RMAX, 1.0);
   c->xnorm2.assign(K, 0.0);

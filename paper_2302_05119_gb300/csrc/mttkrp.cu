@@ -488,6 +488,7 @@ int lead_cpt(int fp64, int RP) {
       switch (RP) {                                                                 \
         case 4: return FN<ST_F64, double, 4>(__VA_ARGS__);                          \
         case 8: return FN<ST_F64, double, 8>(__VA_ARGS__);                          \
+        case 10: return FN<ST_F64, double, 10>(__VA_ARGS__);                        \
         case 12: return FN<ST_F64, double, 12>(__VA_ARGS__);                        \
         case 16: return FN<ST_F64, double, 16>(__VA_ARGS__);                        \
         case 20: return FN<ST_F64, double, 20>(__VA_ARGS__);                        \
@@ -502,6 +503,7 @@ int lead_cpt(int fp64, int RP) {
       switch (RP) {                                                                 \
         case 4: return FN<ST_F32, float, 4>(__VA_ARGS__);                           \
         case 8: return FN<ST_F32, float, 8>(__VA_ARGS__);                           \
+        case 10: return FN<ST_F32, float, 10>(__VA_ARGS__);                         \
         case 12: return FN<ST_F32, float, 12>(__VA_ARGS__);                         \
         case 16: return FN<ST_F32, float, 16>(__VA_ARGS__);                         \
         case 20: return FN<ST_F32, float, 20>(__VA_ARGS__);                         \
@@ -516,6 +518,7 @@ int lead_cpt(int fp64, int RP) {
       switch (RP) {                                                                 \
         case 4: return FN<ST_BF16, float, 4>(__VA_ARGS__);                          \
         case 8: return FN<ST_BF16, float, 8>(__VA_ARGS__);                          \
+        case 10: return FN<ST_BF16, float, 10>(__VA_ARGS__);                        \
         case 12: return FN<ST_BF16, float, 12>(__VA_ARGS__);                        \
         case 16: return FN<ST_BF16, float, 16>(__VA_ARGS__);                        \
         case 20: return FN<ST_BF16, float, 20>(__VA_ARGS__);                        \
@@ -530,6 +533,7 @@ int lead_cpt(int fp64, int RP) {
       switch (RP) {                                                                 \
         case 4: return FN<ST_BF16X2, float, 4>(__VA_ARGS__);                        \
         case 8: return FN<ST_BF16X2, float, 8>(__VA_ARGS__);                        \
+        case 10: return FN<ST_BF16X2, float, 10>(__VA_ARGS__);                      \
         case 12: return FN<ST_BF16X2, float, 12>(__VA_ARGS__);                      \
         case 16: return FN<ST_BF16X2, float, 16>(__VA_ARGS__);                      \
         case 20: return FN<ST_BF16X2, float, 20>(__VA_ARGS__);                      \

@@ -34,6 +34,13 @@ def _P():
     ([(3, 4, 5, 6), (2, 4, 7, 3)], 5),
     ([(9, 7, 5, 4, 3)], 4),
     ([(40, 40, 40)], 33),
+    # one case in every rank bucket of the compiled kernels
+    ([(12, 10, 9)], 10),
+    ([(10, 11, 12)], 16),
+    ([(9, 8, 10)], 24),
+    ([(8, 9, 10)], 32),
+    ([(7, 6, 9)], 48),
+    ([(6, 7, 8)], 64),
 ])
 def test_mttkrp_matches_oracle(dims, R, dt):
     rng = np.random.default_rng(len(dims) * 100 + R)
