@@ -28,8 +28,13 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "APG iterations/s (coupled NCP sweep, FP32, 5x256^3, R=10)"
 UNIT = "iterations/s"
+
+
+def _metric(w, storage):
+    dims = "x".join(str(d) for d in w.dims[0]) if len(set(map(tuple, w.dims))) == 1 else "uneven"
+    return (f"APG iterations/s (coupled NCP sweep, X in {storage.upper()}, FP32 factors, "
+            f"{w.K} blocks of {dims}, R={w.R})")
 
 
 def _dist():
@@ -161,7 +166,7 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     value = args.steps / w.K / dt
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "impl": "reference", "metric": _metric(w, "f32"), "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded Uniform[0,1] factors, 10 dB Gaussian noise, clipped)",
@@ -191,7 +196,7 @@ def run_ours(args):
     Xd = [torch.from_numpy(X).cuda() for X in Xs]
     torch.cuda.synchronize()
 
-    m = P.CoupledNCP(Xd, w.R, w.L, profile=True)
+    m = P.CoupledNCP(Xd, w.R, w.L, profile=True, storage=args.storage)
     m.set_factors(U0)
     m.step(args.warmup)
 
@@ -219,15 +224,15 @@ def run_ours(args):
     value = args.steps * ws / (ms / 1e3)
 
     # roofline of the dominant tensor-streaming kernel
-    es = 4
+    es = {"f32": 4, "bf16": 2, "bf16x2": 4}[args.storage]  # bytes of X per element
     h = (w.N + 1) // 2
     # algorithmic bytes of one launch: X read once, the factors of the modes
     # contracted away read once, the level-1 product written once
     lead_rows = [int(np.prod(d[:h])) for d in w.dims]
     trail_cols = [int(np.prod(d[h:])) for d in w.dims]
     x_bytes = sum(w.elements()) * es
-    trail_alg = x_bytes + sum((lr + sum(d[h:])) * w.R * es for lr, d in zip(lead_rows, w.dims))
-    lead_alg = x_bytes + sum((tc + sum(d[:h])) * w.R * es for tc, d in zip(trail_cols, w.dims))
+    trail_alg = x_bytes + sum((lr + sum(d[h:])) * w.R * 4 for lr, d in zip(lead_rows, w.dims))
+    lead_alg = x_bytes + sum((tc + sum(d[:h])) * w.R * 4 for tc, d in zip(trail_cols, w.dims))
     nl = max(1, s["stream_launches"] // 2)
     t_trail = s["trail_ms"] / nl
     t_lead = s["lead_ms"] / nl
@@ -247,7 +252,7 @@ def run_ours(args):
     Xh = [torch.from_numpy(X).pin_memory() for X in Xs]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    m2 = P.CoupledNCP(Xh, w.R, w.L)
+    m2 = P.CoupledNCP(Xh, w.R, w.L, storage=args.storage)
     m2.set_factors(U0)
     s2 = m2.step(args.steps)
     out = m2.factors(np.float32)
@@ -266,12 +271,13 @@ def run_ours(args):
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "metric": _metric(w, args.storage), "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded Uniform[0,1] factors, 10 dB Gaussian noise, clipped)",
             "config": {"workload": w.name, "K": w.K, "dims": list(w.dims[0]), "R": w.R, "L": w.L,
-                       "storage": "f32", "l2": "inputs larger than L2 (335 MB of tensors)",
+                       "storage": args.storage,
+                       "l2": f"inputs larger than L2 ({x_bytes / 1e6:.0f} MB of stored tensors)",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "reupdates": s["reupdates"], "fit": s["fit"],
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
@@ -290,6 +296,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sim_256cube")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "bf16x2"],
+                    help="element type of X on the device (factors and accumulation stay FP32)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -146,17 +146,20 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// 2-D FP32 tensor map over a rows x cols matrix with row pitch `pitch`
-// elements, box (box_cols x box_rows), out-of-range elements read as zero.
-bool encode_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64_t pitch, int box_cols, int box_rows,
-                CUtensorMapSwizzle swz) {
+// 2-D tensor map (FP32 or BF16 elements) over a rows x cols matrix with row
+// pitch `pitch` elements, box (box_cols x box_rows), out-of-range elements
+// read as zero.
+bool encode_map(CUtensorMap* m, const void* base, int st, int64_t rows, int64_t cols, int64_t pitch, int box_cols,
+                int box_rows, CUtensorMapSwizzle swz) {
   auto enc = tensor_map_encoder();
   if (!enc) return false;
+  const int esz = st == ST_BF16 ? 2 : 4;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)(pitch * 4)};
+  cuuint64_t strides[1] = {(cuuint64_t)(pitch * esz)};
   cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, es,
+  CUresult r = enc(m, st == ST_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                   const_cast<void*>(base), dims, strides, box, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -273,7 +276,7 @@ int enqueue_mode_m(cncpd_ctx* c, int n) {
 int enqueue_trailing(cncpd_ctx* c, const DevDesc* dd, const DevDesc& hd, int RP) {
   LaunchCfg lc{c->stream, c->num_sms};
   TRY(record(c, 0));
-  if (hd.use_tma) CU(launch_trailing_tma(lc, dd, hd, RP));
+  if (hd.use_tma) CU(launch_trailing_tma(lc, dd, hd, RP, c->st));
   else CU(launch_trailing_contract(lc, dd, hd, c->st, RP));
   TRY(record(c, 1));
   return CNCPD_OK;
@@ -286,7 +289,7 @@ int enqueue_lead(cncpd_ctx* c, const DevDesc* dd, const DevDesc& hd, int RP, con
   LaunchCfg lc{c->stream, c->num_sms};
   TRY(record(c, 2));
   if (hd.use_tma) {
-    CU(launch_lead_tma(lc, dd, hd, RP));
+    CU(launch_lead_tma(lc, dd, hd, RP, c->st));
     TRY(record(c, 3));
     if (with_reduce) CU(launch_reduce_splits(lc, hd, c->fp64));
   } else {
@@ -909,15 +912,18 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
     }
     d.H[k] = static_cast<char*>(d.Hbase) + (size_t)k * rr * c->fsz;
   }
-  // TMA descriptors of X for the FP32 kernels (two box shapes per block)
-  if (st == ST_F32 && tensor_map_encoder()) {
+  // TMA descriptors of X for the FP32 / BF16 kernels (two box shapes per
+  // block: 256 rows x 128 bytes, swizzled, for the trailing pass; 256 columns
+  // x 32 KiB for the lead pass)
+  if ((st == ST_F32 || st == ST_BF16) && tensor_map_encoder()) {
     std::vector<CUtensorMap> maps(2 * CNCPD_KMAX);
     bool ok = true;
+    const int esz = st == ST_BF16 ? 2 : 4;
     for (int k = 0; k < K && ok; ++k) {
-      ok = encode_map(&maps[k], d.X[k], d.lead_rows[k], d.trail_cols[k], d.pitch[k], 32, 256,
+      ok = encode_map(&maps[k], d.X[k], st, d.lead_rows[k], d.trail_cols[k], d.pitch[k], 128 / esz, 256,
                       CU_TENSOR_MAP_SWIZZLE_128B) &&
-           encode_map(&maps[CNCPD_KMAX + k], d.X[k], d.lead_rows[k], d.trail_cols[k], d.pitch[k], 256, 32,
-                      CU_TENSOR_MAP_SWIZZLE_NONE);
+           encode_map(&maps[CNCPD_KMAX + k], d.X[k], st, d.lead_rows[k], d.trail_cols[k], d.pitch[k], 256,
+                      lead_tma_rows(st), CU_TENSOR_MAP_SWIZZLE_NONE);
     }
     if (ok) {
       CUtensorMap* dm = nullptr;
@@ -927,7 +933,7 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
       d.tmap_lead = dm + CNCPD_KMAX;
     }
   }
-  d.use_tma = (d.tmap_trail != nullptr) && tma_rank_supported(c->RP) && !getenv("CNCPD_NO_TMA");
+  d.use_tma = (d.tmap_trail != nullptr) && tma_rank_supported(c->RP);
   size_t pel = 0;
   plan_lead_splits(c, d, c->RP, c->fp64, &pel);
   plan_trailing_tiles(d);
@@ -1191,7 +1197,7 @@ int cncpd_lra(cncpd_t h, const int* R_tilde, const void* const* Ut0, cncpd_dtype
     h->hd.Vinv[k] = a.Vinv[k] = p;
   }
   size_t pel = 0;
-  a.use_tma = (a.tmap_trail != nullptr) && tma_rank_supported(h->RPt) && !getenv("CNCPD_NO_TMA");
+  a.use_tma = (a.tmap_trail != nullptr) && tma_rank_supported(h->RPt);
   plan_lead_splits(h, a, h->RPt, h->fp64, &pel);
   plan_trailing_tiles(a);
   TRY(dalloc(h, &a.partial, pel * h->fsz));

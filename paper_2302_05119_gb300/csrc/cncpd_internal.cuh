@@ -103,8 +103,8 @@ struct DevDesc {
   int64_t partial_off[CNCPD_KMAX];     // element offset of block k's partials
   int nsplit[CNCPD_KMAX];
   int64_t split_rows[CNCPD_KMAX];
-  const CUtensorMap* tmap_trail;        // per-block TMA descriptors of X (FP32 storage), 256 x 32 boxes
-  const CUtensorMap* tmap_lead;         // per-block TMA descriptors of X (FP32 storage), 32 x 256 boxes
+  const CUtensorMap* tmap_trail;        // per-block TMA descriptors of X, boxes of 256 rows x 128 bytes (swizzled)
+  const CUtensorMap* tmap_lead;         // per-block TMA descriptors of X, boxes of 32 KiB x 256 columns
   int use_tma;                          // 1: the TMA kernels run the level-1 contractions
   int lt_rows;                          // rows per tile of the trailing contraction (64 or 256)
   int tt_cols;                          // columns per tile of the lead contraction
@@ -229,8 +229,10 @@ cudaError_t launch_lead_contract(const LaunchCfg& c, const DevDesc* d_desc, cons
 int lead_cpt(int fp64, int RP);
 bool tma_rank_supported(int RP);
 cudaError_t launch_reduce_splits(const LaunchCfg& c, const DevDesc& h_desc, int fp64);
-cudaError_t launch_trailing_tma(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int RP);
-cudaError_t launch_lead_tma(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int RP);
+// TMA-staged passes for FP32 (st = ST_F32) and BF16 (st = ST_BF16) storage
+cudaError_t launch_trailing_tma(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int RP, int st);
+cudaError_t launch_lead_tma(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int RP, int st);
+int lead_tma_rows(int st);
 cudaError_t launch_level2(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int RP, int n);
 cudaError_t launch_gram(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int n_begin, int n_end, int which);
 // Level-2 of mode n (two-mode groups) and H / L of mode n in one launch

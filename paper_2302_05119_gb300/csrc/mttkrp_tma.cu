@@ -1,4 +1,5 @@
-// TMA-staged level-1 contractions of the dimension tree for FP32 tensors.
+// TMA-staged level-1 contractions of the dimension tree for FP32 and BF16
+// tensors (BF16 elements are widened to FP32 in registers; FP32 accumulate).
 //
 // Both kernels stream X^(k) (viewed as lead_rows x trail_cols, row pitch a
 // multiple of 16 elements) from HBM exactly once.  One thread issues
@@ -24,26 +25,57 @@ __device__ __forceinline__ void decode32_t(const DevDesc* d, int k, int m0, int 
   }
 }
 
+// Sixteen bytes of X as FP32 values: four FP32 or eight BF16 elements.
+template <typename XT>
+struct XChunk {
+  static constexpr int N = 16 / (int)sizeof(XT);
+};
+
+__device__ __forceinline__ void widen(const uint4& raw, float (&v)[4], float) {
+  v[0] = __uint_as_float(raw.x);
+  v[1] = __uint_as_float(raw.y);
+  v[2] = __uint_as_float(raw.z);
+  v[3] = __uint_as_float(raw.w);
+}
+// BF16 -> FP32 is exact: the 16 bits become the high half of the FP32 word.
+__device__ __forceinline__ void widen(const uint4& raw, float (&v)[8], __nv_bfloat16) {
+  const uint32_t u[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    v[2 * i] = __uint_as_float(u[i] << 16);
+    v[2 * i + 1] = __uint_as_float(u[i] & 0xffff0000u);
+  }
+}
+// Four consecutive elements (16 bytes of FP32, 8 bytes of BF16).
+__device__ __forceinline__ float4 load4(const unsigned char* p, float) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float4 load4(const unsigned char* p, __nv_bfloat16) {
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u), __uint_as_float(u.y << 16),
+                     __uint_as_float(u.y & 0xffff0000u));
+}
+
 // ---------------------------------------------------------------------------
 // Trailing contraction Pl[row, r] = sum_col X[row, col] W_t[col, r].
-// Tile = 256 rows; stage = 256 rows x 32 columns (32 KiB, 128-byte swizzle).
-// Consumer warp w owns rows 128 (w % 2) + 32 j + lane (j = 0..3) of the tile
-// and columns 8 (w / 2) .. 8 (w / 2) + 7 of every stage, so each Khatri-Rao
-// value read from shared memory feeds four rows; the four column quarters are
-// added at the end of the tile.  Two consumer warps per scheduler hide the
-// shared-memory latency of one another.
+// Tile = 256 rows; stage = 256 rows x 128 bytes (32 FP32 or 64 BF16 columns,
+// 32 KiB, 128-byte swizzle).  Consumer warp w owns rows 128 (w % 2) + 32 j +
+// lane (j = 0..3) of the tile and the (w / 2)-th quarter of the stage's
+// columns (two 16-byte chunks), so each Khatri-Rao value read from shared
+// memory feeds four rows; the four column quarters are added at the end of
+// the tile.  Two consumer warps per scheduler hide the shared-memory latency
+// of one another.
 // ---------------------------------------------------------------------------
 constexpr int TT_ROWS = 256;
-constexpr int TT_BC = 32;
 constexpr int TT_CONS = 8;  // 2 row halves x 4 column quarters
 constexpr size_t SMEM_LIMIT = 232448;  // 227 KiB of dynamic shared memory per CTA
 constexpr int NKR = 3;  // Khatri-Rao warps, stage i handled by warp i mod NKR
 
-template <int RP>
+template <int RP, typename XT>
 struct TrailTma {
+  static constexpr int BC = 128 / (int)sizeof(XT);  // columns per stage
+  static constexpr int CPC = XChunk<XT>::N;         // columns per 16-byte chunk
   static constexpr int WST = (RP + 3) / 4 * 4;
-  static constexpr uint32_t X_BYTES = TT_ROWS * TT_BC * 4;
-  static constexpr uint32_t W_BYTES = TT_BC * WST * 4;
+  static constexpr uint32_t X_BYTES = TT_ROWS * 128;
+  static constexpr uint32_t W_BYTES = BC * WST * 4;
   static constexpr uint32_t RED_BYTES = 3 * TT_ROWS * RP * 4;  // partial sums of column quarters 1..3
   // as many stages as fit (at most 6): bytes in flight hide the memory latency
   static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 128 - RED_BYTES) / (X_BYTES + W_BYTES));
@@ -51,9 +83,10 @@ struct TrailTma {
   static constexpr size_t SMEM = 1024 + STAGES * (size_t)(X_BYTES + W_BYTES) + RED_BYTES + 2 * STAGES * 8;
 };
 
-template <int RP>
+template <int RP, typename XT>
 __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(const DevDesc* __restrict__ d) {
-  using S = TrailTma<RP>;
+  using S = TrailTma<RP, XT>;
+  constexpr int TT_BC = S::BC;
   constexpr int TST = S::STAGES;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* xs = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -118,24 +151,27 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
         const int s = it % TST;
         const uint32_t ph = (it / TST) & 1;
         if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, err)) { ok = false; break; }
-        // Khatri-Rao rows of the trailing factors for the 32 columns of this stage
-        const int j = c * TT_BC + lane;
-        float w[S::WST];
+        // Khatri-Rao rows of the trailing factors for the columns of this stage
 #pragma unroll
-        for (int r = 0; r < S::WST; ++r) w[r] = (j < J && r < R) ? 1.f : 0.f;
-        if (j < J) {
-          int idx[CNCPD_NMAX];
-          decode32_t(d, k, h, N, j, idx);
-          for (int m = h; m < N; ++m) {
-            const float* U = reinterpret_cast<const float*>(d->U1[k][m]) + (int64_t)idx[m] * R;
+        for (int jj = lane; jj < TT_BC; jj += 32) {
+          const int j = c * TT_BC + jj;
+          float w[S::WST];
 #pragma unroll
-            for (int r = 0; r < RP; ++r)
-              if (r < R) w[r] *= __ldg(U + r);
+          for (int r = 0; r < S::WST; ++r) w[r] = (j < J && r < R) ? 1.f : 0.f;
+          if (j < J) {
+            int idx[CNCPD_NMAX];
+            decode32_t(d, k, h, N, j, idx);
+            for (int m = h; m < N; ++m) {
+              const float* U = reinterpret_cast<const float*>(d->U1[k][m]) + (int64_t)idx[m] * R;
+#pragma unroll
+              for (int r = 0; r < RP; ++r)
+                if (r < R) w[r] *= __ldg(U + r);
+            }
           }
-        }
-        float4* wrow = reinterpret_cast<float4*>(ws + s * (S::W_BYTES / 4) + lane * S::WST);
+          float4* wrow = reinterpret_cast<float4*>(ws + s * (S::W_BYTES / 4) + jj * S::WST);
 #pragma unroll
-        for (int q = 0; q < S::WST / 4; ++q) wrow[q] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+          for (int q = 0; q < S::WST / 4; ++q) wrow[q] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+        }
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&full[s]));
       }
@@ -167,17 +203,16 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
       const float* wt = ws + s * (S::W_BYTES / 4);
 #pragma unroll
       for (int q = 2 * cq; q < 2 * cq + 2; ++q) {
-        float xv[4][4];
+        float xv[4][S::CPC];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           // 128-byte swizzle: 16-byte chunk q of row r sits at chunk q ^ (r & 7)
           const int r = rq * 128 + 32 * j + lane;
-          const float4 x = *reinterpret_cast<const float4*>(xt + r * 128 + ((q ^ (r & 7)) << 4));
-          xv[j][0] = x.x; xv[j][1] = x.y; xv[j][2] = x.z; xv[j][3] = x.w;
+          widen(*reinterpret_cast<const uint4*>(xt + r * 128 + ((q ^ (r & 7)) << 4)), xv[j], XT());
         }
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const uint64_t* wr = reinterpret_cast<const uint64_t*>(wt + (4 * q + e) * S::WST);
+        for (int e = 0; e < S::CPC; ++e) {
+          const uint64_t* wr = reinterpret_cast<const uint64_t*>(wt + (S::CPC * q + e) * S::WST);
           uint64_t x2[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) x2[j] = pack2(xv[j][e], xv[j][e]);
@@ -241,30 +276,31 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
 
 // ---------------------------------------------------------------------------
 // Lead contraction (split over rows) Pt[col, r] = sum_row X[row, col] W_l[row, r].
-// Unit = 256 columns x one row split; stage = 32 rows x 256 columns (32 KiB,
-// whole 1 KiB rows when the tensor has 256 trailing columns).  Consumer warp
-// w owns columns 128 (w % 2) + 4 lane .. + 3 and rows 8 (w / 2) .. + 7 of
-// every stage, so each Khatri-Rao value read from shared memory feeds four
-// columns; the four row quarters are added at the end of the unit.
+// Unit = 256 columns x one row split; stage = 32 KiB = 32 FP32 or 64 BF16
+// rows x 256 columns.  Consumer warp w owns columns 128 (w % 2) + 4 lane .. + 3
+// and the (w / 2)-th quarter of the stage's rows, so each Khatri-Rao value
+// read from shared memory feeds four columns; the four row quarters are added
+// at the end of the unit.
 // ---------------------------------------------------------------------------
-constexpr int LT_ROWS = 32;
 constexpr int LT_COLS = 256;
 constexpr int LT_CONS = 8;
 
-template <int RP>
+template <int RP, typename XT>
 struct LeadTma {
+  static constexpr int ROWS = 128 / (int)sizeof(XT);  // rows per stage (32 KiB)
   static constexpr int WST = (RP + 3) / 4 * 4;
-  static constexpr uint32_t X_BYTES = LT_ROWS * LT_COLS * 4;
-  static constexpr uint32_t W_BYTES = LT_ROWS * WST * 4;
+  static constexpr uint32_t X_BYTES = ROWS * LT_COLS * (int)sizeof(XT);
+  static constexpr uint32_t W_BYTES = ROWS * WST * 4;
   static constexpr uint32_t RED_BYTES = 3 * LT_COLS * RP * 4;  // partial sums of row quarters 1..3
   static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 128 - RED_BYTES) / (X_BYTES + W_BYTES));
   static constexpr int STAGES = STAGES_FIT > 6 ? 6 : STAGES_FIT;
   static constexpr size_t SMEM = 1024 + STAGES * (size_t)(X_BYTES + W_BYTES) + RED_BYTES + 2 * STAGES * 8;
 };
 
-template <int RP>
+template <int RP, typename XT>
 __global__ void __launch_bounds__((LT_CONS + NKR + 1) * 32, 1) k_lead_tma(const DevDesc* __restrict__ d) {
-  using S = LeadTma<RP>;
+  using S = LeadTma<RP, XT>;
+  constexpr int LT_ROWS = S::ROWS;
   constexpr int ST = S::STAGES;
   constexpr int RH = RP / 2;
   extern __shared__ unsigned char smem_raw[];
@@ -335,24 +371,27 @@ __global__ void __launch_bounds__((LT_CONS + NKR + 1) * 32, 1) k_lead_tma(const 
         const int s = it % ST;
         const uint32_t ph = (it / ST) & 1;
         if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, err)) { ok = false; break; }
-        // Khatri-Rao row of the lead factors for row r0 + lane
-        const int row = r0 + lane;
-        float w[S::WST];
+        // Khatri-Rao rows of the lead factors for the rows of this stage
 #pragma unroll
-        for (int r = 0; r < S::WST; ++r) w[r] = (row < re && r < R) ? 1.f : 0.f;
-        if (row < re) {
-          int idx[CNCPD_NMAX];
-          decode32_t(d, k, 0, h, row, idx);
-          for (int m = 0; m < h; ++m) {
-            const float* U = reinterpret_cast<const float*>(d->U1[k][m]) + (int64_t)idx[m] * R;
+        for (int ii = lane; ii < LT_ROWS; ii += 32) {
+          const int row = r0 + ii;
+          float w[S::WST];
 #pragma unroll
-            for (int r = 0; r < RP; ++r)
-              if (r < R) w[r] *= __ldg(U + r);
+          for (int r = 0; r < S::WST; ++r) w[r] = (row < re && r < R) ? 1.f : 0.f;
+          if (row < re) {
+            int idx[CNCPD_NMAX];
+            decode32_t(d, k, 0, h, row, idx);
+            for (int m = 0; m < h; ++m) {
+              const float* U = reinterpret_cast<const float*>(d->U1[k][m]) + (int64_t)idx[m] * R;
+#pragma unroll
+              for (int r = 0; r < RP; ++r)
+                if (r < R) w[r] *= __ldg(U + r);
+            }
           }
-        }
-        float4* dst = reinterpret_cast<float4*>(ws + s * (S::W_BYTES / 4) + lane * S::WST);
+          float4* dst = reinterpret_cast<float4*>(ws + s * (S::W_BYTES / 4) + ii * S::WST);
 #pragma unroll
-        for (int q = 0; q < S::WST / 4; ++q) dst[q] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+          for (int q = 0; q < S::WST / 4; ++q) dst[q] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+        }
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&full[s]));
       }
@@ -386,9 +425,10 @@ __global__ void __launch_bounds__((LT_CONS + NKR + 1) * 32, 1) k_lead_tma(const 
       if (!mbar_wait(smem_u32(&full[s]), ph, err)) continue;  // error recorded; keep the barrier schedule
       const unsigned char* xt = xs + s * S::X_BYTES;
       const float* wt = ws + s * (S::W_BYTES / 4);
+      constexpr int RQ = LT_ROWS / 4;  // rows per quarter
 #pragma unroll 4
-      for (int i = rq * 8; i < rq * 8 + 8; ++i) {
-        const float4 x = *reinterpret_cast<const float4*>(xt + i * (LT_COLS * 4) + colw * 4);
+      for (int i = rq * RQ; i < rq * RQ + RQ; ++i) {
+        const float4 x = load4(xt + (i * LT_COLS + colw) * (int)sizeof(XT), XT());
         const uint64_t x0 = pack2(x.x, x.x), x1 = pack2(x.y, x.y), x2 = pack2(x.z, x.z), x3 = pack2(x.w, x.w);
         const uint64_t* wr = reinterpret_cast<const uint64_t*>(wt + i * S::WST);
 #pragma unroll
@@ -453,27 +493,27 @@ __global__ void __launch_bounds__((LT_CONS + NKR + 1) * 32, 1) k_lead_tma(const 
 
 // ------------------------------------------------------------- launchers ----
 
-template <int RP>
+template <int RP, typename XT>
 static cudaError_t trailing_tma_impl(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd) {
   const int total = hd.lt_prefix[hd.K];
   if (total == 0) return cudaSuccess;
-  const size_t smem = TrailTma<RP>::SMEM;
-  cudaError_t e = cudaFuncSetAttribute(k_trailing_tma<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = TrailTma<RP, XT>::SMEM;
+  cudaError_t e = cudaFuncSetAttribute(k_trailing_tma<RP, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = total < c.num_sms ? total : c.num_sms;
-  k_trailing_tma<RP><<<grid, (TT_CONS + NKR + 1) * 32, smem, c.stream>>>(dd);
+  k_trailing_tma<RP, XT><<<grid, (TT_CONS + NKR + 1) * 32, smem, c.stream>>>(dd);
   return cudaGetLastError();
 }
 
-template <int RP>
+template <int RP, typename XT>
 static cudaError_t lead_tma_impl(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd) {
   const int total = hd.tt_prefix[hd.K];
   if (total == 0) return cudaSuccess;
-  const size_t smem = LeadTma<RP>::SMEM;
-  cudaError_t e = cudaFuncSetAttribute(k_lead_tma<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = LeadTma<RP, XT>::SMEM;
+  cudaError_t e = cudaFuncSetAttribute(k_lead_tma<RP, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = total < c.num_sms ? total : c.num_sms;
-  k_lead_tma<RP><<<grid, (LT_CONS + NKR + 1) * 32, smem, c.stream>>>(dd);
+  k_lead_tma<RP, XT><<<grid, (LT_CONS + NKR + 1) * 32, smem, c.stream>>>(dd);
   return cudaGetLastError();
 }
 
@@ -486,17 +526,23 @@ bool tma_rank_supported(int RP) {
   return false;
 }
 
-cudaError_t launch_trailing_tma(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int RP) {
-#define TCASE(V) \
-  case V: return trailing_tma_impl<V>(c, dd, hd);
+// Rows of the lead contraction per TMA stage (the split-K plan keeps every
+// split a multiple of this).
+int lead_tma_rows(int st) { return st == ST_BF16 ? LeadTma<4, __nv_bfloat16>::ROWS : LeadTma<4, float>::ROWS; }
+
+cudaError_t launch_trailing_tma(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int RP, int st) {
+#define TCASE(V)                                                                             \
+  case V:                                                                                    \
+    return st == ST_BF16 ? trailing_tma_impl<V, __nv_bfloat16>(c, dd, hd) : trailing_tma_impl<V, float>(c, dd, hd);
   switch (RP) { CNCPD_TMA_RP(TCASE) }
 #undef TCASE
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_lead_tma(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int RP) {
-#define TCASE(V) \
-  case V: return lead_tma_impl<V>(c, dd, hd);
+cudaError_t launch_lead_tma(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int RP, int st) {
+#define TCASE(V)                                                                             \
+  case V:                                                                                    \
+    return st == ST_BF16 ? lead_tma_impl<V, __nv_bfloat16>(c, dd, hd) : lead_tma_impl<V, float>(c, dd, hd);
   switch (RP) { CNCPD_TMA_RP(TCASE) }
 #undef TCASE
   return cudaErrorInvalidValue;

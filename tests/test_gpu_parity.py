@@ -58,6 +58,38 @@ def test_mttkrp_matches_oracle(dims, R, dt):
     m.close()
 
 
+def _to_bf16(a):
+    """Round FP32 values to the nearest BF16 (ties to even), returned as FP32."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+@pytest.mark.parametrize("dims,R", [
+    ([(70, 37, 150), (9, 64, 130)], 10),
+    ([(33, 41, 200)], 20),
+    ([(5, 6, 7, 8)], 12),
+    ([(20, 30, 40)], 33),
+])
+def test_mttkrp_bf16_storage_exact_inputs(dims, R):
+    """BF16 storage of a tensor whose values are already BF16 numbers is
+    lossless, so the MTTKRP (FP32 accumulation) must match the FP64 oracle on
+    the same values to FP32 accumulation accuracy; shapes span several tiles
+    with ragged tails."""
+    rng = np.random.default_rng(R * 7 + len(dims))
+    Xs = [_to_bf16(rng.random(d).astype(np.float32)) for d in dims]
+    N = len(dims[0])
+    U = [[rng.random((I, R)).astype(np.float32) for I in d] for d in dims]
+    m = _P().CoupledNCP(Xs, R, [0] * N, storage="bf16")
+    m.set_factors(U)
+    for k in range(len(dims)):
+        for n in range(N):
+            got = m.mttkrp(k, n)
+            want = O.mttkrp(Xs[k].astype(np.float64), [A.astype(np.float64) for A in U[k]], n)
+            assert rel_fro(got, want) <= 2e-6, (k, n)
+    m.close()
+
+
 # --------------------------------------------------------- Lipschitz -----
 
 @pytest.mark.parametrize("R", [1, 2, 5, 10, 20, 33, 64])
