@@ -878,9 +878,11 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
       off += ((size_t)c->dim(k, n) * R[k] + 31) / 32 * 32;
     }
   c->arena_elems = off;
-  CTRY(dalloc(c, (void**)&c->A1, off * c->fsz));
-  CTRY(dalloc(c, (void**)&c->A2, off * c->fsz));
-  CTRY(dalloc(c, (void**)&c->AS, off * c->fsz));
+  // 64 elements of slack past the last factor: kernels read factor rows as
+  // whole 16-byte vectors up to the padded rank
+  CTRY(dalloc(c, (void**)&c->A1, (off + 64) * c->fsz));
+  CTRY(dalloc(c, (void**)&c->A2, (off + 64) * c->fsz));
+  CTRY(dalloc(c, (void**)&c->AS, (off + 64) * c->fsz));
   const size_t rr = (size_t)c->Rmax * c->Rmax;
   CTRY(dalloc(c, (void**)&d.Gbase, (size_t)K * N * rr * sizeof(double)));
   CTRY(dalloc(c, &d.Hbase, (size_t)K * rr * c->fsz));
@@ -1172,7 +1174,7 @@ int cncpd_lra(cncpd_t h, const int* R_tilde, const void* const* Ut0, cncpd_dtype
     a.R[k] = a.Rt[k] = R_tilde[k];
     for (int n = 0; n < N; ++n) {
       void* u = nullptr;
-      TRY(dalloc(h, &u, (size_t)h->dim(k, n) * R_tilde[k] * h->fsz + 16));
+      TRY(dalloc(h, &u, ((size_t)h->dim(k, n) * R_tilde[k] + 64) * h->fsz));  // slack for whole-row reads
       h->hd.Ut[k][n] = a.Ut[k][n] = a.U1[k][n] = u;
       a.U2[k][n] = nullptr;
       double* g = nullptr;

@@ -307,8 +307,9 @@ def test_host_and_device_inputs_agree():
 
 # ------------------------------------------------------------------ LRA ---
 
-@pytest.mark.parametrize("dt,tol,Rt", [(np.float64, 1e-8, 4), (np.float64, 1e-8, 3), (np.float32, 2e-4, 3)])
-def test_lra_path_matches_oracle(dt, tol, Rt):
+@pytest.mark.parametrize("dt,tol,Rt,storage", [(np.float64, 1e-8, 4, None), (np.float64, 1e-8, 3, None),
+                                               (np.float32, 2e-4, 3, None), (np.float32, 2e-4, 3, "bf16")])
+def test_lra_path_matches_oracle(dt, tol, Rt, storage):
     """lraCoNCPD-APG: ALS low-rank approximation of each block, then the
     collapsed APG iterations, against the oracle's Algorithm 2.  FP32 is
     checked at R~ = R (the paper's setting): with R~ above the data's rank
@@ -316,6 +317,8 @@ def test_lra_path_matches_oracle(dt, tol, Rt):
     dims = [(14, 12, 10)] * 3
     Xs, _, U0 = coupled_inputs(dims, 3, [2, 0, 0], seed=12)
     Xs = [X.astype(dt) for X in Xs]
+    if storage == "bf16":  # values already BF16 numbers: the stored tensor is exact
+        Xs = [_to_bf16(X) for X in Xs]
     X64 = [X.astype(np.float64) for X in Xs]
     rng = np.random.default_rng(13)
     Ut0 = [[rng.random((d, Rt)) for d in dims[0]] for _ in range(3)]
@@ -329,7 +332,7 @@ def test_lra_path_matches_oracle(dt, tol, Rt):
     res = O.apg(prob, U0, max_it=10, eps=0.0,
                 callback=lambda it, st, info: snaps.append([[A.copy() for A in Uk] for Uk in st.U1]))
     P = _P()
-    m = P.CoupledNCP(Xs, 3, [2, 0, 0])
+    m = P.CoupledNCP(Xs, 3, [2, 0, 0], storage=storage)
     m.set_factors(U0)
     st = m.lra(Rt, Ut0)
     assert st["lra_sweeps"] == max(sweeps)
