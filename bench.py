@@ -6,9 +6,16 @@ of the workload.  Default workload: K = 5 coupled tensors of 256^3 in FP32,
 R = 10, L = [3, 3, 0], 10 dB noise (the simulation workload at scale).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME] [--storage f32|bf16|bf16x2] [--lra]
+    python bench.py --time-to-fit [--workload NAME]
 
 Prints one JSON line (rank 0).  The tensors (5 x 67 MB) exceed the 129 MB
-L2, so no flush is needed between iterations.
+L2, so no flush is needed between iterations.  --lra runs the low-rank
+approximation step of lraCoNCPD-APG (rank R~ of the workload) before the
+timed iterations, which then use the collapsed products.  --time-to-fit
+measures, from the host tensors, the wall time until the global fit is within
+1e-4 of the converged FP64 fit, for plain FP32 storage and for the mixed form
+(BF16 storage, plus the LRA step when the workload has an R~).
 """
 
 import argparse
@@ -198,6 +205,13 @@ def run_ours(args):
 
     m = P.CoupledNCP(Xd, w.R, w.L, profile=True, storage=args.storage)
     m.set_factors(U0)
+    lra = None
+    if args.lra:
+        Rt = w.R_lra or w.R
+        t0 = time.perf_counter()
+        sl = m.lra(Rt, synth.init_lra_factors(w.dims, Rt, w.seed))
+        lra = {"R_tilde": Rt, "seconds": time.perf_counter() - t0, "als_sweeps": sl["lra_sweeps"],
+               "als_relerr": sl["lra_relerr"]}
     m.step(args.warmup)
 
     def barrier():
@@ -239,12 +253,17 @@ def run_ours(args):
     kern, tk = ("lead_contract", t_lead) if t_lead >= t_trail else ("trailing_contract", t_trail)
     peak, peak_kind = _peaks()
     pass_bytes = lead_alg if kern == "lead_contract" else trail_alg
-    achieved = pass_bytes / (tk / 1e3) / 1e9
-    roof = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_source": peak_kind,
-            "traffic": _traffic(kern, w.name),
-            "other_kernel_ms": t_trail if kern == "lead_contract" else t_lead,
-            "algorithmic_bytes_per_launch": pass_bytes}
+    if s["stream_launches"] > 0:
+        achieved = pass_bytes / (tk / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": _traffic(kern, w.name),
+                "other_kernel_ms": t_trail if kern == "lead_contract" else t_lead,
+                "algorithmic_bytes_per_launch": pass_bytes}
+    else:  # after the LRA step no iteration reads X
+        roof = {"bound": "latency", "kernel": None, "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
+                "peak_source": peak_kind, "traffic": None,
+                "note": "collapsed products: the iterations read only the low-rank factors (launch/latency bound)"}
     m.close()
     del Xd
 
@@ -254,6 +273,8 @@ def run_ours(args):
     t0 = time.perf_counter()
     m2 = P.CoupledNCP(Xh, w.R, w.L, storage=args.storage)
     m2.set_factors(U0)
+    if args.lra:
+        m2.lra(lra["R_tilde"], synth.init_lra_factors(w.dims, lra["R_tilde"], w.seed))
     s2 = m2.step(args.steps)
     out = m2.factors(np.float32)
     t_e2e = time.perf_counter() - t0
@@ -279,13 +300,77 @@ def run_ours(args):
                        "storage": args.storage,
                        "l2": f"inputs larger than L2 ({x_bytes / 1e6:.0f} MB of stored tensors)",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
-            "reupdates": s["reupdates"], "fit": s["fit"],
+            "reupdates": s["reupdates"], "fit": s["fit"], "lra": lra,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": s["launches"], "clocks": clk,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_time_to_fit(args):
+    """Time-to-fit: wall time from the host tensors (create + set_factors
+    [+ LRA] + iterations) until the fit is within 1e-4 of the fit of the FP64
+    path run to convergence (|delta RelErr| < 1e-8, at most 1000 iterations).
+    The fit of each run's final factors is re-evaluated against the FP32
+    tensors (not the stored BF16 copy) before it counts."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2302_05119_gb300 as P
+    import synth
+    w = _workload(args.workload)
+    X64, _ = synth.make_tensors(w, dtype=np.float64)
+    Xs = [X.astype(np.float32) for X in X64]
+    U0 = synth.init_factors(w.dims, w.R, w.seed)
+    # target: FP64 storage and factors to convergence
+    t0 = time.perf_counter()
+    m = P.CoupledNCP(X64, w.R, w.L, eps=1e-8, max_it=1000)
+    m.set_factors(U0)
+    sf = m.fit()
+    target = m.global_fit()
+    t_ref = time.perf_counter() - t0
+    m.close()
+    del X64
+
+    def fit_vs_fp32(U):
+        v = P.CoupledNCP(Xs, w.R, w.L)
+        v.set_factors(U)
+        f = v.global_fit()
+        v.close()
+        return f
+
+    def run(storage, lra, check_every=10, cap=2000):
+        Xh = [torch.from_numpy(X).pin_memory() for X in Xs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m = P.CoupledNCP(Xh, w.R, w.L, storage=storage)
+        m.set_factors(U0)
+        lra_s = None
+        if lra:
+            Rt = w.R_lra
+            m.lra(Rt, synth.init_lra_factors(w.dims, Rt, w.seed))
+            lra_s = time.perf_counter() - t0
+        it, fit = 0, 0.0
+        while it < cap:
+            m.step(check_every)
+            it += check_every
+            fit = m.global_fit()
+            if fit >= target - 1e-4:
+                break
+        dt = time.perf_counter() - t0
+        U = m.factors(np.float64)
+        m.close()
+        return {"storage": storage, "lra": bool(lra), "seconds": dt, "iterations": it, "fit_stored": fit,
+                "fit_fp32_data": fit_vs_fp32(U), "reached": fit >= target - 1e-4, "lra_seconds": lra_s}
+
+    fp32 = run("f32", False)
+    mixed = run("bf16", bool(w.R_lra))
+    line = {"metric": "time to fit within 1e-4 of the converged FP64 fit", "unit": "s", "workload": w.name,
+            "target_fit": target, "target": {"iterations": sf["total_iters"], "seconds": t_ref},
+            "fp32": fp32, "mixed": mixed,
+            "speedup_mixed_vs_fp32": fp32["seconds"] / mixed["seconds"] if mixed["seconds"] > 0 else None}
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -298,11 +383,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "bf16x2"],
                     help="element type of X on the device (factors and accumulation stay FP32)")
+    ap.add_argument("--lra", action="store_true", help="run the LRA step (lraCoNCPD-APG) before the timed steps")
+    ap.add_argument("--time-to-fit", action="store_true",
+                    help="time to reach the converged FP64 fit within 1e-4, FP32 vs mixed precision")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.time_to_fit:
+        run_time_to_fit(args)
     else:
         run_ours(args)
 
