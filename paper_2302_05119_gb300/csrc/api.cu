@@ -13,6 +13,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
+#include <queue>
 #include <string>
 #include <vector>
 
@@ -213,6 +215,74 @@ void plan_trailing_tiles(DevDesc& d) {
   for (int k = 0; k < d.K; ++k) d.lt_prefix[k + 1] = d.lt_prefix[k] + (int)((d.lead_rows[k] + d.lt_rows - 1) / d.lt_rows);
 }
 
+// Assign units of cost cost[u] to P persistent CTAs, longest first, each to
+// the CTA with the least work so far (ties: lowest index); every CTA then
+// walks its units in increasing id.  Returns P + 1 start offsets followed by
+// the ids.  With equal costs this is the plain round-robin order.
+std::vector<int> lpt_schedule(const std::vector<int64_t>& cost, int P) {
+  const int n = (int)cost.size();
+  std::vector<int> order(n);
+  for (int u = 0; u < n; ++u) order[u] = u;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  using Slot = std::pair<int64_t, int>;  // (load, CTA)
+  std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> heap;
+  for (int p = 0; p < P; ++p) heap.push({0, p});
+  std::vector<std::vector<int>> lists(P);
+  for (int u : order) {
+    Slot s = heap.top();
+    heap.pop();
+    lists[s.second].push_back(u);
+    heap.push({s.first + cost[u], s.second});
+  }
+  std::vector<int> out(P + 1 + n);
+  int pos = P + 1;
+  for (int p = 0; p < P; ++p) {
+    out[p] = pos - (P + 1);
+    std::sort(lists[p].begin(), lists[p].end());
+    for (int u : lists[p]) out[pos++] = u;
+  }
+  out[P] = n;
+  return out;
+}
+
+// Balanced unit lists of the two TMA passes.  A unit's cost is its number of
+// 32 KiB stages plus two for its epilogue.
+int plan_tma_schedules(cncpd_ctx* c, DevDesc& d) {
+  d.lt_sched = d.tt_sched = nullptr;
+  d.lt_grid = d.tt_grid = 0;
+  if (!d.use_tma) return CNCPD_OK;
+  const int bc = trail_tma_cols(c->st), lr = lead_tma_rows(c->st);
+  std::vector<int64_t> lt, tt;
+  for (int k = 0; k < d.K; ++k) {
+    const int64_t nch = (d.trail_cols[k] + bc - 1) / bc;
+    for (int g = d.lt_prefix[k]; g < d.lt_prefix[k + 1]; ++g) lt.push_back(nch + 2);
+    for (int s = 0; s < d.nsplit[k]; ++s) {
+      const int64_t rb = s * d.split_rows[k];
+      const int64_t re = std::min<int64_t>(d.lead_rows[k], rb + d.split_rows[k]);
+      for (int t = 0; t < d.tt_ctiles[k]; ++t) tt.push_back((re - rb + lr - 1) / lr + 2);
+    }
+  }
+  const std::vector<int64_t>* costs[2] = {&lt, &tt};
+  for (int which = 0; which < 2; ++which) {
+    const std::vector<int64_t>& cost = *costs[which];
+    if (cost.empty()) continue;
+    const int P = std::min<int>((int)cost.size(), c->num_sms);
+    const std::vector<int> sched = lpt_schedule(cost, P);
+    int* dev = nullptr;
+    TRY(dalloc(c, (void**)&dev, sched.size() * sizeof(int)));
+    CU(cudaMemcpyAsync(dev, sched.data(), sched.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (which == 0) {
+      d.lt_sched = dev;
+      d.lt_grid = P;
+    } else {
+      d.tt_sched = dev;
+      d.tt_grid = P;
+    }
+  }
+  return CNCPD_OK;
+}
+
 int upload_desc(cncpd_ctx* c) {
   CU(cudaMemcpyAsync(c->dd, &c->hd, sizeof(DevDesc), cudaMemcpyHostToDevice, c->stream));
   if (c->dd_als) CU(cudaMemcpyAsync(c->dd_als, &c->hd_als, sizeof(DevDesc), cudaMemcpyHostToDevice, c->stream));
@@ -381,14 +451,12 @@ int timeout_error(cncpd_ctx* c) {
   return set_err(CNCPD_ETIMEOUT, "a bounded device-side wait expired (pipeline stalled); iteration state discarded");
 }
 
-// The objective at the end of a sweep publishes F to the host mirror; the
-// LRA objective does not, so that path reads the scalars back.
+// The objective at the end of a sweep publishes F to the host mirror.
 // (The snapshot S of U2 taken for a re-update is written by the update kernels.)
 int enqueue_main(cncpd_ctx* c) {
   LaunchCfg lc{c->stream, c->num_sms};
   if (!begin_in_sweep(c)) CU(launch_iter_begin(lc, c->dd, c->hd, c->opts.use_core));
-  TRY(enqueue_sweep(c, 1, 1));
-  return c->lra ? enqueue_readback(c) : CNCPD_OK;
+  return enqueue_sweep(c, 1, 1);
 }
 
 int enqueue_redo(cncpd_ctx* c) {
@@ -398,8 +466,7 @@ int enqueue_redo(cncpd_ctx* c) {
   CU(cudaMemcpyAsync(c->A2, c->AS, arena_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
   CU(launch_gram(lc, c->dd, c->hd, c->fp64, 0, c->N, 0));
   if (c->lra) CU(launch_cross_gram(lc, c->dd, c->hd, c->fp64, 0, c->N));
-  TRY(enqueue_sweep(c, 0, 0));
-  return c->lra ? enqueue_readback(c) : CNCPD_OK;
+  return enqueue_sweep(c, 0, 0);
 }
 
 int capture(cncpd_ctx* c, int (*fn)(cncpd_ctx*), cudaGraphExec_t* out) {
@@ -444,11 +511,10 @@ int run_redo(cncpd_ctx* c) {
 }
 
 // Wait until the objective kernel has published a sequence number other than
-// s0 to the host mirror (or, on the LRA path, until the stream is idle).  The
-// stream is queried now and then, so that a failed launch or a fault ends the
-// wait; a bounded time limit guards against anything else.
+// s0 to the host mirror.  The stream is queried now and then, so that a
+// failed launch or a fault ends the wait; a bounded time limit guards
+// against anything else.
 int wait_published(cncpd_ctx* c, unsigned int s0) {
-  if (c->lra) return sync(c);
   const double t0 = now_s();
   for (unsigned long n = 1;; ++n) {
     if (c->hm->seq != s0) {
@@ -580,7 +646,7 @@ int run_iterations(cncpd_ctx* c, int n_iters, bool use_eps, cncpd_stats* out) {
     TRY(wait_published(c, s0));
     st.x_bytes += pb;
     st.launches += kernels_per_replay(c, 0);
-    double F = c->lra ? c->hs->F : c->hm->F;
+    double F = c->hm->F;
     const bool redo = c->opts.reupdate && (F - c->F_prev) > c->tie_tol * std::fabs(c->F_prev);
     if (redo) {
       const unsigned int s1 = c->hm->seq;
@@ -589,11 +655,11 @@ int run_iterations(cncpd_ctx* c, int n_iters, bool use_eps, cncpd_stats* out) {
       TRY(read_profile(c, &st, 2));
       st.x_bytes += pb;
       st.launches += kernels_per_replay(c, 1);
-      F = c->lra ? c->hs->F : c->hm->F;
+      F = c->hm->F;
       st.reupdates++;
     }
-    const int timeout = c->lra ? c->hs->timeout : c->hm->timeout;
-    const int nonfinite = c->lra ? c->hs->nonfinite : c->hm->nonfinite;
+    const int timeout = c->hm->timeout;
+    const int nonfinite = c->hm->nonfinite;
     if (timeout) {
       TRY(sync(c));
       return timeout_error(c);
@@ -603,7 +669,7 @@ int run_iterations(cncpd_ctx* c, int n_iters, bool use_eps, cncpd_stats* out) {
       return set_err(CNCPD_ENONFINITE, "objective or Lipschitz constant not finite at iteration %d",
                      c->total_iters + 1);
     }
-    const double rel = c->lra ? c->hs->relerr : c->hm->relerr;
+    const double rel = c->hm->relerr;
     c->total_iters++;
     st.iters++;
     c->F_prev = F;
@@ -939,6 +1005,7 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
   size_t pel = 0;
   plan_lead_splits(c, d, c->RP, c->fp64, &pel);
   plan_trailing_tiles(d);
+  CTRY(plan_tma_schedules(c, d));
   CTRY(dalloc(c, &d.partial, pel * c->fsz));
 
   {
@@ -1202,6 +1269,7 @@ int cncpd_lra(cncpd_t h, const int* R_tilde, const void* const* Ut0, cncpd_dtype
   a.use_tma = (a.tmap_trail != nullptr) && tma_rank_supported(h->RPt);
   plan_lead_splits(h, a, h->RPt, h->fp64, &pel);
   plan_trailing_tiles(a);
+  TRY(plan_tma_schedules(h, a));
   TRY(dalloc(h, &a.partial, pel * h->fsz));
   std::vector<int64_t> pre(K + 1, 0);
   for (int k = 0; k < K; ++k) pre[k + 1] = pre[k] + a.trail_cols[k] * R_tilde[k];
@@ -1261,6 +1329,7 @@ int cncpd_lra(cncpd_t h, const int* R_tilde, const void* const* Ut0, cncpd_dtype
       aa.lt_prefix[k + 1] = aa.lt_prefix[k] + (active[k] ? full.lt_prefix[k + 1] - full.lt_prefix[k] : 0);
       aa.tt_prefix[k + 1] = aa.tt_prefix[k] + (active[k] ? full.tt_prefix[k + 1] - full.tt_prefix[k] : 0);
     }
+    if (nact < K) aa.lt_sched = aa.tt_sched = nullptr;  // the lists number the units of all blocks
     CU(cudaMemcpyAsync(h->dd_als, &aa, sizeof(DevDesc), cudaMemcpyHostToDevice, h->stream));
     CU(cudaMemcpyAsync(h->d_active, active.data(), CNCPD_KMAX * sizeof(int), cudaMemcpyHostToDevice, h->stream));
     CU(cudaMemsetAsync(h->d_status, 0, CNCPD_KMAX * sizeof(int), h->stream));

@@ -49,8 +49,6 @@ struct DevScalars {
   double Ldprev[CNCPD_KMAX], Ldcur[CNCPD_KMAX];
   double cterm[CNCPD_KMAX][CNCPD_RMAX];    // (U^{odot})^T vec(X^(k)) at the current factors
   double cterm_save[CNCPD_KMAX][CNCPD_RMAX];
-  double ip[CNCPD_KMAX];                   // <X^(k), X_hat^(k)>
-  double xhat2[CNCPD_KMAX];                // ||X_hat^(k)||^2
   double lam1[CNCPD_KMAX][CNCPD_RMAX];     // cores: current, previous, snapshot
   double lam2[CNCPD_KMAX][CNCPD_RMAX];
   double lamS[CNCPD_KMAX][CNCPD_RMAX];
@@ -115,6 +113,11 @@ struct DevDesc {
   int tt_ctiles[CNCPD_KMAX];           // column tiles per block
   int tt_cpt;                          // columns per thread of that kernel
   int pad1;
+  // balanced unit lists of the TMA passes (null: unit g goes to CTA g mod grid).
+  // Layout: grid + 1 start offsets, then the unit ids of CTA 0, CTA 1, ...
+  const int* lt_sched;
+  const int* tt_sched;
+  int lt_grid, tt_grid;                // CTAs the lists were made for
   DevScalars* sc;
   int* err;                            // device error word (bounded waits, bad state)
   HostMirror* hm;                      // device address of the host mirror (null: none)
@@ -233,6 +236,7 @@ cudaError_t launch_reduce_splits(const LaunchCfg& c, const DevDesc& h_desc, int 
 cudaError_t launch_trailing_tma(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int RP, int st);
 cudaError_t launch_lead_tma(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int RP, int st);
 int lead_tma_rows(int st);
+int trail_tma_cols(int st);
 cudaError_t launch_level2(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int RP, int n);
 cudaError_t launch_gram(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int n_begin, int n_end, int which);
 // Level-2 of mode n (two-mode groups) and H / L of mode n in one launch

@@ -13,44 +13,56 @@
 namespace cncpd {
 
 // C^(n,k) = U~^(n,k)^T U^(n,k) (R~ x R), FP64 output (Table II operations 8, 9).
+// One CTA per (block, mode); rows are staged in shared memory CG_ROWS at a
+// time, each thread keeps up to CG_PT entries of C: an FMA chain in the
+// factor type over the rows of a tile, added to an FP64 sum per tile.
+constexpr int CG_ROWS = 32;
+constexpr int CG_PT = CNCPD_RMAX * CNCPD_RMAX / 256;
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_cross_gram(const DevDesc* __restrict__ d, int n_begin, int n_end) {
   const int nm = n_end - n_begin;
   const int k = blockIdx.x / nm;
   const int n = n_begin + blockIdx.x % nm;
-  const T* A = reinterpret_cast<const T*>(d->Ut[k][n]);
-  const T* B = reinterpret_cast<const T*>(d->U1[k][n]);
+  const T* __restrict__ A = reinterpret_cast<const T*>(d->Ut[k][n]);
+  const T* __restrict__ B = reinterpret_cast<const T*>(d->U1[k][n]);
   const int Ra = d->Rt[k], Rb = d->R[k];
   double* C = d->C[k][n];
   const int64_t I = d->dims[k][n];
   const int P = Ra * Rb;
-  __shared__ double red[256];
   const int tid = threadIdx.x;
-  for (int p0 = 0; p0 < P; p0 += 256) {
-    const int np = min(256, P - p0);
-    const int Y = max(1, 256 / np);
-    const int p = p0 + tid % np;
-    const int y = tid / np;
-    double acc = 0.0;
-    if (tid < np * Y) {
-      const int a = p / Rb, b = p % Rb;
-      T part = T(0);
-      int cnt = 0;
-      for (int64_t i = y; i < I; i += Y) {
-        part = fma(A[i * Ra + a], B[i * Rb + b], part);
-        if (++cnt == 64) { acc += (double)part; part = T(0); cnt = 0; }
-      }
-      acc += (double)part;
-    }
-    red[tid] = acc;
-    __syncthreads();
-    if (tid < np) {
-      double s = 0.0;
-      for (int yy = 0; yy < Y; ++yy) s += red[yy * np + tid];
-      C[p0 + tid] = s;
-    }
-    __syncthreads();
+  __shared__ T As[CG_ROWS * CNCPD_RMAX];
+  __shared__ T Bs[CG_ROWS * CNCPD_RMAX];
+  const int mine = P > tid ? (P - tid + 255) / 256 : 0;  // entries of this thread: p = tid + 256 j
+  int ia[CG_PT], ib[CG_PT];
+  double acc[CG_PT];
+#pragma unroll
+  for (int j = 0; j < CG_PT; ++j) {
+    const int p = min(tid + 256 * j, P - 1);
+    ia[j] = p / Rb;
+    ib[j] = p % Rb;
+    acc[j] = 0.0;
   }
+  for (int64_t i0 = 0; i0 < I; i0 += CG_ROWS) {
+    const int nr = (int)(I - i0 < CG_ROWS ? I - i0 : CG_ROWS);
+    __syncthreads();
+    for (int e = tid; e < nr * Ra; e += 256) As[e] = A[i0 * Ra + e];
+    for (int e = tid; e < nr * Rb; e += 256) Bs[e] = B[i0 * Rb + e];
+    __syncthreads();
+    T ch[CG_PT];
+#pragma unroll
+    for (int j = 0; j < CG_PT; ++j) ch[j] = T(0);
+    for (int i = 0; i < nr; ++i) {
+#pragma unroll
+      for (int j = 0; j < CG_PT; ++j)
+        if (j < mine) ch[j] = fma(As[i * Ra + ia[j]], Bs[i * Rb + ib[j]], ch[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < CG_PT; ++j) acc[j] += (double)ch[j];
+  }
+#pragma unroll
+  for (int j = 0; j < CG_PT; ++j)
+    if (j < mine) C[tid + 256 * j] = acc[j];
 }
 
 cudaError_t launch_cross_gram(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int n_begin,
@@ -105,54 +117,88 @@ cudaError_t launch_collapsed_m(const LaunchCfg& c, const DevDesc* dd, const DevD
 // Objective of Eq. cosfunclra at the current factors:
 //   F_k = 1/2 (||X~||^2 - 2 lambda^T c + lambda^T (*_m G^(m)) lambda),
 //   c_r = sum_q prod_m C^(m)[q, r]  (Eq. eqlrag; also the next core term).
-__global__ void __launch_bounds__(64) k_lra_objective(const DevDesc* __restrict__ d) {
-  const int K = d->K, N = d->N;
+// One CTA per block, FP64 throughout; the last CTA to finish adds the blocks
+// up in order and publishes F to the host mirror.
+__global__ void __launch_bounds__(256) k_lra_objective(const DevDesc* __restrict__ d) {
+  const int N = d->N, k = blockIdx.x, tid = threadIdx.x;
   DevScalars* sc = d->sc;
-  __shared__ double cr[CNCPD_RMAX];
-  for (int k = 0; k < K; ++k) {
-    const int R = d->R[k], Rt = d->Rt[k];
-    for (int r = threadIdx.x; r < R; r += blockDim.x) {
-      double s = 0.0;
-      for (int q = 0; q < Rt; ++q) {
-        double p = 1.0;
-        for (int m = 0; m < N; ++m) p *= d->C[k][m][q * R + r];
-        s += p;
-      }
-      cr[r] = s;
-      sc->cterm[k][r] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double ip = 0.0, xx = 0.0;
-      for (int a = 0; a < R; ++a) {
-        const double la = sc->lam1[k][a];
-        ip += la * cr[a];
-        for (int b = 0; b < R; ++b) {
-          double g = 1.0;
-          for (int m = 0; m < N; ++m) g *= d->G[k][m][a * R + b];
-          xx += la * sc->lam1[k][b] * g;
-        }
-      }
-      const double x2 = sc->xnorm2[k];
-      const double Fk = 0.5 * (x2 - 2.0 * ip + xx);
-      sc->Fk[k] = Fk;
-      sc->relk[k] = x2 > 0.0 ? sqrt(fmax(2.0 * Fk, 0.0) / x2) : 0.0;
-      sc->ip[k] = ip;
-      sc->xhat2[k] = xx;
-    }
-    __syncthreads();
+  const int R = d->R[k], Rt = d->Rt[k];
+  __shared__ double pr[CNCPD_RMAX * CNCPD_RMAX];
+  __shared__ double part[8][CNCPD_RMAX];
+  __shared__ double wsum[8];
+  __shared__ int is_last;
+  // prod_m C^(m)[q, r] for every (q, r)
+  for (int p = tid; p < Rt * R; p += 256) {
+    double v = 1.0;
+    for (int m = 0; m < N; ++m) v *= d->C[k][m][p];
+    pr[p] = v;
   }
-  if (threadIdx.x == 0) {
+  // lambda^T (*_m G^(m)) lambda, one term per thread and (a, b)
+  double xx = 0.0;
+  for (int p = tid; p < R * R; p += 256) {
+    double g = sc->lam1[k][p / R] * sc->lam1[k][p % R];
+    for (int m = 0; m < N; ++m) g *= d->G[k][m][p];
+    xx += g;
+  }
+  __syncthreads();
+  // c_r: the rows q = y, y + Y, ... in thread (y, r), then the Y partial sums in order
+  const int Y = min(8, 256 / R);
+  if (tid < Y * R) {
+    const int y = tid / R, r = tid % R;
+    double s = 0.0;
+    for (int q = y; q < Rt; q += Y) s += pr[q * R + r];
+    part[y][r] = s;
+  }
+  __syncthreads();
+  if (tid < R) {
+    double s = 0.0;
+    for (int y = 0; y < Y; ++y) s += part[y][tid];
+    sc->cterm[k][tid] = s;
+    xx -= 2.0 * sc->lam1[k][tid] * s;
+  }
+  for (int o = 16; o > 0; o >>= 1) xx += __shfl_xor_sync(0xffffffffu, xx, o);
+  if ((tid & 31) == 0) wsum[tid >> 5] = xx;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += wsum[q];
+    const double x2 = sc->xnorm2[k];
+    const double Fk = 0.5 * (x2 + t);
+    sc->Fk[k] = Fk;
+    sc->relk[k] = sqrt(fmax(2.0 * Fk, 0.0) * sc->inv_xnorm2[k]);
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) is_last = (atomicAdd(&sc->done_counter[1], 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (is_last && tid == 0) {
+    __threadfence();
     double F = 0.0, rel = 0.0;
-    for (int k = 0; k < K; ++k) { F += sc->Fk[k]; rel += sc->relk[k]; }
+    for (int q = 0; q < (int)gridDim.x; ++q) {
+      F += __ldcg(&sc->Fk[q]);
+      rel += __ldcg(&sc->relk[q]);
+    }
+    const double relerr = rel / gridDim.x;
     sc->F = F;
-    sc->relerr = rel / K;
+    sc->relerr = relerr;
     if (!isfinite(F)) sc->nonfinite = 1;
+    sc->done_counter[1] = 0;
+    if (d->hm) {
+      HostMirror* hm = d->hm;
+      hm->F = F;
+      hm->relerr = relerr;
+      hm->nonfinite = *((volatile int*)&sc->nonfinite);
+      hm->timeout = *((volatile int*)&sc->timeout);
+      const unsigned int q = sc->seq + 1;
+      sc->seq = q;
+      __threadfence_system();
+      hm->seq = q;
+    }
   }
 }
 
-cudaError_t launch_lra_objective(const LaunchCfg& c, const DevDesc* dd, const DevDesc&, int, int) {
-  k_lra_objective<<<1, 64, 0, c.stream>>>(dd);
+cudaError_t launch_lra_objective(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int, int) {
+  k_lra_objective<<<hd.K, 256, 0, c.stream>>>(dd);
   return cudaGetLastError();
 }
 

@@ -25,6 +25,27 @@ __device__ __forceinline__ void decode32_t(const DevDesc* d, int k, int m0, int 
   }
 }
 
+// The work units of this CTA: the host's balanced list when there is one,
+// else every gridDim.x-th unit.  unit(j) for j = first; j < end; j += step.
+struct Units {
+  const int* ids;
+  int first, end, step;
+  __device__ __forceinline__ Units(const int* sched, int total) {
+    if (sched) {
+      ids = sched + gridDim.x + 1;
+      first = __ldg(sched + blockIdx.x);
+      end = __ldg(sched + blockIdx.x + 1);
+      step = 1;
+    } else {
+      ids = nullptr;
+      first = blockIdx.x;
+      end = total;
+      step = gridDim.x;
+    }
+  }
+  __device__ __forceinline__ int unit(int j) const { return ids ? __ldg(ids + j) : j; }
+};
+
 // Sixteen bytes of X as FP32 values: four FP32 or eight BF16 elements.
 template <typename XT>
 struct XChunk {
@@ -81,6 +102,10 @@ struct TrailTma {
   static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 128 - RED_BYTES) / (X_BYTES + W_BYTES));
   static constexpr int STAGES = STAGES_FIT > 6 ? 6 : STAGES_FIT;
   static constexpr size_t SMEM = 1024 + STAGES * (size_t)(X_BYTES + W_BYTES) + RED_BYTES + 2 * STAGES * 8;
+  // A Khatri-Rao warp takes every NKR-th stage; with more warps than stages it
+  // could reach a slot two phases ahead of its consumers, which a parity wait
+  // cannot tell from the phase it wants.
+  static_assert(STAGES >= NKR, "the stage ring must hold at least one stage per Khatri-Rao warp");
 };
 
 template <int RP, typename XT>
@@ -107,20 +132,21 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
   }
   __syncthreads();
   const int K = d->K, N = d->N, h = d->h;
-  const int total = d->lt_prefix[K];
+  const Units us(d->lt_sched, d->lt_prefix[K]);
 
   if (warp == TT_CONS + NKR) {
     // ------------------------------------------- TMA issuer (one thread)
     if (lane != 0) return;
     uint32_t it = 0;
     bool ok = true;
-    for (int g = blockIdx.x; g < total && ok; g += gridDim.x) {
+    for (int j = us.first; j < us.end && ok; j += us.step) {
+      const int g = us.unit(j);
       int k = 0;
       while (d->lt_prefix[k + 1] <= g) ++k;
       const int row0 = (g - d->lt_prefix[k]) * TT_ROWS;
       const int J = (int)d->trail_cols[k];
       const int nch = (J + TT_BC - 1) / TT_BC;
-      if (g == blockIdx.x) prefetch_tmap(&maps[k]);
+      prefetch_tmap(&maps[k]);
       for (int c = 0; c < nch; ++c, ++it) {
         const int s = it % TST;
         const uint32_t ph = (it / TST) & 1;
@@ -140,7 +166,8 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
     const int kw = warp - TT_CONS;
     uint32_t it = 0;
     bool ok = true;
-    for (int g = blockIdx.x; g < total && ok; g += gridDim.x) {
+    for (int jn = us.first; jn < us.end && ok; jn += us.step) {
+      const int g = us.unit(jn);
       int k = 0;
       while (d->lt_prefix[k + 1] <= g) ++k;
       const int J = (int)d->trail_cols[k];
@@ -183,7 +210,8 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
   uint32_t it = 0;
   const int rq = warp & 1, cq = warp >> 1;  // row half (128 rows, 4 per lane), column quarter (8 columns)
   constexpr int RH = RP / 2;
-  for (int g = blockIdx.x; g < total; g += gridDim.x) {
+  for (int jn = us.first; jn < us.end; jn += us.step) {
+    const int g = us.unit(jn);
     int k = 0;
     while (d->lt_prefix[k + 1] <= g) ++k;
     const int row0 = (g - d->lt_prefix[k]) * TT_ROWS;
@@ -295,6 +323,7 @@ struct LeadTma {
   static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 128 - RED_BYTES) / (X_BYTES + W_BYTES));
   static constexpr int STAGES = STAGES_FIT > 6 ? 6 : STAGES_FIT;
   static constexpr size_t SMEM = 1024 + STAGES * (size_t)(X_BYTES + W_BYTES) + RED_BYTES + 2 * STAGES * 8;
+  static_assert(STAGES >= NKR, "the stage ring must hold at least one stage per Khatri-Rao warp");
 };
 
 template <int RP, typename XT>
@@ -322,14 +351,15 @@ __global__ void __launch_bounds__((LT_CONS + NKR + 1) * 32, 1) k_lead_tma(const 
   }
   __syncthreads();
   const int K = d->K, h = d->h;
-  const int total = d->tt_prefix[K];
+  const Units us(d->tt_sched, d->tt_prefix[K]);
 
   if (warp == LT_CONS + NKR) {
     // ------------------------------------------- TMA issuer (one thread)
     if (lane != 0) return;
     uint32_t it = 0;
     bool ok = true;
-    for (int u = blockIdx.x; u < total && ok; u += gridDim.x) {
+    for (int j = us.first; j < us.end && ok; j += us.step) {
+      const int u = us.unit(j);
       int k = 0;
       while (d->tt_prefix[k + 1] <= u) ++k;
       const int local = u - d->tt_prefix[k];
@@ -338,7 +368,7 @@ __global__ void __launch_bounds__((LT_CONS + NKR + 1) * 32, 1) k_lead_tma(const 
       const int rows = (int)d->lead_rows[k];
       const int rb = split * (int)d->split_rows[k];
       const int re = min(rows, rb + (int)d->split_rows[k]);
-      if (u == blockIdx.x) prefetch_tmap(&maps[k]);
+      prefetch_tmap(&maps[k]);
       for (int r0 = rb; r0 < re; r0 += LT_ROWS, ++it) {
         const int s = it % ST;
         const uint32_t ph = (it / ST) & 1;
@@ -357,7 +387,8 @@ __global__ void __launch_bounds__((LT_CONS + NKR + 1) * 32, 1) k_lead_tma(const 
     const int kw = warp - LT_CONS;
     uint32_t it = 0;
     bool ok = true;
-    for (int u = blockIdx.x; u < total && ok; u += gridDim.x) {
+    for (int j = us.first; j < us.end && ok; j += us.step) {
+      const int u = us.unit(j);
       int k = 0;
       while (d->tt_prefix[k + 1] <= u) ++k;
       const int local = u - d->tt_prefix[k];
@@ -403,7 +434,8 @@ __global__ void __launch_bounds__((LT_CONS + NKR + 1) * 32, 1) k_lead_tma(const 
   const int ch = warp & 1, rq = warp >> 1;  // column half (128 columns, 4 per lane), row quarter (8 rows)
   const int colw = ch * 128 + 4 * lane;    // first of this lane's four columns within the tile
   uint32_t it = 0;
-  for (int u = blockIdx.x; u < total; u += gridDim.x) {
+  for (int j = us.first; j < us.end; j += us.step) {
+    const int u = us.unit(j);
     int k = 0;
     while (d->tt_prefix[k + 1] <= u) ++k;
     const int local = u - d->tt_prefix[k];
@@ -500,7 +532,7 @@ static cudaError_t trailing_tma_impl(const LaunchCfg& c, const DevDesc* dd, cons
   const size_t smem = TrailTma<RP, XT>::SMEM;
   cudaError_t e = cudaFuncSetAttribute(k_trailing_tma<RP, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int grid = total < c.num_sms ? total : c.num_sms;
+  const int grid = hd.lt_sched ? hd.lt_grid : (total < c.num_sms ? total : c.num_sms);
   k_trailing_tma<RP, XT><<<grid, (TT_CONS + NKR + 1) * 32, smem, c.stream>>>(dd);
   return cudaGetLastError();
 }
@@ -512,7 +544,7 @@ static cudaError_t lead_tma_impl(const LaunchCfg& c, const DevDesc* dd, const De
   const size_t smem = LeadTma<RP, XT>::SMEM;
   cudaError_t e = cudaFuncSetAttribute(k_lead_tma<RP, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int grid = total < c.num_sms ? total : c.num_sms;
+  const int grid = hd.tt_sched ? hd.tt_grid : (total < c.num_sms ? total : c.num_sms);
   k_lead_tma<RP, XT><<<grid, (LT_CONS + NKR + 1) * 32, smem, c.stream>>>(dd);
   return cudaGetLastError();
 }
@@ -529,6 +561,8 @@ bool tma_rank_supported(int RP) {
 // Rows of the lead contraction per TMA stage (the split-K plan keeps every
 // split a multiple of this).
 int lead_tma_rows(int st) { return st == ST_BF16 ? LeadTma<4, __nv_bfloat16>::ROWS : LeadTma<4, float>::ROWS; }
+// Columns of the trailing contraction per TMA stage.
+int trail_tma_cols(int st) { return st == ST_BF16 ? TrailTma<4, __nv_bfloat16>::BC : TrailTma<4, float>::BC; }
 
 cudaError_t launch_trailing_tma(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int RP, int st) {
 #define TCASE(V)                                                                             \
