@@ -245,21 +245,28 @@ std::vector<int> lpt_schedule(const std::vector<int64_t>& cost, int P) {
   return out;
 }
 
-// Balanced unit lists of the two TMA passes.  A unit's cost is its number of
-// 32 KiB stages plus two for its epilogue.
+// Balanced unit lists of the two TMA passes.  A unit's cost is the number of
+// tensor elements it reads (the in-range part of its tiles) plus two stages'
+// worth for its epilogue.
 int plan_tma_schedules(cncpd_ctx* c, DevDesc& d) {
   d.lt_sched = d.tt_sched = nullptr;
   d.lt_grid = d.tt_grid = 0;
   if (!d.use_tma) return CNCPD_OK;
-  const int bc = trail_tma_cols(c->st), lr = lead_tma_rows(c->st);
+  const int64_t stage_elems = 32768 / (c->st == ST_BF16 ? 2 : 4);
   std::vector<int64_t> lt, tt;
   for (int k = 0; k < d.K; ++k) {
-    const int64_t nch = (d.trail_cols[k] + bc - 1) / bc;
-    for (int g = d.lt_prefix[k]; g < d.lt_prefix[k + 1]; ++g) lt.push_back(nch + 2);
+    const int64_t rows = d.lead_rows[k], J = d.trail_cols[k];
+    for (int g = d.lt_prefix[k]; g < d.lt_prefix[k + 1]; ++g) {
+      const int64_t r0 = (int64_t)(g - d.lt_prefix[k]) * d.lt_rows;
+      lt.push_back(std::min<int64_t>(d.lt_rows, rows - r0) * J + 2 * stage_elems);
+    }
     for (int s = 0; s < d.nsplit[k]; ++s) {
       const int64_t rb = s * d.split_rows[k];
-      const int64_t re = std::min<int64_t>(d.lead_rows[k], rb + d.split_rows[k]);
-      for (int t = 0; t < d.tt_ctiles[k]; ++t) tt.push_back((re - rb + lr - 1) / lr + 2);
+      const int64_t re = std::min<int64_t>(rows, rb + d.split_rows[k]);
+      for (int t = 0; t < d.tt_ctiles[k]; ++t) {
+        const int64_t cols = std::min<int64_t>(d.tt_cols, J - (int64_t)t * d.tt_cols);
+        tt.push_back((re - rb) * cols + 2 * stage_elems);
+      }
     }
   }
   const std::vector<int64_t>* costs[2] = {&lt, &tt};

@@ -236,7 +236,6 @@ cudaError_t launch_reduce_splits(const LaunchCfg& c, const DevDesc& h_desc, int 
 cudaError_t launch_trailing_tma(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int RP, int st);
 cudaError_t launch_lead_tma(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int RP, int st);
 int lead_tma_rows(int st);
-int trail_tma_cols(int st);
 cudaError_t launch_level2(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int RP, int n);
 cudaError_t launch_gram(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int n_begin, int n_end, int which);
 // Level-2 of mode n (two-mode groups) and H / L of mode n in one launch

@@ -97,7 +97,7 @@ struct TrailTma {
   static constexpr int WST = (RP + 3) / 4 * 4;
   static constexpr uint32_t X_BYTES = TT_ROWS * 128;
   static constexpr uint32_t W_BYTES = BC * WST * 4;
-  static constexpr uint32_t RED_BYTES = 3 * TT_ROWS * RP * 4;  // partial sums of column quarters 1..3
+  static constexpr uint32_t RED_BYTES = 3 * TT_ROWS * RP * 4;  // partial sums of column quarters 1..3, [quarter][rank][row]
   // as many stages as fit (at most 6): bytes in flight hide the memory latency
   static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 128 - RED_BYTES) / (X_BYTES + W_BYTES));
   static constexpr int STAGES = STAGES_FIT > 6 ? 6 : STAGES_FIT;
@@ -272,8 +272,8 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
         for (int p = 0; p < RH; ++p) {
           const float2 v = unpack2(acc[j][p]);
           const int r = rq * 128 + 32 * j + lane;
-          red[((cq - 1) * TT_ROWS + r) * RP + 2 * p] = v.x;
-          red[((cq - 1) * TT_ROWS + r) * RP + 2 * p + 1] = v.y;
+          red[((cq - 1) * RP + 2 * p) * TT_ROWS + r] = v.x;
+          red[((cq - 1) * RP + 2 * p + 1) * TT_ROWS + r] = v.y;
         }
     }
     named_bar(1, TT_CONS * 32);
@@ -290,8 +290,8 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
             float o0 = v.x, o1 = v.y;
 #pragma unroll
             for (int q4 = 0; q4 < 3; ++q4) {
-              o0 += red[(q4 * TT_ROWS + r) * RP + 2 * p];
-              o1 += red[(q4 * TT_ROWS + r) * RP + 2 * p + 1];
+              o0 += red[(q4 * RP + 2 * p) * TT_ROWS + r];
+              o1 += red[(q4 * RP + 2 * p + 1) * TT_ROWS + r];
             }
             if (2 * p < R) P[(int64_t)(row0 + r) * R + 2 * p] = o0;
             if (2 * p + 1 < R) P[(int64_t)(row0 + r) * R + 2 * p + 1] = o1;
@@ -319,7 +319,7 @@ struct LeadTma {
   static constexpr int WST = (RP + 3) / 4 * 4;
   static constexpr uint32_t X_BYTES = ROWS * LT_COLS * (int)sizeof(XT);
   static constexpr uint32_t W_BYTES = ROWS * WST * 4;
-  static constexpr uint32_t RED_BYTES = 3 * LT_COLS * RP * 4;  // partial sums of row quarters 1..3
+  static constexpr uint32_t RED_BYTES = 3 * LT_COLS * RP * 4;  // partial sums of row quarters 1..3, [quarter][rank][slot]
   static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 128 - RED_BYTES) / (X_BYTES + W_BYTES));
   static constexpr int STAGES = STAGES_FIT > 6 ? 6 : STAGES_FIT;
   static constexpr size_t SMEM = 1024 + STAGES * (size_t)(X_BYTES + W_BYTES) + RED_BYTES + 2 * STAGES * 8;
@@ -488,14 +488,17 @@ __global__ void __launch_bounds__((LT_CONS + NKR + 1) * 32, 1) k_lead_tma(const 
     }
     // row quarters 1..3 park their sums; quarter 0 adds them in order
     named_bar(1, LT_CONS * 32);
+    // slot c * 64 + ch * 32 + lane holds column colw + c: consecutive lanes,
+    // consecutive words
     if (rq > 0) {
 #pragma unroll
       for (int c = 0; c < 4; ++c)
 #pragma unroll
         for (int p = 0; p < RH; ++p) {
           const float2 v = unpack2(acc[c][p]);
-          red[((rq - 1) * LT_COLS + colw + c) * RP + 2 * p] = v.x;
-          red[((rq - 1) * LT_COLS + colw + c) * RP + 2 * p + 1] = v.y;
+          const int slot = c * 64 + ch * 32 + lane;
+          red[((rq - 1) * RP + 2 * p) * LT_COLS + slot] = v.x;
+          red[((rq - 1) * RP + 2 * p + 1) * LT_COLS + slot] = v.y;
         }
     }
     named_bar(1, LT_CONS * 32);
@@ -510,9 +513,11 @@ __global__ void __launch_bounds__((LT_CONS + NKR + 1) * 32, 1) k_lead_tma(const 
             const float2 v = unpack2(acc[c][p]);
             float o0 = v.x, o1 = v.y;
 #pragma unroll
+            const int slot = c * 64 + ch * 32 + lane;
+#pragma unroll
             for (int q4 = 0; q4 < 3; ++q4) {
-              o0 += red[(q4 * LT_COLS + colw + c) * RP + 2 * p];
-              o1 += red[(q4 * LT_COLS + colw + c) * RP + 2 * p + 1];
+              o0 += red[(q4 * RP + 2 * p) * LT_COLS + slot];
+              o1 += red[(q4 * RP + 2 * p + 1) * LT_COLS + slot];
             }
             if (2 * p < R) part[(int64_t)col * R + 2 * p] = o0;
             if (2 * p + 1 < R) part[(int64_t)col * R + 2 * p + 1] = o1;
@@ -561,8 +566,6 @@ bool tma_rank_supported(int RP) {
 // Rows of the lead contraction per TMA stage (the split-K plan keeps every
 // split a multiple of this).
 int lead_tma_rows(int st) { return st == ST_BF16 ? LeadTma<4, __nv_bfloat16>::ROWS : LeadTma<4, float>::ROWS; }
-// Columns of the trailing contraction per TMA stage.
-int trail_tma_cols(int st) { return st == ST_BF16 ? TrailTma<4, __nv_bfloat16>::BC : TrailTma<4, float>::BC; }
 
 cudaError_t launch_trailing_tma(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int RP, int st) {
 #define TCASE(V)                                                                             \
