@@ -75,7 +75,9 @@ typedef struct {
                         (F64 input -> F64 path; anything else -> F32 factors) */
   int use_graph;     /* 1: replay each sweep as a CUDA graph */
   int profile;       /* 1: time the tensor-streaming kernels with CUDA events */
-  int reserved[6];
+  int tensor_cores;  /* 1: BF16-stored third-order tensors with ranks up to 32 stream
+                        through tcgen05 tensor-core passes; 0: CUDA-core passes only */
+  int reserved[5];
 } cncpd_opts;
 
 /* Results of a solver call. */

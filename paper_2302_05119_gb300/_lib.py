@@ -20,7 +20,7 @@ class cncpd_opts(ctypes.Structure):
                 ("delta_w", ctypes.c_double), ("use_core", ctypes.c_int),
                 ("reupdate", ctypes.c_int), ("storage", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("profile", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("tensor_cores", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
 class cncpd_stats(ctypes.Structure):

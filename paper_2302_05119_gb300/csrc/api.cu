@@ -167,6 +167,22 @@ bool encode_map(CUtensorMap* m, const void* base, int st, int64_t rows, int64_t 
   return r == CUDA_SUCCESS;
 }
 
+// 3-D tensor map of a BF16 third-order tensor stored as (I0 I1) rows of J
+// elements (row pitch `pitch`): dims (J, I1, I0), boxes of 64 x 64 x 1 with
+// the 128-byte swizzle.
+bool encode_x3(CUtensorMap* m, const void* base, int64_t J, int64_t I1, int64_t I0, int64_t pitch) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)J, (cuuint64_t)I1, (cuuint64_t)I0};
+  cuuint64_t strides[2] = {(cuuint64_t)(pitch * 2), (cuuint64_t)(I1 * pitch * 2)};
+  cuuint32_t box[3] = {64, 64, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 int dalloc(cncpd_ctx* c, void** p, size_t bytes) {
   if (bytes == 0) bytes = 16;
   cudaError_t e = cudaMalloc(p, bytes);
@@ -178,10 +194,47 @@ int dalloc(cncpd_ctx* c, void** p, size_t bytes) {
   return CNCPD_OK;
 }
 
+// tcgen05 passes of a BF16 third-order problem with ranks up to 32: buffers
+// for the split factors that are the MMAs' B operands and the TMA
+// descriptors of the 3-D view of X and of the split factors.  d.use_umma
+// stays 0 when the problem does not qualify (the CUDA-core passes run).
+int setup_umma(cncpd_ctx* c, DevDesc& d, int Rmax) {
+  d.use_umma = 0;
+  d.umma_np = 0;
+  const int np = umma_np(Rmax);
+  if (!c->opts.tensor_cores || c->st != ST_BF16 || d.N != 3 || d.h != 2 || np == 0 || !d.tmap_trail ||
+      !tensor_map_encoder())
+    return CNCPD_OK;
+  std::vector<CUtensorMap> maps(3 * CNCPD_KMAX);
+  for (int k = 0; k < d.K; ++k) {
+    const int64_t J = d.trail_cols[k], I1 = d.dims[k][1], I0 = d.dims[k][0];
+    d.bt_pitch[k] = (J + 7) / 8 * 8;
+    d.bl_pitch[k] = (I1 + 7) / 8 * 8;
+    TRY(dalloc(c, &d.Bt[k], (size_t)3 * np * d.bt_pitch[k] * 2));
+    TRY(dalloc(c, &d.Bl[k], (size_t)3 * np * d.bl_pitch[k] * 2));
+    if (!encode_x3(&maps[k], d.X[k], J, I1, I0, d.pitch[k]) ||
+        !encode_map(&maps[CNCPD_KMAX + k], d.Bt[k], ST_BF16, 3 * np, J, d.bt_pitch[k], 64, 3 * np,
+                    CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !encode_map(&maps[2 * CNCPD_KMAX + k], d.Bl[k], ST_BF16, 3 * np, I1, d.bl_pitch[k], 64, 3 * np,
+                    CU_TENSOR_MAP_SWIZZLE_128B))
+      return CNCPD_OK;
+  }
+  CUtensorMap* dm = nullptr;
+  TRY(dalloc(c, (void**)&dm, maps.size() * sizeof(CUtensorMap)));
+  CU(cudaMemcpyAsync(dm, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  d.tmap_lead3 = dm;
+  d.tmap_bt = dm + CNCPD_KMAX;
+  d.tmap_bl = dm + 2 * CNCPD_KMAX;
+  d.umma_np = np;
+  d.use_umma = 1;
+  return CNCPD_OK;
+}
+
 // Split-K plan of the lead-mode contraction for rank bucket RP.
 void plan_lead_splits(cncpd_ctx* c, DevDesc& d, int RP, int fp64, size_t* partial_elems) {
   const int cpt = lead_cpt(fp64, RP);
-  const int tile_cols = d.use_tma ? 256 : 64 * cpt;
+  const int tile_cols = (d.use_tma || d.use_umma) ? 256 : 64 * cpt;
   int64_t tot_rows = 0;
   for (int k = 0; k < d.K; ++k) tot_rows += d.lead_rows[k];
   // aim for ~2 CTAs (of 256 threads) per SM in total, at least 64 rows per split
@@ -194,8 +247,13 @@ void plan_lead_splits(cncpd_ctx* c, DevDesc& d, int RP, int fp64, size_t* partia
     const int64_t rows = d.lead_rows[k];
     int64_t want = std::max<int64_t>(1, (target_units * rows) / std::max<int64_t>(1, tot_rows) / ctiles);
     int64_t split_rows = (rows + want - 1) / want;
-    split_rows = std::max<int64_t>(split_rows, 64);
-    split_rows = ((split_rows + 63) / 64) * 64;  // whole stages of the lead contraction
+    if (d.use_umma) {
+      const int64_t I1 = d.dims[k][1];
+      split_rows = (split_rows + I1 - 1) / I1 * I1;  // whole i0 slabs of the tensor-core pass
+    } else {
+      split_rows = std::max<int64_t>(split_rows, 64);
+      split_rows = ((split_rows + 63) / 64) * 64;  // whole stages of the lead contraction
+    }
     const int ns = (int)((rows + split_rows - 1) / split_rows);
     d.tt_ctiles[k] = ctiles;
     d.nsplit[k] = ns;
@@ -210,7 +268,7 @@ void plan_lead_splits(cncpd_ctx* c, DevDesc& d, int RP, int fp64, size_t* partia
 }
 
 void plan_trailing_tiles(DevDesc& d) {
-  d.lt_rows = d.use_tma ? 256 : 64;
+  d.lt_rows = (d.use_tma || d.use_umma) ? 256 : 64;
   d.lt_prefix[0] = 0;
   for (int k = 0; k < d.K; ++k) d.lt_prefix[k + 1] = d.lt_prefix[k] + (int)((d.lead_rows[k] + d.lt_rows - 1) / d.lt_rows);
 }
@@ -251,7 +309,7 @@ std::vector<int> lpt_schedule(const std::vector<int64_t>& cost, int P) {
 int plan_tma_schedules(cncpd_ctx* c, DevDesc& d) {
   d.lt_sched = d.tt_sched = nullptr;
   d.lt_grid = d.tt_grid = 0;
-  if (!d.use_tma) return CNCPD_OK;
+  if (!d.use_tma && !d.use_umma) return CNCPD_OK;
   const int64_t stage_elems = 32768 / (c->st == ST_BF16 ? 2 : 4);
   std::vector<int64_t> lt, tt;
   for (int k = 0; k < d.K; ++k) {
@@ -352,8 +410,10 @@ int enqueue_mode_m(cncpd_ctx* c, int n) {
 
 int enqueue_trailing(cncpd_ctx* c, const DevDesc* dd, const DevDesc& hd, int RP) {
   LaunchCfg lc{c->stream, c->num_sms};
+  if (hd.use_umma) CU(launch_split_factor(lc, dd, hd, 0));
   TRY(record(c, 0));
-  if (hd.use_tma) CU(launch_trailing_tma(lc, dd, hd, RP, c->st));
+  if (hd.use_umma) CU(launch_trailing_umma(lc, dd, hd));
+  else if (hd.use_tma) CU(launch_trailing_tma(lc, dd, hd, RP, c->st));
   else CU(launch_trailing_contract(lc, dd, hd, c->st, RP));
   TRY(record(c, 1));
   return CNCPD_OK;
@@ -364,8 +424,13 @@ int enqueue_trailing(cncpd_ctx* c, const DevDesc* dd, const DevDesc& hd, int RP)
 int enqueue_lead(cncpd_ctx* c, const DevDesc* dd, const DevDesc& hd, int RP, const int64_t* red_prefix,
                  int with_reduce = 1) {
   LaunchCfg lc{c->stream, c->num_sms};
+  if (hd.use_umma) CU(launch_split_factor(lc, dd, hd, 1));
   TRY(record(c, 2));
-  if (hd.use_tma) {
+  if (hd.use_umma) {
+    CU(launch_lead_umma(lc, dd, hd));
+    TRY(record(c, 3));
+    if (with_reduce) CU(launch_reduce_splits(lc, hd, c->fp64));
+  } else if (hd.use_tma) {
     CU(launch_lead_tma(lc, dd, hd, RP, c->st));
     TRY(record(c, 3));
     if (with_reduce) CU(launch_reduce_splits(lc, hd, c->fp64));
@@ -608,12 +673,13 @@ double pass_bytes(cncpd_ctx* c) {
 long long kernels_per_replay(cncpd_ctx* c, int redo) {
   long long n = c->opts.use_core ? 1 : 0;                 // core update
   if (!redo && !begin_in_sweep(c)) n += 1;                // iteration bookkeeping
-  if (redo) n += 1 + 2 + (c->lra ? 1 : 0);                // restore, Grams (chunks + sums), cross Grams
+  if (redo) n += 1 + 2 + (c->lra ? 2 : 0);                // restore, Grams (chunks + sums), cross Grams (same)
   if (!c->lra) n += 2 + (fused_last_reduce(c) ? 0 : 1);  // both tensor passes (+ split reduction)
+  if (!c->lra && c->hd.use_umma) n += 2;                  // split factors of the tensor-core passes
   for (int m = 0; m < c->N; ++m) {
     n += 2;                                               // Lipschitz (alone or with level 2), update
     if (c->lra) {
-      n += 2;                                             // collapsed M, cross Gram
+      n += 3;                                             // collapsed M, cross Gram (chunks + sums)
     } else {
       const int gsize = (m < c->h) ? c->h : c->N - c->h;
       const bool forked = (m == c->h);
@@ -753,6 +819,7 @@ void cncpd_default_opts(cncpd_opts* o) {
   o->storage = -1;
   o->use_graph = 1;
   o->profile = 0;
+  o->tensor_cores = 1;
 }
 
 const char* cncpd_last_error(void) { return g_err.c_str(); }
@@ -1009,6 +1076,7 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
     }
   }
   d.use_tma = (d.tmap_trail != nullptr) && tma_rank_supported(c->RP);
+  CTRY(setup_umma(c, d, c->Rmax));
   size_t pel = 0;
   plan_lead_splits(c, d, c->RP, c->fp64, &pel);
   plan_trailing_tiles(d);
@@ -1272,8 +1340,17 @@ int cncpd_lra(cncpd_t h, const int* R_tilde, const void* const* Ut0, cncpd_dtype
     TRY(dalloc(h, &p, (size_t)R_tilde[k] * R_tilde[k] * h->fsz));
     h->hd.Vinv[k] = a.Vinv[k] = p;
   }
+  // chunk values of the cross Grams (main descriptor only)
+  h->hd.cld = rtmax * h->hd.Rmax;
+  for (int n = 0; n < N; ++n) {
+    int64_t imax = 0;
+    for (int k = 0; k < K; ++k) imax = std::max<int64_t>(imax, h->dim(k, n));
+    h->hd.cgnc[n] = (int)((imax + CROSS_ROWS - 1) / CROSS_ROWS);
+    TRY(dalloc(h, &h->hd.Cp[n], (size_t)K * h->hd.cgnc[n] * h->hd.cld * h->fsz));
+  }
   size_t pel = 0;
   a.use_tma = (a.tmap_trail != nullptr) && tma_rank_supported(h->RPt);
+  TRY(setup_umma(h, a, rtmax));
   plan_lead_splits(h, a, h->RPt, h->fp64, &pel);
   plan_trailing_tiles(a);
   TRY(plan_tma_schedules(h, a));

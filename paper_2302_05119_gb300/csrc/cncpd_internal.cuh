@@ -134,7 +134,25 @@ struct DevDesc {
   void* Gp[CNCPD_NMAX];
   int gr[CNCPD_NMAX];
   int gnc[CNCPD_NMAX];
+  // LRA path: chunk values of the cross Grams C^(n,k) = U~^T U, chunks of
+  // CROSS_ROWS rows; chunk c of block k at Cp[n] + (k*cgnc[n] + c)*cld.
+  void* Cp[CNCPD_NMAX];
+  int cgnc[CNCPD_NMAX];
+  int cld, pad3;
+  // tcgen05 passes (BF16 storage, N = 3): the split factors that are the B
+  // operands (3 NP rows, row pitch bt_pitch / bl_pitch elements) and their
+  // TMA descriptors; tmap_lead3 views X^(k) as (J, I1, I0) in boxes of 64 x 64 x 1
+  int use_umma, umma_np;
+  void* Bt[CNCPD_KMAX];
+  void* Bl[CNCPD_KMAX];
+  int64_t bt_pitch[CNCPD_KMAX];
+  int64_t bl_pitch[CNCPD_KMAX];
+  const CUtensorMap* tmap_lead3;
+  const CUtensorMap* tmap_bt;
+  const CUtensorMap* tmap_bl;
 };
+
+constexpr int CROSS_ROWS = 32;
 
 // -------------------------------------------------------------- helpers ----
 
@@ -197,6 +215,45 @@ inline int rank_bucket(int R) {
 // consecutive kernels (the TMA passes need almost all of it) run with one
 // L1 / shared split and the SMs are not reconfigured between launches.  Set
 // once per kernel and device, before the kernel's first launch.
+// Compensated FP32 addition (hi, lo) += x (Knuth's TwoSum); FP64 is slow on
+// this part, and a pair of FP32 values carries about 48 bits.
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  lo += (hi - (s - bp)) + (x - bp);
+  hi = s;
+}
+
+// Sum of the first nch chunk values of entry p (stride rr), in chunk order
+// (compensated FP32 for FP32 factors, FP64 otherwise); the loads of up to 32
+// chunks are issued before any of them is added.
+template <typename T>
+__device__ __forceinline__ double gram_sum(const T* __restrict__ gp, int nch, int rr, int p) {
+  if constexpr (sizeof(T) == 4) {
+    float hi = 0.f, lo = 0.f;
+    for (int c0 = 0; c0 < nch; c0 += 32) {
+      float x[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) x[j] = gp[(size_t)min(c0 + j, nch - 1) * rr + p];  // clamped: no predicate
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (c0 + j < nch) ff_add(hi, lo, x[j]);
+    }
+    return (double)hi + (double)lo;
+  } else {
+    double s = 0.0;
+    for (int c0 = 0; c0 < nch; c0 += 32) {
+      double x[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) x[j] = gp[(size_t)min(c0 + j, nch - 1) * rr + p];
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (c0 + j < nch) s += x[j];
+    }
+    return s;
+  }
+}
+
 template <auto Kernel>
 inline void carve() {
   static std::atomic<unsigned long long> done{0};
@@ -236,6 +293,11 @@ cudaError_t launch_reduce_splits(const LaunchCfg& c, const DevDesc& h_desc, int 
 cudaError_t launch_trailing_tma(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int RP, int st);
 cudaError_t launch_lead_tma(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int RP, int st);
 int lead_tma_rows(int st);
+// tcgen05 passes for BF16 third-order tensors (ranks up to 32)
+int umma_np(int Rmax);
+cudaError_t launch_split_factor(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int which);
+cudaError_t launch_trailing_umma(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc);
+cudaError_t launch_lead_umma(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc);
 cudaError_t launch_level2(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int RP, int n);
 cudaError_t launch_gram(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int n_begin, int n_end, int which);
 // Level-2 of mode n (two-mode groups) and H / L of mode n in one launch

@@ -12,66 +12,66 @@
 
 namespace cncpd {
 
-// C^(n,k) = U~^(n,k)^T U^(n,k) (R~ x R), FP64 output (Table II operations 8, 9).
-// One CTA per (block, mode); rows are staged in shared memory CG_ROWS at a
-// time, each thread keeps up to CG_PT entries of C: an FMA chain in the
-// factor type over the rows of a tile, added to an FP64 sum per tile.
-constexpr int CG_ROWS = 32;
-constexpr int CG_PT = CNCPD_RMAX * CNCPD_RMAX / 256;
+// C^(n,k) = U~^(n,k)^T U^(n,k) (R~ x R), FP64 output (Table II operations 8, 9),
+// formed like the Grams: the rows are cut into chunks of CROSS_ROWS rows, each
+// chunk gives one FMA chain in the factor type per entry (k_cross_chunks, one
+// CTA per chunk, rows staged in shared memory), and the chunk values are
+// added in chunk order (k_cross_reduce, compensated FP32 for FP32 factors).
+template <typename T>
+__global__ void __launch_bounds__(256) k_cross_chunks(const DevDesc* __restrict__ d, int n0, int n1) {
+  const int nm = n1 - n0;
+  const int k = blockIdx.y / nm, n = n0 + blockIdx.y % nm;
+  const int c = blockIdx.x;
+  const int64_t I = d->dims[k][n];
+  const int64_t row0 = (int64_t)c * CROSS_ROWS;
+  if (c >= d->cgnc[n] || row0 >= I) return;
+  const int rows = (int)min((int64_t)CROSS_ROWS, I - row0);
+  const int Ra = d->Rt[k], Rb = d->R[k];
+  __shared__ T As[CROSS_ROWS * CNCPD_RMAX];
+  __shared__ T Bs[CROSS_ROWS * CNCPD_RMAX];
+  const T* __restrict__ A = reinterpret_cast<const T*>(d->Ut[k][n]) + row0 * Ra;
+  const T* __restrict__ B = reinterpret_cast<const T*>(d->U1[k][n]) + row0 * Rb;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < rows * Ra; e += 256) As[e] = A[e];
+#pragma unroll 4
+  for (int e = threadIdx.x; e < rows * Rb; e += 256) Bs[e] = B[e];
+  __syncthreads();
+  T* out = reinterpret_cast<T*>(d->Cp[n]) + ((size_t)k * d->cgnc[n] + c) * d->cld;
+  for (int p = threadIdx.x; p < Ra * Rb; p += 256) {
+    const int a = p / Rb, b = p % Rb;
+    T s = T(0);
+    for (int i = 0; i < rows; ++i) s = fma(As[i * Ra + a], Bs[i * Rb + b], s);
+    out[p] = s;
+  }
+}
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_cross_gram(const DevDesc* __restrict__ d, int n_begin, int n_end) {
-  const int nm = n_end - n_begin;
-  const int k = blockIdx.x / nm;
-  const int n = n_begin + blockIdx.x % nm;
-  const T* __restrict__ A = reinterpret_cast<const T*>(d->Ut[k][n]);
-  const T* __restrict__ B = reinterpret_cast<const T*>(d->U1[k][n]);
-  const int Ra = d->Rt[k], Rb = d->R[k];
+__global__ void __launch_bounds__(256) k_cross_reduce(const DevDesc* __restrict__ d, int n0, int n1) {
+  const int nm = n1 - n0;
+  const int k = blockIdx.x / nm, n = n0 + blockIdx.x % nm;
+  const int P = d->Rt[k] * d->R[k];
+  const int nch = (int)((d->dims[k][n] + CROSS_ROWS - 1) / CROSS_ROWS);
+  const T* gp = reinterpret_cast<const T*>(d->Cp[n]) + (size_t)k * d->cgnc[n] * d->cld;
   double* C = d->C[k][n];
-  const int64_t I = d->dims[k][n];
-  const int P = Ra * Rb;
-  const int tid = threadIdx.x;
-  __shared__ T As[CG_ROWS * CNCPD_RMAX];
-  __shared__ T Bs[CG_ROWS * CNCPD_RMAX];
-  const int mine = P > tid ? (P - tid + 255) / 256 : 0;  // entries of this thread: p = tid + 256 j
-  int ia[CG_PT], ib[CG_PT];
-  double acc[CG_PT];
-#pragma unroll
-  for (int j = 0; j < CG_PT; ++j) {
-    const int p = min(tid + 256 * j, P - 1);
-    ia[j] = p / Rb;
-    ib[j] = p % Rb;
-    acc[j] = 0.0;
-  }
-  for (int64_t i0 = 0; i0 < I; i0 += CG_ROWS) {
-    const int nr = (int)(I - i0 < CG_ROWS ? I - i0 : CG_ROWS);
-    __syncthreads();
-    for (int e = tid; e < nr * Ra; e += 256) As[e] = A[i0 * Ra + e];
-    for (int e = tid; e < nr * Rb; e += 256) Bs[e] = B[i0 * Rb + e];
-    __syncthreads();
-    T ch[CG_PT];
-#pragma unroll
-    for (int j = 0; j < CG_PT; ++j) ch[j] = T(0);
-    for (int i = 0; i < nr; ++i) {
-#pragma unroll
-      for (int j = 0; j < CG_PT; ++j)
-        if (j < mine) ch[j] = fma(As[i * Ra + ia[j]], Bs[i * Rb + ib[j]], ch[j]);
-    }
-#pragma unroll
-    for (int j = 0; j < CG_PT; ++j) acc[j] += (double)ch[j];
-  }
-#pragma unroll
-  for (int j = 0; j < CG_PT; ++j)
-    if (j < mine) C[tid + 256 * j] = acc[j];
+  for (int p = threadIdx.x; p < P; p += 256) C[p] = gram_sum<T>(gp, nch, d->cld, p);
+}
+
+template <typename T>
+static cudaError_t cross_gram_impl(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int n_begin, int n_end) {
+  const int nm = n_end - n_begin;
+  int cmax = 1;
+  for (int n = n_begin; n < n_end; ++n) cmax = hd.cgnc[n] > cmax ? hd.cgnc[n] : cmax;
+  k_cross_chunks<T><<<dim3((unsigned)cmax, (unsigned)(hd.K * nm)), 256, 0, c.stream>>>(dd, n_begin, n_end);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_cross_reduce<T><<<hd.K * nm, 256, 0, c.stream>>>(dd, n_begin, n_end);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_cross_gram(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int n_begin,
                               int n_end) {
   if (n_end <= n_begin) return cudaSuccess;
-  const int grid = hd.K * (n_end - n_begin);
-  if (fp64) k_cross_gram<double><<<grid, 256, 0, c.stream>>>(dd, n_begin, n_end);
-  else k_cross_gram<float><<<grid, 256, 0, c.stream>>>(dd, n_begin, n_end);
-  return cudaGetLastError();
+  return fp64 ? cross_gram_impl<double>(c, dd, hd, n_begin, n_end) : cross_gram_impl<float>(c, dd, hd, n_begin, n_end);
 }
 
 // M^(n,k) = U~^(n) Hc with Hc = (U~^T U)^{circledast_-n} (R~ x R).  Grid

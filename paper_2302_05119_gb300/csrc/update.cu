@@ -217,45 +217,6 @@ __device__ __forceinline__ T gram_chain(const T* U, int64_t row0, int rows, int 
   return s;
 }
 
-// Compensated FP32 addition (hi, lo) += x (Knuth's TwoSum); FP64 is slow on
-// this part, and a pair of FP32 values carries about 48 bits.
-__device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
-  const float s = hi + x;
-  const float bp = s - hi;
-  lo += (hi - (s - bp)) + (x - bp);
-  hi = s;
-}
-
-// Sum of the first nch chunk values of entry p (stride rr), in chunk order
-// (compensated FP32 for FP32 factors, FP64 otherwise); the loads of up to 32
-// chunks are issued before any of them is added.
-template <typename T>
-__device__ __forceinline__ double gram_sum(const T* __restrict__ gp, int nch, int rr, int p) {
-  if constexpr (sizeof(T) == 4) {
-    float hi = 0.f, lo = 0.f;
-    for (int c0 = 0; c0 < nch; c0 += 32) {
-      float x[32];
-#pragma unroll
-      for (int j = 0; j < 32; ++j) x[j] = gp[(size_t)min(c0 + j, nch - 1) * rr + p];  // clamped: no predicate
-#pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (c0 + j < nch) ff_add(hi, lo, x[j]);
-    }
-    return (double)hi + (double)lo;
-  } else {
-    double s = 0.0;
-    for (int c0 = 0; c0 < nch; c0 += 32) {
-      double x[32];
-#pragma unroll
-      for (int j = 0; j < 32; ++j) x[j] = gp[(size_t)min(c0 + j, nch - 1) * rr + p];
-#pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (c0 + j < nch) s += x[j];
-    }
-    return s;
-  }
-}
-
 template <typename T>
 __global__ void __launch_bounds__(256) k_gram_chunks(const DevDesc* __restrict__ d, int n0, int n1) {
   const int nm = n1 - n0;

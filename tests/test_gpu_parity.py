@@ -71,19 +71,40 @@ def _to_bf16(a):
     ([(5, 6, 7, 8)], 12),
     ([(20, 30, 40)], 33),
 ])
-def test_mttkrp_bf16_storage_exact_inputs(dims, R):
+@pytest.mark.parametrize("tensor_cores", [True, False])
+def test_mttkrp_bf16_storage_exact_inputs(dims, R, tensor_cores):
     """BF16 storage of a tensor whose values are already BF16 numbers is
     lossless, so the MTTKRP (FP32 accumulation) must match the FP64 oracle on
     the same values to FP32 accumulation accuracy; shapes span several tiles
-    with ragged tails."""
+    with ragged tails.  Third-order cases with R <= 32 run on the tcgen05
+    passes when tensor_cores is set (the factors enter as three BF16 parts)."""
     rng = np.random.default_rng(R * 7 + len(dims))
     Xs = [_to_bf16(rng.random(d).astype(np.float32)) for d in dims]
     N = len(dims[0])
     U = [[rng.random((I, R)).astype(np.float32) for I in d] for d in dims]
-    m = _P().CoupledNCP(Xs, R, [0] * N, storage="bf16")
+    m = _P().CoupledNCP(Xs, R, [0] * N, storage="bf16", tensor_cores=tensor_cores)
     m.set_factors(U)
     for k in range(len(dims)):
         for n in range(N):
+            got = m.mttkrp(k, n)
+            want = O.mttkrp(Xs[k].astype(np.float64), [A.astype(np.float64) for A in U[k]], n)
+            assert rel_fro(got, want) <= 2e-6, (k, n)
+    m.close()
+
+
+@pytest.mark.parametrize("R", [12, 20])
+def test_mttkrp_bf16_tensor_cores_many_units(R):
+    """The tcgen05 passes with many work units per CTA (hundreds of 256-row
+    tiles, i0 slabs split across CTAs, ragged K and column tails) against the
+    FP64 oracle on BF16-exact values."""
+    rng = np.random.default_rng(40 + R)
+    dims = [(300, 260, 200), (280, 260, 136)]
+    Xs = [_to_bf16(rng.random(d).astype(np.float32)) for d in dims]
+    U = [[rng.random((I, R)).astype(np.float32) for I in d] for d in dims]
+    m = _P().CoupledNCP(Xs, R, [0, 0, 0], storage="bf16", tensor_cores=True)
+    m.set_factors(U)
+    for k in range(len(dims)):
+        for n in range(3):
             got = m.mttkrp(k, n)
             want = O.mttkrp(Xs[k].astype(np.float64), [A.astype(np.float64) for A in U[k]], n)
             assert rel_fro(got, want) <= 2e-6, (k, n)
