@@ -231,48 +231,6 @@ int setup_umma(cncpd_ctx* c, DevDesc& d, int Rmax) {
   return CNCPD_OK;
 }
 
-// Split-K plan of the lead-mode contraction for rank bucket RP.
-void plan_lead_splits(cncpd_ctx* c, DevDesc& d, int RP, int fp64, size_t* partial_elems) {
-  const int cpt = lead_cpt(fp64, RP);
-  const int tile_cols = (d.use_tma || d.use_umma) ? 256 : 64 * cpt;
-  int64_t tot_rows = 0;
-  for (int k = 0; k < d.K; ++k) tot_rows += d.lead_rows[k];
-  // aim for ~2 CTAs (of 256 threads) per SM in total, at least 64 rows per split
-  const int64_t target_units = (int64_t)c->num_sms * 2;
-  d.tt_prefix[0] = 0;
-  size_t off = 0;
-  for (int k = 0; k < d.K; ++k) {
-    const int64_t J = d.trail_cols[k];
-    const int ctiles = (int)((J + tile_cols - 1) / tile_cols);
-    const int64_t rows = d.lead_rows[k];
-    int64_t want = std::max<int64_t>(1, (target_units * rows) / std::max<int64_t>(1, tot_rows) / ctiles);
-    int64_t split_rows = (rows + want - 1) / want;
-    if (d.use_umma) {
-      const int64_t I1 = d.dims[k][1];
-      split_rows = (split_rows + I1 - 1) / I1 * I1;  // whole i0 slabs of the tensor-core pass
-    } else {
-      split_rows = std::max<int64_t>(split_rows, 64);
-      split_rows = ((split_rows + 63) / 64) * 64;  // whole stages of the lead contraction
-    }
-    const int ns = (int)((rows + split_rows - 1) / split_rows);
-    d.tt_ctiles[k] = ctiles;
-    d.nsplit[k] = ns;
-    d.split_rows[k] = split_rows;
-    d.partial_off[k] = (int64_t)off;
-    off += (size_t)ns * J * d.R[k];
-    d.tt_prefix[k + 1] = d.tt_prefix[k] + ctiles * ns;
-  }
-  d.tt_cpt = cpt;
-  d.tt_cols = tile_cols;
-  *partial_elems = off;
-}
-
-void plan_trailing_tiles(DevDesc& d) {
-  d.lt_rows = (d.use_tma || d.use_umma) ? 256 : 64;
-  d.lt_prefix[0] = 0;
-  for (int k = 0; k < d.K; ++k) d.lt_prefix[k + 1] = d.lt_prefix[k] + (int)((d.lead_rows[k] + d.lt_rows - 1) / d.lt_rows);
-}
-
 // Assign units of cost cost[u] to P persistent CTAs, longest first, each to
 // the CTA with the least work so far (ties: lowest index); every CTA then
 // walks its units in increasing id.  Returns P + 1 start offsets followed by
@@ -303,6 +261,115 @@ std::vector<int> lpt_schedule(const std::vector<int64_t>& cost, int P) {
   return out;
 }
 
+// Largest total cost of a CTA when lpt_schedule assigns `cost` to P CTAs.
+int64_t lpt_makespan(const std::vector<int64_t>& cost, int P) {
+  const std::vector<int> sched = lpt_schedule(cost, P);
+  int64_t worst = 0;
+  for (int p = 0; p < P; ++p) {
+    int64_t load = 0;
+    for (int q = sched[p]; q < sched[p + 1]; ++q) load += cost[sched[P + 1 + q]];
+    worst = std::max(worst, load);
+  }
+  return worst;
+}
+
+// Cost of one unit of the persistent passes, in bytes of DRAM time: the
+// larger of the bytes of X it reads (`valid` elements) and its arithmetic on
+// the whole tile (`tile` elements, out-of-range parts included): R FMAs per
+// element on the CUDA cores, 0.16 byte-times each (R = 25 matches the HBM
+// rate of FP32 data on this GPU), or about a quarter of the DRAM time of a
+// full tile on the tensor cores; plus four 32 KiB stages for the unit's
+// epilogue and pipeline refill (measured on the 256^3 workload: 1, 2, 4 and 8
+// lead units per SM took 56, 60, 67 and 74 us).
+int64_t unit_cost(const DevDesc& d, int st, int64_t valid, int64_t tile) {
+  const int64_t es = st == ST_BF16 ? 2 : 4;
+  const int64_t work = d.use_umma ? tile / 2 : tile * d.Rmax * 16 / 100;
+  return std::max(valid * es, work) + 4 * 32768;
+}
+
+// Split-K plan of the lead-mode contraction for rank bucket RP.
+// Split-K plan aiming at about target_units units in all.
+void plan_lead_units(cncpd_ctx* c, DevDesc& d, int RP, int fp64, int64_t target_units, size_t* partial_elems) {
+  const int cpt = lead_cpt(fp64, RP);
+  const int tile_cols = (d.use_tma || d.use_umma) ? 256 : 64 * cpt;
+  int64_t tot_rows = 0;
+  for (int k = 0; k < d.K; ++k) tot_rows += d.lead_rows[k];
+  d.tt_prefix[0] = 0;
+  size_t off = 0;
+  for (int k = 0; k < d.K; ++k) {
+    const int64_t J = d.trail_cols[k];
+    const int ctiles = (int)((J + tile_cols - 1) / tile_cols);
+    const int64_t rows = d.lead_rows[k];
+    int64_t want = std::max<int64_t>(1, (target_units * rows) / std::max<int64_t>(1, tot_rows) / ctiles);
+    int64_t split_rows = (rows + want - 1) / want;
+    if (d.use_umma) {
+      const int64_t I1 = d.dims[k][1];
+      split_rows = (split_rows + I1 - 1) / I1 * I1;  // whole i0 slabs of the tensor-core pass
+    } else {
+      split_rows = std::max<int64_t>(split_rows, 64);
+      split_rows = ((split_rows + 63) / 64) * 64;  // whole stages of the lead contraction
+    }
+    const int ns = (int)((rows + split_rows - 1) / split_rows);
+    d.tt_ctiles[k] = ctiles;
+    d.nsplit[k] = ns;
+    d.split_rows[k] = split_rows;
+    d.partial_off[k] = (int64_t)off;
+    off += (size_t)ns * J * d.R[k];
+    d.tt_prefix[k + 1] = d.tt_prefix[k] + ctiles * ns;
+  }
+  d.tt_cpt = cpt;
+  d.tt_cols = tile_cols;
+  *partial_elems = off;
+}
+
+// Unit costs of the current lead plan (unit order of tt_prefix).
+std::vector<int64_t> lead_unit_costs(const cncpd_ctx* c, const DevDesc& d) {
+  std::vector<int64_t> tt;
+  for (int k = 0; k < d.K; ++k) {
+    const int64_t rows = d.lead_rows[k], J = d.trail_cols[k];
+    for (int s = 0; s < d.nsplit[k]; ++s) {
+      const int64_t rb = s * d.split_rows[k];
+      const int64_t re = std::min<int64_t>(rows, rb + d.split_rows[k]);
+      for (int t = 0; t < d.tt_ctiles[k]; ++t) {
+        const int64_t cols = std::min<int64_t>(d.tt_cols, J - (int64_t)t * d.tt_cols);
+        tt.push_back(unit_cost(d, c->st, (re - rb) * cols, (re - rb) * d.tt_cols));
+      }
+    }
+  }
+  return tt;
+}
+
+// Split-K plan of the lead pass.  The generic kernel takes about two
+// 256-thread CTAs per SM.  For the persistent passes (one CTA per SM walking
+// a longest-first unit list) the plan is the one, among about 1, 2, 3, 4, 6
+// or 8 units per SM, whose list has the smallest largest load; ties go to
+// fewer units (fewer split-K partials to add up).
+void plan_lead_splits(cncpd_ctx* c, DevDesc& d, int RP, int fp64, size_t* partial_elems) {
+  if (!d.use_tma && !d.use_umma) {
+    plan_lead_units(c, d, RP, fp64, (int64_t)c->num_sms * 2, partial_elems);
+    return;
+  }
+  int best = 1;
+  int64_t best_span = -1;
+  for (int mult : {1, 2, 3, 4, 6, 8}) {
+    plan_lead_units(c, d, RP, fp64, (int64_t)c->num_sms * mult, partial_elems);
+    const std::vector<int64_t> cost = lead_unit_costs(c, d);
+    const int P = std::min<int>((int)cost.size(), c->num_sms);
+    const int64_t span = lpt_makespan(cost, P);
+    if (best_span < 0 || span < best_span) {
+      best_span = span;
+      best = mult;
+    }
+  }
+  plan_lead_units(c, d, RP, fp64, (int64_t)c->num_sms * best, partial_elems);
+}
+
+void plan_trailing_tiles(DevDesc& d) {
+  d.lt_rows = (d.use_tma || d.use_umma) ? 256 : 64;
+  d.lt_prefix[0] = 0;
+  for (int k = 0; k < d.K; ++k) d.lt_prefix[k + 1] = d.lt_prefix[k] + (int)((d.lead_rows[k] + d.lt_rows - 1) / d.lt_rows);
+}
+
 // Balanced unit lists of the two TMA passes.  A unit's cost is the number of
 // tensor elements it reads (the in-range part of its tiles) plus two stages'
 // worth for its epilogue.
@@ -310,23 +377,15 @@ int plan_tma_schedules(cncpd_ctx* c, DevDesc& d) {
   d.lt_sched = d.tt_sched = nullptr;
   d.lt_grid = d.tt_grid = 0;
   if (!d.use_tma && !d.use_umma) return CNCPD_OK;
-  const int64_t stage_elems = 32768 / (c->st == ST_BF16 ? 2 : 4);
-  std::vector<int64_t> lt, tt;
+  std::vector<int64_t> lt;
   for (int k = 0; k < d.K; ++k) {
     const int64_t rows = d.lead_rows[k], J = d.trail_cols[k];
     for (int g = d.lt_prefix[k]; g < d.lt_prefix[k + 1]; ++g) {
       const int64_t r0 = (int64_t)(g - d.lt_prefix[k]) * d.lt_rows;
-      lt.push_back(std::min<int64_t>(d.lt_rows, rows - r0) * J + 2 * stage_elems);
-    }
-    for (int s = 0; s < d.nsplit[k]; ++s) {
-      const int64_t rb = s * d.split_rows[k];
-      const int64_t re = std::min<int64_t>(rows, rb + d.split_rows[k]);
-      for (int t = 0; t < d.tt_ctiles[k]; ++t) {
-        const int64_t cols = std::min<int64_t>(d.tt_cols, J - (int64_t)t * d.tt_cols);
-        tt.push_back((re - rb) * cols + 2 * stage_elems);
-      }
+      lt.push_back(unit_cost(d, c->st, std::min<int64_t>(d.lt_rows, rows - r0) * J, (int64_t)d.lt_rows * J));
     }
   }
+  const std::vector<int64_t> tt = lead_unit_costs(c, d);
   const std::vector<int64_t>* costs[2] = {&lt, &tt};
   for (int which = 0; which < 2; ++which) {
     const std::vector<int64_t>& cost = *costs[which];

@@ -223,6 +223,9 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
     for (int j = 0; j < 4; ++j)
 #pragma unroll
       for (int p = 0; p < RH; ++p) acc[j][p] = 0ull;
+    // quarter 0 is done with the previous tile's partial sums: the other
+    // quarters may write this tile's (barrier 2)
+    if (cq == 0) named_bar_arrive(2, TT_CONS * 32);
     for (int c = 0; c < nch; ++c, ++it) {
       const int s = it % TST;
       const uint32_t ph = (it / TST) & 1;
@@ -263,9 +266,10 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
     }
-    // column quarters 1..3 park their sums; quarter 0 adds them in order
-    named_bar(1, TT_CONS * 32);
+    // column quarters 1..3 park their sums and go on with the next tile;
+    // quarter 0 waits for them (barrier 1) and adds them in order
     if (cq > 0) {
+      named_bar(2, TT_CONS * 32);
 #pragma unroll
       for (int j = 0; j < 4; ++j)
 #pragma unroll
@@ -275,9 +279,9 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
           red[((cq - 1) * RP + 2 * p) * TT_ROWS + r] = v.x;
           red[((cq - 1) * RP + 2 * p + 1) * TT_ROWS + r] = v.y;
         }
-    }
-    named_bar(1, TT_CONS * 32);
-    if (cq == 0) {
+      named_bar_arrive(1, TT_CONS * 32);
+    } else {
+      named_bar(1, TT_CONS * 32);
       const int64_t rows = d->lead_rows[k];
       float* P = reinterpret_cast<float*>(d->Pl[k]);
 #pragma unroll

@@ -147,5 +147,10 @@ __device__ __forceinline__ void ffma2x(uint64_t& acc, uint64_t a, uint64_t b) {
 __device__ __forceinline__ void named_bar(int id, int count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
+// Arrival at named barrier `id` without waiting (the other `count` - arrivals
+// threads wait in named_bar).
+__device__ __forceinline__ void named_bar_arrive(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
 
 }  // namespace cncpd

@@ -29,7 +29,7 @@ struct LipArgs {            // H^(n,k) and L^(n,k) for every block
 
 template <typename T>
 struct PairArgs {           // level 2 of a two-mode group
-  int K, first, ni, pad;
+  int K, first, ni, nsl;     // rows per CTA; slices of the a range (n last in its group)
   int In[CNCPD_KMAX], Io[CNCPD_KMAX], R[CNCPD_KMAX];
   int cta0[CNCPD_KMAX + 1];  // first CTA of each block
   const T* P[CNCPD_KMAX];
@@ -448,8 +448,9 @@ __global__ void __launch_bounds__(256) k_lipschitz(const __grid_constant__ LipAr
 // thread t keeps r = t mod R and strides over (b, r) by a multiple of R; a
 // CTA produces ni rows.  With n last, P[a][i_n][r]:
 //   M[i_n, r] = sum_a P[a, i_n, r] W[a, r];
-// a CTA produces ni*R consecutive outputs, with the a range cut into slices.
-// Partial sums are added in a fixed order.
+// a CTA produces ni*R consecutive outputs (a contiguous run of every P[a]),
+// thread (e, slice) summing output e over the slice's a values; the slices
+// are added in order.
 template <typename T>
 __device__ void pair_body(const PairArgs<T>& a, int b, T* red) {
   int k = 0;
@@ -498,20 +499,22 @@ __device__ void pair_body(const PairArgs<T>& a, int b, T* red) {
       M[(int64_t)(i0 + q) * R + r] = s;
     }
   } else {
-    // ni == 1: R outputs, the a range cut into 256 / R slices; 12 a per batch
-    const int nsl = max(1, 256 / R);
-    const int j = t % R, sl = t / R;
+    // outputs e < ni*R of rows i0 .. i0+ni-1, the a range cut into nsl slices;
+    // 12 a per batch
+    const int OF = a.ni * R, nsl = a.nsl;
+    const int e = t % OF, sl = t / OF;
     T acc = T(0);
-    if (sl < nsl) {
-      const T* Pj = P + (int64_t)i0 * R + j;
+    if (sl < nsl && e < ni * R) {
+      const T* Pe = P + (int64_t)i0 * R + e;
+      const T* We = W + e % R;
       const int64_t ps = (int64_t)In * R;
       for (int x0 = sl; x0 < Io; x0 += 12 * nsl) {
         T pv[12], wv[12];
 #pragma unroll
         for (int q = 0; q < 12; ++q) {
           const int x = min(x0 + q * nsl, Io - 1);  // clamped: every load issues at once
-          pv[q] = Pj[(int64_t)x * ps];
-          wv[q] = W[x * R + j];
+          pv[q] = Pe[(int64_t)x * ps];
+          wv[q] = We[x * R];
         }
 #pragma unroll
         for (int q = 0; q < 12; ++q)
@@ -520,9 +523,9 @@ __device__ void pair_body(const PairArgs<T>& a, int b, T* red) {
     }
     red[t] = acc;
     __syncthreads();
-    if (t < R) {
+    if (t < ni * R) {
       T s = T(0);
-      for (int u = 0; u < nsl; ++u) s += red[u * R + t];
+      for (int u = 0; u < nsl; ++u) s += red[u * OF + t];
       M[(int64_t)i0 * R + t] = s;
     }
   }
@@ -589,7 +592,14 @@ static PairArgs<T> pair_args(const DevDesc& hd, int n, int num_sms, int* ctas) {
     // one or two rows per CTA: two unless that leaves fewer than ~4 CTAs per SM
     ni = ((imax + 1) / 2) * hd.K >= 4LL * num_sms ? 2 : 1;
   } else {
-    ni = 1;  // R outputs per CTA; the a range is cut into 256/R slices
+    // about 24 a values per thread; the rest of the 256 threads take more rows
+    int iomax = 1, rmax = 1;
+    for (int k = 0; k < hd.K; ++k) {
+      iomax = std::max<int>(iomax, (int)hd.dims[k][other]);
+      rmax = std::max(rmax, hd.R[k]);
+    }
+    a.nsl = std::max(1, std::min((iomax + 23) / 24, 256 / rmax));
+    ni = std::max(1, 256 / (rmax * a.nsl));
   }
   a.ni = ni;
   int tot = 0;
