@@ -105,7 +105,12 @@ struct cncpd_ctx {
   // one iteration's pass times are read while the next one runs) and the
   // re-update graph (event set 2)
   cudaGraphExec_t g_main[2] = {nullptr, nullptr}, g_redo = nullptr;
-  int main_runs = 0, redo_runs = 0;
+  // with profile = 1 only every PROFILE_EVERY-th main sweep records events
+  // (event nodes in a graph cost several microseconds each); the others
+  // replay g_plain
+  cudaGraphExec_t g_plain = nullptr;
+  int main_runs = 0, redo_runs = 0, prof_runs = 0, timed_runs = 0;
+  bool rec_on = true;
   cudaEvent_t ev[3][4] = {};
   int ev_set = 0;
   HostMirror* hm = nullptr;      // pinned, mapped; written by the objective kernel
@@ -425,7 +430,9 @@ void destroy_graphs(cncpd_ctx* c) {
   }
   if (c->g_redo) cudaGraphExecDestroy(c->g_redo);
   c->g_redo = nullptr;
-  c->main_runs = c->redo_runs = 0;
+  if (c->g_plain) cudaGraphExecDestroy(c->g_plain);
+  c->g_plain = nullptr;
+  c->main_runs = c->redo_runs = c->prof_runs = c->timed_runs = 0;
 }
 
 // Copy the shared first L_n columns of block 0 into every other block (arena A).
@@ -446,7 +453,7 @@ int propagate_common(cncpd_ctx* c, char* arena) {
 // ----------------------------------------------------------- the sweep -----
 
 int record(cncpd_ctx* c, int which_ev) {
-  if (!c->opts.profile) return CNCPD_OK;
+  if (!c->opts.profile || !c->rec_on) return CNCPD_OK;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   CU(cudaStreamIsCapturing(c->stream, &cs));
   CU(cudaEventRecordWithFlags(c->ev[c->ev_set][which_ev], c->stream,
@@ -616,11 +623,29 @@ int capture(cncpd_ctx* c, int (*fn)(cncpd_ctx*), cudaGraphExec_t* out) {
   return CNCPD_OK;
 }
 
+constexpr int PROFILE_EVERY = 8;
+
 // The first replay of each kind runs eagerly (so that every kernel's
 // attributes are set outside stream capture); later ones replay the graph.
-// Main replays alternate between event sets 0 and 1; returns the set used.
+// Timed main replays (every one without profiling, every PROFILE_EVERY-th
+// with it) alternate between event sets 0 and 1; *set_used is the set, or
+// -1 for a replay that records no events.
 int run_main(cncpd_ctx* c, int* set_used) {
-  const int set = c->main_runs & 1;
+  if (c->opts.profile && c->prof_runs++ % PROFILE_EVERY != 0) {
+    *set_used = -1;
+    c->rec_on = false;
+    int r = CNCPD_OK;
+    if (c->opts.use_graph && c->main_runs++ > 0) {
+      if (!c->g_plain) r = capture(c, enqueue_main, &c->g_plain);
+      if (r == CNCPD_OK && cudaGraphLaunch(c->g_plain, c->stream) != cudaSuccess)
+        r = set_err(CNCPD_ECUDA, "graph launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    } else {
+      r = enqueue_main(c);
+    }
+    c->rec_on = true;
+    return r;
+  }
+  const int set = c->timed_runs++ & 1;
   *set_used = set;
   c->ev_set = set;
   if (c->opts.use_graph && c->main_runs++ > 0) {
@@ -770,11 +795,13 @@ int run_iterations(cncpd_ctx* c, int n_iters, bool use_eps, cncpd_stats* out) {
   int pending = -1;  // event set of a main replay whose pass times are not read yet
   for (int it = 0; it < n_iters; ++it) {
     const unsigned int s0 = c->hm->seq;
-    int set = 0;
+    int set = -1;
     TRY(run_main(c, &set));
-    // the previous iteration's pass times, read while this one runs
-    if (pending >= 0) TRY(read_profile(c, &st, pending));
-    pending = set;
+    // the previous timed iteration's pass times, read while this one runs
+    if (set >= 0) {
+      if (pending >= 0) TRY(read_profile(c, &st, pending));
+      pending = set;
+    }
     TRY(wait_published(c, s0));
     st.x_bytes += pb;
     st.launches += kernels_per_replay(c, 0);

@@ -97,7 +97,9 @@ struct TrailTma {
   static constexpr int WST = (RP + 3) / 4 * 4;
   static constexpr uint32_t X_BYTES = TT_ROWS * 128;
   static constexpr uint32_t W_BYTES = BC * WST * 4;
-  static constexpr uint32_t RED_BYTES = 3 * TT_ROWS * RP * 4;  // partial sums of column quarters 1..3, [quarter][rank][row]
+  // partial sums parked for the owner of each row block: [slot][rank][row], slot = the writer's
+  // quarter among the three that do not own the block
+  static constexpr uint32_t RED_BYTES = 3 * TT_ROWS * RP * 4;
   // as many stages as fit (at most 6): bytes in flight hide the memory latency
   static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 128 - RED_BYTES) / (X_BYTES + W_BYTES));
   static constexpr int STAGES = STAGES_FIT > 6 ? 6 : STAGES_FIT;
@@ -223,9 +225,6 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
     for (int j = 0; j < 4; ++j)
 #pragma unroll
       for (int p = 0; p < RH; ++p) acc[j][p] = 0ull;
-    // quarter 0 is done with the previous tile's partial sums: the other
-    // quarters may write this tile's (barrier 2)
-    if (cq == 0) named_bar_arrive(2, TT_CONS * 32);
     for (int c = 0; c < nch; ++c, ++it) {
       const int s = it % TST;
       const uint32_t ph = (it / TST) & 1;
@@ -266,36 +265,47 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
     }
-    // column quarters 1..3 park their sums and go on with the next tile;
-    // quarter 0 waits for them (barrier 1) and adds them in order
-    if (cq > 0) {
-      named_bar(2, TT_CONS * 32);
+    // Each warp of a row half finishes 32 of its rows: quarter cq owns row
+    // block j = cq and adds the other quarters' partial sums of it (parked in
+    // shared memory) to its own, in quarter order.  Barriers per row half (4
+    // warps): 1 + rq frees the buffer (every warp is done reading the
+    // previous tile), 3 + rq publishes this tile's partial sums.
+    named_bar(1 + rq, 4 * 32);
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
+    for (int j = 0; j < 4; ++j) {
+      if (j == cq) continue;
+      const int r = rq * 128 + 32 * j + lane;
+      const int slot = cq < j ? cq : cq - 1;
 #pragma unroll
-        for (int p = 0; p < RH; ++p) {
-          const float2 v = unpack2(acc[j][p]);
-          const int r = rq * 128 + 32 * j + lane;
-          red[((cq - 1) * RP + 2 * p) * TT_ROWS + r] = v.x;
-          red[((cq - 1) * RP + 2 * p + 1) * TT_ROWS + r] = v.y;
-        }
-      named_bar_arrive(1, TT_CONS * 32);
-    } else {
-      named_bar(1, TT_CONS * 32);
+      for (int p = 0; p < RH; ++p) {
+        const float2 v = unpack2(acc[j][p]);
+        red[(slot * RP + 2 * p) * TT_ROWS + r] = v.x;
+        red[(slot * RP + 2 * p + 1) * TT_ROWS + r] = v.y;
+      }
+    }
+    named_bar(3 + rq, 4 * 32);
+    {
       const int64_t rows = d->lead_rows[k];
       float* P = reinterpret_cast<float*>(d->Pl[k]);
+      const int r = rq * 128 + 32 * cq + lane;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const int r = rq * 128 + 32 * j + lane;
+        if (j != cq) continue;  // j == cq: the owned block, with a compile-time index into acc
         if (row0 + r < rows) {
 #pragma unroll
           for (int p = 0; p < RH; ++p) {
             const float2 v = unpack2(acc[j][p]);
-            float o0 = v.x, o1 = v.y;
+            float o0 = 0.f, o1 = 0.f;
 #pragma unroll
-            for (int q4 = 0; q4 < 3; ++q4) {
-              o0 += red[(q4 * RP + 2 * p) * TT_ROWS + r];
-              o1 += red[(q4 * RP + 2 * p + 1) * TT_ROWS + r];
+            for (int q4 = 0; q4 < 4; ++q4) {
+              if (q4 == cq) {
+                o0 += v.x;
+                o1 += v.y;
+              } else {
+                const int slot = q4 < cq ? q4 : q4 - 1;
+                o0 += red[(slot * RP + 2 * p) * TT_ROWS + r];
+                o1 += red[(slot * RP + 2 * p + 1) * TT_ROWS + r];
+              }
             }
             if (2 * p < R) P[(int64_t)(row0 + r) * R + 2 * p] = o0;
             if (2 * p + 1 < R) P[(int64_t)(row0 + r) * R + 2 * p + 1] = o1;
