@@ -14,4 +14,4 @@ ImportError if it is missing (there is no fallback implementation).
 
 from . import _lib  # noqa: F401
 from ._lib import CncpdError, lib  # noqa: F401
-from .api import CoupledNCP, default_opts, lipschitz  # noqa: F401
+from .api import CoupledCPLoss, CoupledNCP, default_opts, lipschitz  # noqa: F401

@@ -241,3 +241,49 @@ def lipschitz(H):
     out = ctypes.c_double()
     C.check(C.cncpd_lipschitz(H.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), H.shape[0], ctypes.byref(out)))
     return out.value
+
+
+def _autograd_function():
+    torch = _torch()
+    if torch is None:  # pragma: no cover
+        return None
+
+    class CoupledCPLoss(torch.autograd.Function):
+        """F of Eq. costfunc as a differentiable function of the factors.
+
+        ``F = CoupledCPLoss.apply(model, *factors)`` with ``factors`` the
+        K*N tensors U^(n,k) (block-major, I_n x R_k).  The value and the
+        gradient (Eq. solbpgU) are computed by the library at these factors.
+        As in ``set_factors``, the shared first L_n columns come from block
+        0: their gradient is the sum over blocks (App. A) and lands on block
+        0's columns; the other blocks' copies get zero.
+        """
+
+        @staticmethod
+        def forward(ctx, model, *factors):
+            K, N = model.K, model.N
+            U = [[factors[k * N + n].detach().to("cpu", torch.float64).numpy() for n in range(N)]
+                 for k in range(K)]
+            model.set_factors(U)
+            F, gU, gC = model.objective_grad()
+            grads = []
+            for k in range(K):
+                for n in range(N):
+                    g = gU[k][n].copy()
+                    Ln = model.L[n]
+                    if Ln:
+                        g[:, :Ln] = gC[n] if k == 0 else 0.0
+                    f = factors[k * N + n]
+                    grads.append(torch.from_numpy(g).to(f.device, f.dtype))
+            ctx.save_for_backward(*grads)
+            return torch.tensor(F, dtype=factors[0].dtype, device=factors[0].device)
+
+        @staticmethod
+        def backward(ctx, gF):
+            return (None, *[gF * g for g in ctx.saved_tensors])
+
+    return CoupledCPLoss
+
+
+CoupledCPLoss = _autograd_function()
+

@@ -60,6 +60,7 @@ template <typename T>
 struct ObjArgs {            // objective with the last mode just updated
   int K, N, rr, gnc;
   int gr, commit, reduce_last, pad;
+  double inv_K;             // 1 / K
   DevScalars* sc;
   HostMirror* hm;
   double* G;
@@ -1099,6 +1100,7 @@ __global__ void __launch_bounds__(256) k_objective(const __grid_constant__ ObjAr
   __shared__ T red[256];
   __shared__ double cr[RP];
   __shared__ double wsum[2][8];
+  __shared__ float fsum[2][8];
   __shared__ int is_last;
   const int R = a.R[k];
   const int64_t I = a.I[k];
@@ -1106,6 +1108,12 @@ __global__ void __launch_bounds__(256) k_objective(const __grid_constant__ ObjAr
   const T* __restrict__ U = a.U[k];
   const int rr = a.rr;
   double* Gk = a.G + (size_t)k * N * rr;
+  // the scalars thread 0 needs at the end, loaded now
+  double x2 = 0.0, ix2 = 0.0;
+  if (tid == 0) {
+    x2 = a.commit ? sc->xnorm2[k] : sc->xnorm2_orig[k];
+    ix2 = a.commit ? sc->inv_xnorm2[k] : sc->inv_xnorm2_orig[k];
+  }
   // <M, U> per column: an FMA chain in the factor type per thread
   T acc_t = T(0);
   if (r < R && y < Y) {
@@ -1173,8 +1181,8 @@ __global__ void __launch_bounds__(256) k_objective(const __grid_constant__ ObjAr
       lo += ol;
     }
     if ((tid & 31) == 0) {
-      wsum[0][tid >> 5] = (double)hi;
-      wsum[1][tid >> 5] = (double)lo;
+      fsum[0][tid >> 5] = hi;
+      fsum[1][tid >> 5] = lo;
     }
   } else {
     for (int o = 16; o > 0; o >>= 1) xx += __shfl_xor_sync(0xffffffffu, xx, o);
@@ -1185,10 +1193,20 @@ __global__ void __launch_bounds__(256) k_objective(const __grid_constant__ ObjAr
   }
   __syncthreads();
   if (tid == 0) {
-    double t = 0.0;
-    for (int q = 0; q < 8; ++q) t += wsum[0][q] + wsum[1][q];
-    const double x2 = a.commit ? sc->xnorm2[k] : sc->xnorm2_orig[k];
-    const double ix2 = a.commit ? sc->inv_xnorm2[k] : sc->inv_xnorm2_orig[k];
+    double t;
+    if constexpr (sizeof(T) == 4) {
+      // the eight warp sums as one compensated FP32 pair, one conversion
+      float hi = 0.f, lo = 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        ff_add(hi, lo, fsum[0][q]);
+        lo += fsum[1][q];
+      }
+      t = (double)hi + (double)lo;
+    } else {
+      t = 0.0;
+      for (int q = 0; q < 8; ++q) t += wsum[0][q];
+    }
     const double Fk = 0.5 * (x2 + t);
     const double rel = sqrt(fmax(2.0 * Fk, 0.0) * ix2);
     if (a.commit) {
@@ -1203,28 +1221,36 @@ __global__ void __launch_bounds__(256) k_objective(const __grid_constant__ ObjAr
   __syncthreads();
   if (tid == 0) is_last = (atomicAdd(&sc->done_counter[1], 1) == (int)gridDim.x - 1);
   __syncthreads();
-  if (is_last && tid == 0) {
+  if (is_last && tid < 32) {
+    // the blocks' F_k and RelErr_k added by warp 0 (lane q holds blocks q,
+    // q + 32, ...), in a fixed order
     __threadfence();
     double F = 0.0, rel = 0.0;
-    for (int q = 0; q < (int)gridDim.x; ++q) {
+    for (int q = tid; q < (int)gridDim.x; q += 32) {
       F += __ldcg(&sc->Fk[q]);
       rel += __ldcg(&sc->relk[q]);
     }
-    const double relerr = rel / gridDim.x;
-    sc->F = F;
-    sc->relerr = relerr;
-    if (!isfinite(F)) sc->nonfinite = 1;
-    sc->done_counter[1] = 0;
-    if (a.hm) {
-      HostMirror* hm = a.hm;
-      hm->F = F;
-      hm->relerr = relerr;
-      hm->nonfinite = *((volatile int*)&sc->nonfinite);
-      hm->timeout = *((volatile int*)&sc->timeout);
-      const unsigned int q = sc->seq + 1;
-      sc->seq = q;
-      __threadfence_system();
-      hm->seq = q;
+    for (int o = 16; o > 0; o >>= 1) {
+      F += __shfl_xor_sync(0xffffffffu, F, o);
+      rel += __shfl_xor_sync(0xffffffffu, rel, o);
+    }
+    if (tid == 0) {
+      const double relerr = rel * a.inv_K;
+      sc->F = F;
+      sc->relerr = relerr;
+      if (!isfinite(F)) sc->nonfinite = 1;
+      sc->done_counter[1] = 0;
+      if (a.hm) {
+        HostMirror* hm = a.hm;
+        hm->F = F;
+        hm->relerr = relerr;
+        hm->nonfinite = *((volatile int*)&sc->nonfinite);
+        hm->timeout = *((volatile int*)&sc->timeout);
+        const unsigned int q = sc->seq + 1;
+        sc->seq = q;
+        __threadfence_system();
+        hm->seq = q;
+      }
     }
   }
 }
@@ -1238,6 +1264,7 @@ static cudaError_t objective_impl(const LaunchCfg& c, const DevDesc& hd, int com
   a.rr = hd.Rmax * hd.Rmax;
   a.commit = commit;
   a.reduce_last = (reduce_last && hd.Gp[n]) ? 1 : 0;
+  a.inv_K = 1.0 / hd.K;
   a.sc = hd.sc;
   a.hm = commit ? hd.hm : nullptr;
   a.G = hd.Gbase;

@@ -281,6 +281,32 @@ def test_gradient_matches_oracle():
     m.close()
 
 
+def test_autograd_loss_matches_oracle_gradient():
+    """CoupledCPLoss: F and torch.autograd gradients equal the oracle's
+    objective and gradient; the shared columns' gradient (the sum over
+    blocks) lands on block 0's copy."""
+    torch = pytest.importorskip("torch")
+    dims = [(12, 10, 8)] * 2
+    L = [2, 1, 0]
+    Xs, _, U0 = coupled_inputs(dims, 3, L, seed=9)
+    P = _P()
+    m = P.CoupledNCP(Xs, 3, L)
+    fac = [torch.tensor(U0[k][n], dtype=torch.float64, requires_grad=True) for k in range(2) for n in range(3)]
+    F = P.CoupledCPLoss.apply(m, *fac)
+    grads = torch.autograd.grad(F, fac)
+    prob = O.Problem(Xs, [3, 3], L)
+    Uc = O.couple_initial(prob, U0)
+    lam = [np.ones(3)] * 2
+    assert float(F.detach()) == pytest.approx(prob.objective_fn(Uc, lam), rel=1e-10)
+    for k in range(2):
+        for n in range(3):
+            want = O.gradient(prob, Uc, lam, k, n).copy()
+            if L[n]:
+                want[:, :L[n]] = sum(O.gradient(prob, Uc, lam, kk, n)[:, :L[n]] for kk in range(2)) if k == 0 else 0.0
+            assert rel_fro(grads[k * 3 + n].numpy(), want) <= 1e-10
+    m.close()
+
+
 def test_checkpoint_resume_is_bitwise():
     dims = [(14, 11, 9)] * 3
     Xs, _, U0 = coupled_inputs(dims, 4, [2, 0, 0], seed=8)
