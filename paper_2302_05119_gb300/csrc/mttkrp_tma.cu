@@ -78,15 +78,20 @@ __device__ __forceinline__ float4 load4(const unsigned char* p, __nv_bfloat16) {
 // ---------------------------------------------------------------------------
 // Trailing contraction Pl[row, r] = sum_col X[row, col] W_t[col, r].
 // Tile = 256 rows; stage = 256 rows x 128 bytes (32 FP32 or 64 BF16 columns,
-// 32 KiB, 128-byte swizzle).  Consumer warp w owns rows 128 (w % 2) + 32 j +
-// lane (j = 0..3) of the tile and the (w / 2)-th quarter of the stage's
-// columns (two 16-byte chunks), so each Khatri-Rao value read from shared
-// memory feeds four rows; the four column quarters are added at the end of
-// the tile.  Two consumer warps per scheduler hide the shared-memory latency
-// of one another.
+// 32 KiB, 128-byte swizzle).  Consumer warp w owns rows 32 w .. 32 w + 31 of
+// the tile; lane (i, cq) = (lane mod 8, lane / 8) takes rows 32 w + i + 8 t
+// (t = 0..3) and the cq-th quarter of the stage's columns, so each
+// Khatri-Rao value read from shared memory feeds four rows, and the four
+// quarters of a row meet in one warp: the tile's sums are two butterfly
+// shuffles, with no barrier across warps.  A warp's 32 rows are 32 R
+// consecutive floats of Pl: they go out through the warp's own staging rows
+// in shared memory as coalesced stores (scattered 4-byte stores of the rows
+// cost about 9 us of the 256^3 pass).  The Khatri-Rao rows of a stage are
+// stored with 16 bytes of padding per column quarter, so the four quarters'
+// rows read by a warp fall in distinct banks.
 // ---------------------------------------------------------------------------
 constexpr int TT_ROWS = 256;
-constexpr int TT_CONS = 8;  // 2 row halves x 4 column quarters
+constexpr int TT_CONS = 8;  // 32 rows each
 constexpr size_t SMEM_LIMIT = 232448;  // 227 KiB of dynamic shared memory per CTA
 constexpr int NKR = 3;  // Khatri-Rao warps, stage i handled by warp i mod NKR
 
@@ -96,14 +101,15 @@ struct TrailTma {
   static constexpr int CPC = XChunk<XT>::N;         // columns per 16-byte chunk
   static constexpr int WST = (RP + 3) / 4 * 4;
   static constexpr uint32_t X_BYTES = TT_ROWS * 128;
-  static constexpr uint32_t W_BYTES = BC * WST * 4;
-  // partial sums parked for the owner of each row block: [slot][rank][row], slot = the writer's
-  // quarter among the three that do not own the block
-  static constexpr uint32_t RED_BYTES = 3 * TT_ROWS * RP * 4;
+  static constexpr int QC = BC / 4;                  // columns per quarter
+  static constexpr uint32_t W_BYTES = BC * WST * 4 + 4 * 16;  // + 16 bytes of padding per quarter
   // as many stages as fit (at most 6): bytes in flight hide the memory latency
-  static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 128 - RED_BYTES) / (X_BYTES + W_BYTES));
+  static constexpr uint32_t OUT_BYTES = TT_CONS * 32 * (RP + 1) * 4;  // output staging, 32 rows per warp
+  static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 128 - OUT_BYTES) / (X_BYTES + W_BYTES));
   static constexpr int STAGES = STAGES_FIT > 6 ? 6 : STAGES_FIT;
-  static constexpr size_t SMEM = 1024 + STAGES * (size_t)(X_BYTES + W_BYTES) + RED_BYTES + 2 * STAGES * 8;
+  static constexpr size_t SMEM = 1024 + STAGES * (size_t)(X_BYTES + W_BYTES) + OUT_BYTES + 2 * STAGES * 8;
+  // float offset of the Khatri-Rao row of column jj within a stage
+  static __device__ __forceinline__ int wrow(int jj) { return jj * WST + (jj / QC) * 4; }
   // A Khatri-Rao warp takes every NKR-th stage; with more warps than stages it
   // could reach a slot two phases ahead of its consumers, which a parity wait
   // cannot tell from the phase it wants.
@@ -118,8 +124,8 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
   extern __shared__ unsigned char smem_raw[];
   unsigned char* xs = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   float* ws = reinterpret_cast<float*>(xs + TST * S::X_BYTES);
-  float* red = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(ws) + TST * S::W_BYTES);
-  uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(red) + S::RED_BYTES);
+  float* ostg = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(ws) + TST * S::W_BYTES);
+  uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(ostg) + S::OUT_BYTES);
   uint64_t* empty = full + TST;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int* err = &d->sc->timeout;
@@ -197,7 +203,7 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
                 if (r < R) w[r] *= __ldg(U + r);
             }
           }
-          float4* wrow = reinterpret_cast<float4*>(ws + s * (S::W_BYTES / 4) + jj * S::WST);
+          float4* wrow = reinterpret_cast<float4*>(ws + s * (S::W_BYTES / 4) + S::wrow(jj));
 #pragma unroll
           for (int q = 0; q < S::WST / 4; ++q) wrow[q] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
         }
@@ -210,7 +216,7 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
 
   // -------------------------------------------------------------- consumers
   uint32_t it = 0;
-  const int rq = warp & 1, cq = warp >> 1;  // row half (128 rows, 4 per lane), column quarter (8 columns)
+  const int li = lane & 7, cq = lane >> 3;  // row offset, column quarter
   constexpr int RH = RP / 2;
   for (int jn = us.first; jn < us.end; jn += us.step) {
     const int g = us.unit(jn);
@@ -220,11 +226,11 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
     const int J = (int)d->trail_cols[k];
     const int R = d->R[k];
     const int nch = (J + TT_BC - 1) / TT_BC;
-    uint64_t acc[4][RH];  // [row j][pair of ranks]
+    uint64_t acc[4][RH];  // [row t][pair of ranks]
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int t = 0; t < 4; ++t)
 #pragma unroll
-      for (int p = 0; p < RH; ++p) acc[j][p] = 0ull;
+      for (int p = 0; p < RH; ++p) acc[t][p] = 0ull;
     for (int c = 0; c < nch; ++c, ++it) {
       const int s = it % TST;
       const uint32_t ph = (it / TST) & 1;
@@ -235,84 +241,67 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
       for (int q = 2 * cq; q < 2 * cq + 2; ++q) {
         float xv[4][S::CPC];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          // 128-byte swizzle: 16-byte chunk q of row r sits at chunk q ^ (r & 7)
-          const int r = rq * 128 + 32 * j + lane;
-          widen(*reinterpret_cast<const uint4*>(xt + r * 128 + ((q ^ (r & 7)) << 4)), xv[j], XT());
+        for (int t = 0; t < 4; ++t) {
+          // 128-byte swizzle: 16-byte chunk q of row r sits at chunk q ^ (r & 7), and r & 7 = li
+          const int r = 32 * warp + li + 8 * t;
+          widen(*reinterpret_cast<const uint4*>(xt + r * 128 + ((q ^ li) << 4)), xv[t], XT());
         }
 #pragma unroll
         for (int e = 0; e < S::CPC; ++e) {
-          const uint64_t* wr = reinterpret_cast<const uint64_t*>(wt + (S::CPC * q + e) * S::WST);
+          const uint64_t* wr = reinterpret_cast<const uint64_t*>(wt + S::wrow(S::CPC * q + e));
           uint64_t x2[4];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) x2[j] = pack2(xv[j][e], xv[j][e]);
+          for (int t = 0; t < 4; ++t) x2[t] = pack2(xv[t][e], xv[t][e]);
 #pragma unroll
           for (int p = 0; p + 2 <= RH; p += 2) {
             const ulonglong2 w = *reinterpret_cast<const ulonglong2*>(wr + p);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              ffma2x(acc[j][p], x2[j], w.x);
-              ffma2x(acc[j][p + 1], x2[j], w.y);
+            for (int t = 0; t < 4; ++t) {
+              ffma2x(acc[t][p], x2[t], w.x);
+              ffma2x(acc[t][p + 1], x2[t], w.y);
             }
           }
           if constexpr (RH % 2 == 1) {
             const uint64_t w = wr[RH - 1];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) ffma2x(acc[j][RH - 1], x2[j], w);
+            for (int t = 0; t < 4; ++t) ffma2x(acc[t][RH - 1], x2[t], w);
           }
         }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
     }
-    // Each warp of a row half finishes 32 of its rows: quarter cq owns row
-    // block j = cq and adds the other quarters' partial sums of it (parked in
-    // shared memory) to its own, in quarter order.  Barriers per row half (4
-    // warps): 1 + rq frees the buffer (every warp is done reading the
-    // previous tile), 3 + rq publishes this tile's partial sums.
-    named_bar(1 + rq, 4 * 32);
+    // the four quarters of each row, by butterfly over lanes li, li + 8, li + 16,
+    // li + 24 (every lane ends with the same sums); lane (li, cq) stages row
+    // li + 8 cq of the warp, then the warp's rows go out as one run of Pl
+    float* stg = ostg + warp * 32 * (RP + 1);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (j == cq) continue;
-      const int r = rq * 128 + 32 * j + lane;
-      const int slot = cq < j ? cq : cq - 1;
+    for (int t = 0; t < 4; ++t) {
 #pragma unroll
       for (int p = 0; p < RH; ++p) {
-        const float2 v = unpack2(acc[j][p]);
-        red[(slot * RP + 2 * p) * TT_ROWS + r] = v.x;
-        red[(slot * RP + 2 * p + 1) * TT_ROWS + r] = v.y;
-      }
-    }
-    named_bar(3 + rq, 4 * 32);
-    {
-      const int64_t rows = d->lead_rows[k];
-      float* P = reinterpret_cast<float*>(d->Pl[k]);
-      const int r = rq * 128 + 32 * cq + lane;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (j != cq) continue;  // j == cq: the owned block, with a compile-time index into acc
-        if (row0 + r < rows) {
-#pragma unroll
-          for (int p = 0; p < RH; ++p) {
-            const float2 v = unpack2(acc[j][p]);
-            float o0 = 0.f, o1 = 0.f;
-#pragma unroll
-            for (int q4 = 0; q4 < 4; ++q4) {
-              if (q4 == cq) {
-                o0 += v.x;
-                o1 += v.y;
-              } else {
-                const int slot = q4 < cq ? q4 : q4 - 1;
-                o0 += red[(slot * RP + 2 * p) * TT_ROWS + r];
-                o1 += red[(slot * RP + 2 * p + 1) * TT_ROWS + r];
-              }
-            }
-            if (2 * p < R) P[(int64_t)(row0 + r) * R + 2 * p] = o0;
-            if (2 * p + 1 < R) P[(int64_t)(row0 + r) * R + 2 * p + 1] = o1;
-          }
+        float2 v = unpack2(acc[t][p]);
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, 8);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, 8);
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, 16);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, 16);
+        if (t == cq) {
+          stg[(li + 8 * t) * (RP + 1) + 2 * p] = v.x;
+          stg[(li + 8 * t) * (RP + 1) + 2 * p + 1] = v.y;
         }
       }
     }
+    __syncwarp();
+    const int64_t wrow0 = (int64_t)row0 + 32 * warp;
+    const int64_t rows = d->lead_rows[k];
+    const int nrow = rows - wrow0 < 32 ? (int)(rows - wrow0) : 32;
+    const int ne = nrow > 0 ? nrow * R : 0;
+    float* dst = reinterpret_cast<float*>(d->Pl[k]) + wrow0 * R;
+    if (R == RP) {
+      for (int e = lane; e < ne; e += 32) dst[e] = stg[(e / RP) * (RP + 1) + e % RP];
+    } else {
+      for (int e = lane; e < ne; e += 32) dst[e] = stg[(e / R) * (RP + 1) + e % R];
+    }
+    __syncwarp();
   }
 }
 
