@@ -515,6 +515,10 @@ bool begin_in_sweep(const cncpd_ctx* c) { return !c->lra && !c->opts.use_core; }
 // update of that mode sums its split-K partials itself.
 bool fused_last_reduce(const cncpd_ctx* c) { return !c->lra && c->N - c->h == 1; }
 
+// The update of the last mode also evaluates and publishes the objective
+// (tensor-pass path, block-parallel update with room for the rows of M).
+bool fused_objective(const cncpd_ctx* c) { return !c->lra && update_fuses_objective(c->hd, c->fp64, c->RP); }
+
 // Launch H / L of mode n (with the Gram of mode n-1) on the side stream so
 // that it runs concurrently with the tensor pass enqueued next on the main
 // stream; the main stream joins before the update of mode n.
@@ -562,14 +566,17 @@ int enqueue_sweep(cncpd_ctx* c, int use_w, int begin) {
       TRY(enqueue_mode_m(c, n));
       CU(launch_lipschitz(lc, c->dd, c->hd, c->fp64, n, core, n - 1, beg));  // also the Gram of mode n-1
     }
-    CU(launch_update(lc, c->dd, c->hd, c->fp64, c->RP, n, use_w, dw, core, (fuse_reduce && n == c->N - 1) ? 1 : 0));
+    const int last = n == c->N - 1;
+    CU(launch_update(lc, c->dd, c->hd, c->fp64, c->RP, n, use_w, dw, core, (fuse_reduce && last) ? 1 : 0,
+                     (last && fused_objective(c)) ? 1 : 0));
     if (c->lra) CU(launch_cross_gram(lc, c->dd, c->hd, c->fp64, n, n + 1));
   }
   if (c->lra) {
     CU(launch_gram(lc, c->dd, c->hd, c->fp64, c->N - 1, c->N, 0));
     CU(launch_lra_objective(lc, c->dd, c->hd, c->fp64, core));
+  } else if (!fused_objective(c)) {
+    CU(launch_objective(lc, c->dd, c->hd, c->fp64, c->RP, 1, 1));
   }
-  else CU(launch_objective(lc, c->dd, c->hd, c->fp64, c->RP, 1, 1));
   return CNCPD_OK;
 }
 
@@ -770,7 +777,7 @@ long long kernels_per_replay(cncpd_ctx* c, int redo) {
       if (gsize > 2 || (gsize == 2 && forked)) n += 1;   // level 2 in its own launch
     }
   }
-  n += c->lra ? 3 : 1;                                    // (last Gram: chunks + sums) + objective
+  n += c->lra ? 3 : (fused_objective(c) ? 0 : 1);         // (last Gram: chunks + sums) + objective
   return n;
 }
 
@@ -1119,6 +1126,8 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
     d.gnc[n] = (int)((imax + d.gr[n] - 1) / d.gr[n]);
     CTRY(dalloc(c, &d.Gp[n], (size_t)K * d.gnc[n] * rr * c->fsz));
   }
+  // per-CTA <M, U_new> sums of the objective fused into the last update
+  CTRY(dalloc(c, &d.dotp, (size_t)d.gnc[N - 1] * K * c->RP * c->fsz));
   for (int k = 0; k < K; ++k)
     for (int n = 0; n < N; ++n) {
       d.U1[k][n] = c->U1p(k, n);

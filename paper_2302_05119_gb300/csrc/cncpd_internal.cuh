@@ -142,6 +142,9 @@ struct DevDesc {
   // tcgen05 passes (BF16 storage, N = 3): the split factors that are the B
   // operands (3 NP rows, row pitch bt_pitch / bl_pitch elements) and their
   // TMA descriptors; tmap_lead3 views X^(k) as (J, I1, I0) in boxes of 64 x 64 x 1
+  // objective fused into the last mode's update: per-CTA sums of <M, U_new>,
+  // [chunk CTA][block][RP] in the factor type (null: separate objective kernel)
+  void* dotp;
   int use_umma, umma_np;
   void* Bt[CNCPD_KMAX];
   void* Bl[CNCPD_KMAX];
@@ -227,14 +230,19 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
 // Sum of the first nch chunk values of entry p (stride rr), in chunk order
 // (compensated FP32 for FP32 factors, FP64 otherwise); the loads of up to 32
 // chunks are issued before any of them is added.
-template <typename T>
+// CG = true reads through L2 only (values other CTAs of the same kernel wrote).
+template <typename T, bool CG = false>
 __device__ __forceinline__ double gram_sum(const T* __restrict__ gp, int nch, int rr, int p) {
+  auto ld = [](const T* q) -> T {
+    if constexpr (CG) return __ldcg(q);
+    else return *q;
+  };
   if constexpr (sizeof(T) == 4) {
     float hi = 0.f, lo = 0.f;
     for (int c0 = 0; c0 < nch; c0 += 32) {
       float x[32];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) x[j] = gp[(size_t)min(c0 + j, nch - 1) * rr + p];  // clamped: no predicate
+      for (int j = 0; j < 32; ++j) x[j] = ld(gp + (size_t)min(c0 + j, nch - 1) * rr + p);  // clamped: no predicate
 #pragma unroll
       for (int j = 0; j < 32; ++j)
         if (c0 + j < nch) ff_add(hi, lo, x[j]);
@@ -245,7 +253,7 @@ __device__ __forceinline__ double gram_sum(const T* __restrict__ gp, int nch, in
     for (int c0 = 0; c0 < nch; c0 += 32) {
       double x[32];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) x[j] = gp[(size_t)min(c0 + j, nch - 1) * rr + p];
+      for (int j = 0; j < 32; ++j) x[j] = ld(gp + (size_t)min(c0 + j, nch - 1) * rr + p);
 #pragma unroll
       for (int j = 0; j < 32; ++j)
         if (c0 + j < nch) s += x[j];
@@ -312,8 +320,12 @@ cudaError_t launch_lipschitz(const LaunchCfg& c, const DevDesc* d_desc, const De
                              int prev, int begin = 0);
 // msplit = 1: M of mode n (the last mode, a one-mode trailing group) is summed
 // here from the lead contraction's split-K partials (and stored).
+// with_objective = 1 (the last mode of a sweep, update_fuses_objective true):
+// the update also evaluates and publishes the objective, as launch_objective
+// with commit = 1 and reduce_last = 1 would.
 cudaError_t launch_update(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int RP, int n,
-                          int use_w, double delta_w, int use_core, int msplit);
+                          int use_w, double delta_w, int use_core, int msplit, int with_objective = 0);
+bool update_fuses_objective(const DevDesc& h_desc, int fp64, int RP);
 // commit = 1: write F/relerr/core term of the solver state; 0: only out_relk against xnorm2_orig.
 // reduce_last = 1: the Gram of the last mode is first summed from the chunk values the update left.
 cudaError_t launch_objective(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int RP, int commit,

@@ -54,6 +54,14 @@ struct UpdArgs {            // fused APG update of mode n
   const T* H[CNCPD_KMAX];
   const T* part[CNCPD_KMAX];  // non-null: M is summed from these split-K partials
   int nsplit[CNCPD_KMAX];
+  // obj = 1: the objective is fused into this (last-mode) update; every CTA
+  // leaves its <M, U_new> sums in dotp[cta][k][RP], the last CTA to finish
+  // evaluates F and publishes it
+  int obj, N;
+  double inv_K;
+  T* dotp;
+  double* G;
+  HostMirror* hm;
 };
 
 template <typename T>
@@ -877,6 +885,94 @@ __global__ void __launch_bounds__(128) k_update(const __grid_constant__ UpdArgs<
   }
 }
 
+// Objective of Eq. costfunc at the end of the last mode's update, by the last
+// CTA to finish (the other CTAs' Gram chunk values of mode n and <M, U_new>
+// sums are read through L2).  Full warps take the blocks; per block the
+// lanes sum the Gram of mode n from its chunks (stored as G^(n,k)), the
+// lambda^T (*_m G^(m)) lambda terms and lambda^T c with c the column sums of
+// <M, U_new> (the next core term); warp 0 then adds the blocks up in order.
+template <typename T, int RP>
+__device__ void update_objective_tail(const UpdArgs<T>& a, int tid, int NT) {
+  const int K = a.K, N = a.N, n = a.n, rr = a.rr;
+  DevScalars* sc = a.sc;
+  const int warp = tid >> 5, lane = tid & 31, nw = NT >> 5;
+  const int wpb = nw / K;  // whole warps per block (at least 2: checked on the host)
+  __shared__ double pxx[32], pip[32];
+  if (warp < K * wpb) {
+    const int kk = warp / wpb, gl = (warp % wpb) * 32 + lane, G = wpb * 32;
+    const int Rk = a.R[kk];
+    const int nch = (int)((a.I[kk] + a.gr - 1) / a.gr);
+    double* Gk = a.G + (size_t)kk * N * rr;
+    const T* gp = a.Gp + (size_t)kk * a.gnc * rr;
+    double xx = 0.0;
+    for (int p = gl; p < Rk * Rk; p += G) {
+      const double g = gram_sum<T, true>(gp, nch, rr, p);
+      Gk[(size_t)n * rr + p] = g;
+      double t = sc->lam1[kk][p / Rk] * sc->lam1[kk][p % Rk] * g;
+      for (int m = 0; m < N; ++m)
+        if (m != n) t *= Gk[(size_t)m * rr + p];
+      xx += t;
+    }
+    double ip = 0.0;
+    for (int cc = gl; cc < Rk; cc += G) {
+      const double cr = gram_sum<T, true>(a.dotp + (size_t)kk * RP, (int)gridDim.x, K * RP, cc);
+      sc->cterm[kk][cc] = cr;
+      ip += sc->lam1[kk][cc] * cr;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      xx += __shfl_xor_sync(0xffffffffu, xx, o);
+      ip += __shfl_xor_sync(0xffffffffu, ip, o);
+    }
+    if (lane == 0) {
+      pxx[warp] = xx;
+      pip[warp] = ip;
+    }
+  }
+  __syncthreads();
+  if (tid < K) {
+    // the block's warp sums in order
+    double xx = 0.0, ip = 0.0;
+    for (int q = 0; q < wpb; ++q) {
+      xx += pxx[tid * wpb + q];
+      ip += pip[tid * wpb + q];
+    }
+    const double Fk = 0.5 * (sc->xnorm2[tid] + xx - 2.0 * ip);
+    sc->Fk[tid] = Fk;
+    sc->relk[tid] = sqrt(fmax(2.0 * Fk, 0.0) * sc->inv_xnorm2[tid]);
+  }
+  __threadfence_block();
+  __syncthreads();
+  if (tid < 32) {
+    double F = 0.0, rel = 0.0;
+    for (int q = tid; q < K; q += 32) {
+      F += sc->Fk[q];
+      rel += sc->relk[q];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      F += __shfl_xor_sync(0xffffffffu, F, o);
+      rel += __shfl_xor_sync(0xffffffffu, rel, o);
+    }
+    if (tid == 0) {
+      const double relerr = rel * a.inv_K;
+      sc->F = F;
+      sc->relerr = relerr;
+      if (!isfinite(F)) sc->nonfinite = 1;
+      sc->done_counter[1] = 0;
+      if (a.hm) {
+        HostMirror* hm = a.hm;
+        hm->F = F;
+        hm->relerr = relerr;
+        hm->nonfinite = *((volatile int*)&sc->nonfinite);
+        hm->timeout = *((volatile int*)&sc->timeout);
+        const unsigned int q = sc->seq + 1;
+        sc->seq = q;
+        __threadfence_system();
+        hm->seq = q;
+      }
+    }
+  }
+}
+
 // The same update with one thread per (column c, block k, row y): the loads
 // of a pass are issued together, the shared-column gradient sum is formed in
 // shared memory in block order, and the CTA's new rows stay in shared memory
@@ -892,9 +988,11 @@ __global__ void __launch_bounds__(512) k_update_kp(const __grid_constant__ UpdAr
   T* uh = Hs + (size_t)K * RP * RP;           // [TY][K][RP]
   T* gC = uh + (size_t)TY * K * RP;           // [TY][K][RP]
   T* nvs = gC + (size_t)TY * K * RP;          // [K][gr][RP]
+  T* mvs = nvs + (size_t)K * a.gr * RP;        // [K][gr][RP], with the fused objective
   __shared__ T wsh[CNCPD_KMAX + 1];
   __shared__ T Lsh[CNCPD_KMAX];
   __shared__ T LCsh;
+  __shared__ int is_last;
   DevScalars* sc = a.sc;
   const int64_t row0 = (int64_t)blockIdx.x * a.gr;
   const int R = a.R[k];
@@ -945,6 +1043,7 @@ __global__ void __launch_bounds__(512) k_update_kp(const __grid_constant__ UpdAr
     } else {
       mv = valid ? a.M[k][off] : T(0);
     }
+    if (a.obj && inchunk) mvs[((size_t)k * a.gr + p0 + y) * RP + c] = mv;
     __syncthreads();  // weights and H staged; the previous pass is done with uh / gC
     const T w = (c < Ln) ? wsh[K] : wsh[k];
     const T uhat = u1 + w * (u1 - u2);
@@ -1006,11 +1105,63 @@ __global__ void __launch_bounds__(512) k_update_kp(const __grid_constant__ UpdAr
       a.Gp[((size_t)kk * a.gnc + blockIdx.x) * a.rr + ra * Rk + rb] = gv;
     }
   }
+  if (!a.obj) return;
+  // <M, U_new> over this CTA's rows per (block, column): thread (c, k, y)
+  // takes rows y, y + TY, ..., then the TY sums are added in order
+  T ds = T(0);
+  for (int p = y; p < a.gr; p += TY) {
+    if (row0 + p < I && c < R)
+      ds = fma(mvs[((size_t)k * a.gr + p) * RP + c], nvs[((size_t)k * a.gr + p) * RP + c], ds);
+  }
+  gC[((size_t)y * K + k) * RP + c] = ds;  // gC is free: the update loop is done with it
+  __syncthreads();
+  if (y == 0) {
+    T s;
+    if constexpr (sizeof(T) == 4) {
+      float hi = 0.f, lo = 0.f;
+      for (int yy = 0; yy < TY; ++yy) ff_add(hi, lo, gC[((size_t)yy * K + k) * RP + c]);
+      s = hi + lo;
+    } else {
+      s = T(0);
+      for (int yy = 0; yy < TY; ++yy) s += gC[((size_t)yy * K + k) * RP + c];
+    }
+    a.dotp[((size_t)blockIdx.x * K + k) * RP + c] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) is_last = (atomicAdd(&sc->done_counter[1], 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  update_objective_tail<T, RP>(a, tid, NT);
+}
+
+// Shared memory of the block-parallel update with the fused objective (the
+// rows of M staged next to the new rows), 0 when the objective stays a
+// kernel of its own (no chunk buffers, no scratch, not the block-parallel
+// kernel, or not enough shared memory).
+template <typename T>
+static size_t fused_objective_smem(const DevDesc& hd, int RP) {
+  const int n = hd.N - 1;
+  if (!hd.dotp || !hd.Gp[n]) return 0;
+  int64_t imax = 0;
+  for (int k = 0; k < hd.K; ++k) imax = std::max<int64_t>(imax, hd.dims[k][n]);
+  const UpdGeom geo = update_geometry(RP, hd.K, imax, sizeof(T));
+  if (!geo.kp) return 0;
+  // the last CTA evaluates the objective with at least two whole warps per
+  // block; with fewer the separate objective kernel (one CTA per block) is faster
+  if ((RP * hd.K * geo.ty) / 32 < 2 * hd.K) return 0;
+  const size_t smem = geo.smem + (size_t)hd.K * geo.gr * RP * sizeof(T);
+  return smem <= 200 * 1024 ? smem : 0;
+}
+
+bool update_fuses_objective(const DevDesc& hd, int fp64, int RP) {
+  return fp64 ? fused_objective_smem<double>(hd, RP) > 0 : fused_objective_smem<float>(hd, RP) > 0;
 }
 
 template <typename T, int RP>
 static cudaError_t update_impl(const LaunchCfg& c, const DevDesc& hd, int n, int use_w, double delta_w,
-                               int use_core, int msplit) {
+                               int use_core, int msplit, int with_objective) {
   UpdArgs<T> a{};
   a.K = hd.K;
   a.n = n;
@@ -1044,12 +1195,23 @@ static cudaError_t update_impl(const LaunchCfg& c, const DevDesc& hd, int n, int
     }
   }
   const unsigned grid = (unsigned)((imax + a.gr - 1) / a.gr);
+  size_t smem = geo.smem;
+  if (with_objective) {
+    smem = fused_objective_smem<T>(hd, RP);
+    if (n != hd.N - 1 || smem == 0 || (unsigned)hd.gnc[n] < grid) return cudaErrorInvalidValue;
+    a.obj = 1;
+    a.N = hd.N;
+    a.inv_K = 1.0 / hd.K;
+    a.dotp = reinterpret_cast<T*>(hd.dotp);
+    a.G = hd.Gbase;
+    a.hm = hd.hm;
+  }
   if (geo.kp) {
     a.stage_rows = 1;
-    cudaError_t e = allow_smem(k_update_kp<T, RP>, geo.smem);
+    cudaError_t e = allow_smem(k_update_kp<T, RP>, smem);
     if (e != cudaSuccess) return e;
     carve<k_update_kp<T, RP>>();
-    k_update_kp<T, RP><<<grid, dim3(RP, hd.K, geo.ty), geo.smem, c.stream>>>(a);
+    k_update_kp<T, RP><<<grid, dim3(RP, hd.K, geo.ty), smem, c.stream>>>(a);
     return cudaGetLastError();
   }
   size_t dyn = 0;
@@ -1066,12 +1228,12 @@ static cudaError_t update_impl(const LaunchCfg& c, const DevDesc& hd, int n, int
 }
 
 cudaError_t launch_update(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int RP, int n,
-                          int use_w, double delta_w, int use_core, int msplit) {
+                          int use_w, double delta_w, int use_core, int msplit, int with_objective) {
   (void)dd;
-#define UCASE(V)                                                                  \
-  case V:                                                                         \
-    return fp64 ? update_impl<double, V>(c, hd, n, use_w, delta_w, use_core, msplit)      \
-                : update_impl<float, V>(c, hd, n, use_w, delta_w, use_core, msplit);
+#define UCASE(V)                                                                                   \
+  case V:                                                                                          \
+    return fp64 ? update_impl<double, V>(c, hd, n, use_w, delta_w, use_core, msplit, with_objective) \
+                : update_impl<float, V>(c, hd, n, use_w, delta_w, use_core, msplit, with_objective);
   switch (RP) { CNCPD_FOR_EACH_RP(UCASE) }
 #undef UCASE
   return cudaErrorInvalidValue;
