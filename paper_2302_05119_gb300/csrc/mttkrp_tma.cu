@@ -105,8 +105,10 @@ struct TrailTma {
   static constexpr uint32_t W_BYTES = BC * WST * 4 + 4 * 16;  // + 16 bytes of padding per quarter
   // as many stages as fit (at most 6): bytes in flight hide the memory latency
   static constexpr uint32_t OUT_BYTES = TT_CONS * 32 * (RP + 1) * 4;  // output staging, 32 rows per warp
+  // at most 5 stages: on the 256^3 workload 4, 5 and 6 stages took 64.9, 62.6
+  // and 64.6 us (a deeper ring only adds to the queues in front of DRAM)
   static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 128 - OUT_BYTES) / (X_BYTES + W_BYTES));
-  static constexpr int STAGES = STAGES_FIT > 6 ? 6 : STAGES_FIT;
+  static constexpr int STAGES = STAGES_FIT > 5 ? 5 : STAGES_FIT;
   static constexpr size_t SMEM = 1024 + STAGES * (size_t)(X_BYTES + W_BYTES) + OUT_BYTES + 2 * STAGES * 8;
   // float offset of the Khatri-Rao row of column jj within a stage
   static __device__ __forceinline__ int wrow(int jj) { return jj * WST + (jj / QC) * 4; }
