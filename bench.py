@@ -14,8 +14,10 @@ L2, so no flush is needed between iterations.  --lra runs the low-rank
 approximation step of lraCoNCPD-APG (rank R~ of the workload) before the
 timed iterations, which then use the collapsed products.  --time-to-fit
 measures, from the host tensors, the wall time until the global fit is within
-1e-4 of the converged FP64 fit, for plain FP32 storage and for the mixed form
-(BF16 storage, plus the LRA step when the workload has an R~).
+1e-4 of the converged FP64 fit, for plain FP32 storage, for BF16 storage
+(tensor-core passes for third-order tensors) and, when the workload has an
+R~, for BF16 storage with the LRA step.  The roofline's pass times are CUDA
+events around each tensor pass of every 8th iteration of the timed region.
 """
 
 import argparse
