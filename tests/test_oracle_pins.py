@@ -477,3 +477,236 @@ def test_planted_core_term_mistake_is_caught(monkeypatch):
     monkeypatch.setattr(O, "kr_all", lambda U: O.khatri_rao(list(U)))
     with pytest.raises(AssertionError):
         test_kruskal_and_core_term_match_brute_force()
+
+
+# ------------------------- extrapolated coupled sweep (golden, w > 0) -----
+
+def _golden_sweep(root):
+    import json
+    with open(os.path.join(root, "tests", "golden", "coupled_sweep.json")) as f:
+        return json.load(f)
+
+
+def _check_coupled_sweep(root, case_name):
+    """One sweep with w_hat = 0.6 > 0 against the 50-digit elementwise
+    computation in tests/golden/coupled_sweep.json (written by
+    make_coupled_sweep.py from Eqs. eqextraPU, eqextrawu, solUnsI, solUnC and,
+    with the core, eqextraPG / solD; reading R3 for the shared weight)."""
+    g = _golden_sweep(root)
+    case = g["cases"][case_name]
+    K, N = g["K"], len(g["dims"])
+    Xs = [np.array(X) for X in g["X"]]
+    prob = O.Problem(Xs, [g["R"]] * K, g["L"])
+    st = O.State([[np.array(A) for A in Uk] for Uk in g["U1"]], [[np.array(A) for A in Uk] for Uk in g["U2"]],
+                 [np.array(l) for l in g["lam1"]], [np.array(l) for l in g["lam2"]])
+    Lp = {}
+    for n in range(N):
+        for k in range(K):
+            Lp[("u", n, k)] = case["Lprev"]["u"][n][k]
+        if case["Lprev"]["c"][n] is not None:
+            Lp[("c", n)] = case["Lprev"]["c"][n]
+    if case["use_core"]:
+        for k in range(K):
+            Lp[("d", k)] = case["Lprev"]["d"][k]
+    new, Lnew = O.sweep(prob, st, g["w_hat"], Lp, case["use_core"], g["delta_w"])
+    ex = case["expect"]
+    tr = ex["trace"]
+    for n in range(N):
+        for k in range(K):
+            want = np.array(ex["U1"][k][n], dtype=np.float64)
+            err = np.max(np.abs(new.U1[k][n] - want)) / np.max(np.abs(want))
+            assert err <= 1e-13, (case_name, n, k, err)
+            np.testing.assert_array_equal(new.U2[k][n], st.U1[k][n])
+            assert Lnew[("u", n, k)] == pytest.approx(float(tr[f"L_{n}_{k}"]), rel=1e-13)
+        assert Lnew[("c", n)] == pytest.approx(float(tr[f"LC_{n}"]), rel=1e-13)
+    if case["use_core"]:
+        for k in range(K):
+            np.testing.assert_allclose(new.lam1[k], np.array(ex["lam1"][k], dtype=np.float64), rtol=1e-13)
+            assert Lnew[("d", k)] == pytest.approx(float(tr[f"Ld_{k}"]), rel=1e-13)
+
+
+@pytest.mark.parametrize("case_name", ["plain", "core"])
+def test_extrapolated_coupled_sweep_matches_golden(root, case_name):
+    _check_coupled_sweep(root, case_name)
+
+
+def _planted(fn, old, new):
+    """A copy of oracle function ``fn`` with one source fragment replaced."""
+    import inspect
+    import textwrap
+    src = textwrap.dedent(inspect.getsource(fn))
+    assert src.count(old) == 1, old
+    ns = dict(vars(O))
+    exec(compile(src.replace(old, new), "<planted mistake>", "exec"), ns)
+    return ns[fn.__name__]
+
+
+@pytest.mark.parametrize("case_name,old,new", [
+    # extrapolation sign of the individual columns (Eq. eqextraPU)
+    ("plain", "U1n[k] + w[k] * (U1n[k] - U2n[k])", "U1n[k] - w[k] * (U1n[k] - U2n[k])"),
+    # extrapolation sign of the shared columns
+    ("plain", "UhatC = UC1 + wC * (UC1 - UC2)", "UhatC = UC1 - wC * (UC1 - UC2)"),
+    # one block's weight in place of the shared weight w_C (reading R3)
+    ("plain", "UhatC = UC1 + wC * (UC1 - UC2)", "UhatC = UC1 + w[0] * (UC1 - UC2)"),
+    # w_C from one block's L history instead of the block sums
+    ("plain", 'Lprev.get(("c", n))', 'Lprev.get(("u", n, 0))'),
+    # one block's step instead of 1 / sum_k L (Eq. solUnC)
+    ("plain", "newC = project(UhatC - GC / LC", "newC = project(UhatC - GC / Lu[0]"),
+    # no momentum: the previous iterate read as the current one
+    ("plain", "U2n = [st.U2[k][n] for k in range(K)]", "U2n = [st.U1[k][n] for k in range(K)]"),
+    # the shared gradient from block 0 alone instead of the block sum
+    ("plain", "GC = sum(Ghat[k][:, :Ln] for k in range(K))", "GC = Ghat[0][:, :Ln]"),
+    # core extrapolation sign (Eq. eqextraPG)
+    ("core", "st.lam1[k] + w * (st.lam1[k] - st.lam2[k])", "st.lam1[k] - w * (st.lam1[k] - st.lam2[k])"),
+    # the core's weight from the factor history
+    ("core", 'Lprev.get(("d", k))', 'Lprev.get(("u", 0, k))'),
+])
+def test_planted_sweep_mistakes_are_caught(root, monkeypatch, case_name, old, new):
+    monkeypatch.setattr(O, "sweep", _planted(O.sweep, old, new))
+    with pytest.raises(AssertionError):
+        _check_coupled_sweep(root, case_name)
+
+
+# ------------------------------------------------------ RelErr and Fit -----
+
+def _relerr_case():
+    """Two 2x2x2 blocks with rank-1 all-ones models (X_hat = 1 everywhere):
+    block 0 is all ones but one entry 4 (residual 3, ||X||^2 = 7 + 16 = 23);
+    block 1 is all twos (residual norm sqrt(8), ||X|| = sqrt(32))."""
+    X0 = np.ones((2, 2, 2))
+    X0[1, 0, 1] = 4.0
+    X1 = 2.0 * np.ones((2, 2, 2))
+    U = [np.ones((2, 1)) for _ in range(3)]
+    return [X0, X1], [U, U], [np.ones(1), np.ones(1)]
+
+
+def test_relerr_and_fit_hand_values():
+    """RelErr = mean_k ||X - X_hat|| / ||X|| (Section III-C) and Fit = 1 -
+    RelErr (Section IV) on hand-computed values: 3 / sqrt(23) and 1/2."""
+    Xs, Us, lams = _relerr_case()
+    per = O.block_relerrs(Xs, Us, lams)
+    assert per[0] == pytest.approx(3.0 / math.sqrt(23.0), rel=1e-15)
+    assert per[1] == pytest.approx(0.5, rel=1e-15)
+    rel = (3.0 / math.sqrt(23.0) + 0.5) / 2.0
+    assert O.relerr(Xs, Us, lams) == pytest.approx(rel, rel=1e-15)
+    assert O.fit(Xs, Us, lams) == pytest.approx(1.0 - rel, rel=1e-15)
+
+
+@pytest.mark.parametrize("fn,old,new", [
+    ("block_relerrs", "np.linalg.norm(X - kruskal(lam, U)) / np.linalg.norm(X)",
+     "np.linalg.norm(X - kruskal(lam, U)) ** 2 / np.linalg.norm(X) ** 2"),
+    ("block_relerrs", "np.linalg.norm(X - kruskal(lam, U)) / np.linalg.norm(X)",
+     "np.linalg.norm(X - kruskal(lam, U))"),
+    ("relerr", "np.mean(block_relerrs(Xs, Us, lams))", "np.sum(block_relerrs(Xs, Us, lams))"),
+])
+def test_planted_relerr_mistakes_are_caught(monkeypatch, fn, old, new):
+    monkeypatch.setattr(O, fn, _planted(getattr(O, fn), old, new))
+    with pytest.raises(AssertionError):
+        test_relerr_and_fit_hand_values()
+
+
+# ------------------------------------------- termination and safeguard -----
+
+def _stopping_case():
+    Xs, _, U0, L = _coupled_problem(seed=11, K=2, noise=0.1)
+    return O.Problem(Xs, [3, 3], L), U0
+
+
+def test_stops_on_first_small_relerr_change():
+    """Section III-C: the iteration stops at the first k with
+    |RelErr_k - RelErr_{k-1}| < eps, and not before.  The change sequence is
+    taken from an eps = 0 run; eps is placed between the first change that
+    drops below all earlier ones (past iteration 15) and the smallest earlier
+    change."""
+    prob, U0 = _stopping_case()
+    full = O.apg(prob, U0, max_it=80, eps=0.0)
+    rel = full["hist"]["relerr"]
+    d = [abs(rel[i] - rel[i - 1]) for i in range(1, len(rel))]
+    stop = next(i for i in range(15, len(d)) if d[i] < min(d[:i]))
+    eps = 0.5 * (d[stop] + min(d[:stop]))
+    res = O.apg(prob, U0, max_it=80, eps=eps)
+    assert res["iters"] == stop + 1
+    assert res["hist"]["relerr"] == rel[:stop + 2]
+
+
+def test_planted_stopping_mistake_is_caught(monkeypatch):
+    """Comparing against the initial RelErr instead of the previous one."""
+    monkeypatch.setattr(O, "apg", _planted(O.apg, "        rel_prev = rel\n", "        pass\n"))
+    with pytest.raises(AssertionError):
+        test_stops_on_first_small_relerr_change()
+
+
+def test_momentum_sequence_in_apg(root):
+    """The weights hat w the solver passes to its sweeps follow Appendix A
+    (reading R1): 0, then (t_1 - 1)/t_2, (t_2 - 1)/t_3."""
+    sympy = pytest.importorskip("sympy")
+    table = {}
+    with open(os.path.join(root, "tests", "golden", "momentum_closed_form.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                name, expr = line.split(None, 1)
+                table[name] = float(sympy.N(sympy.sympify(expr), 30))
+    prob, U0 = _stopping_case()
+    seen = []
+    O.apg(prob, U0, max_it=3, eps=0.0, reupdate=False, callback=lambda it, st, info: seen.append(info["w_hat"]))
+    assert seen[0] == 0.0
+    assert seen[1] == pytest.approx(table["w2"], rel=1e-14)
+    assert seen[2] == pytest.approx(table["w3"], rel=1e-14)
+
+
+def test_planted_momentum_mistake_is_caught(root, monkeypatch):
+    monkeypatch.setattr(O, "apg", _planted(O.apg, "w_hat = (t - 1.0) / t_new", "w_hat = (t_new - 1.0) / t_new"))
+    with pytest.raises(AssertionError):
+        test_momentum_sequence_in_apg(root)
+
+
+def test_safeguard_accepts_no_increase():
+    """Algorithm 1's safeguard with reading R8: every accepted iterate has
+    F(k) <= F(k-1) (1 + 1e-13) unless it came from the w = 0 redo, and the
+    redo fired on this problem."""
+    Xs, _, U0, L = _coupled_problem(seed=5, K=3, noise=0.2)
+    prob = O.Problem(Xs, [3] * 3, L)
+    res = O.apg(prob, U0, max_it=300, eps=0.0)
+    F, redo = res["hist"]["F"], res["hist"]["redo"]
+    assert any(redo)
+    for i, r in enumerate(redo):
+        if not r:
+            assert F[i + 1] <= F[i] + O.TIE_TOL * abs(F[i]), i
+    # the redo fires exactly where the plain (no safeguard) iteration first
+    # raises F, and not before: up to there both runs are the same
+    off = O.apg(prob, U0, max_it=300, eps=0.0, reupdate=False)["hist"]["F"]
+    first = next(i for i in range(1, len(off)) if off[i] - off[i - 1] > O.TIE_TOL * abs(off[i - 1]))
+    assert not any(redo[:first - 1])
+    assert redo[first - 1]
+    assert F[:first] == off[:first]
+
+
+def test_planted_safeguard_mistake_is_caught(monkeypatch):
+    monkeypatch.setattr(O, "apg", _planted(O.apg, "(F - F_prev) > TIE_TOL", "(F_prev - F) > TIE_TOL"))
+    with pytest.raises(AssertionError):
+        test_safeguard_accepts_no_increase()
+
+
+# ------------------------------------------------------- problem set-up -----
+
+def test_couple_initial_takes_shared_columns_from_block_zero():
+    """Eq. tensormodel: U_C^(n,1) = ... = U_C^(n,K); the oracle takes them
+    from block 0 and leaves every individual column as given."""
+    rng = np.random.default_rng(3)
+    dims, L = (4, 3, 5), [2, 1, 0]
+    U0 = [[rng.random((d, 3)) for d in dims] for _ in range(3)]
+    prob = O.Problem([np.zeros(dims)] * 3, [3] * 3, L)
+    U = O.couple_initial(prob, U0)
+    for k in range(3):
+        for n in range(3):
+            np.testing.assert_array_equal(U[k][n][:, :L[n]], U0[0][n][:, :L[n]])
+            np.testing.assert_array_equal(U[k][n][:, L[n]:], U0[k][n][:, L[n]:])
+
+
+def test_problem_rejects_invalid_coupling():
+    """L_n <= min_k R_k (Section II-C) and coupled modes of equal size."""
+    with pytest.raises(AssertionError):
+        O.Problem([np.zeros((3, 3, 3))] * 2, [2, 3], [3, 0, 0])
+    with pytest.raises(AssertionError):
+        O.Problem([np.zeros((3, 3, 3)), np.zeros((4, 3, 3))], [2, 2], [1, 0, 0])
+    O.Problem([np.zeros((3, 3, 3)), np.zeros((4, 3, 3))], [2, 2], [0, 1, 0])
