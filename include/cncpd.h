@@ -207,6 +207,21 @@ int cncpd_load_state(cncpd_t h, const void *blob, size_t nbytes);
 void cncpd_free_blob(void *blob);
 
 /*
+ * Failure-detection self-test (Section III-A's algorithm has no counterpart;
+ * this checks the library's own guard against a stalled pipeline).  Every
+ * wait of the tensor passes on an mbarrier is bounded in time; one that runs
+ * out sets the handle's device error word and the call that launched it
+ * returns CNCPD_ETIMEOUT.  This call runs a one-CTA kernel on the handle's
+ * stream whose single wait expects an arrival that never comes, with no
+ * copy or MMA in flight, and a limit of limit_ms (0.001 .. 2000 ms).
+ * Returns CNCPD_ETIMEOUT (the expected result) after clearing the error
+ * word; the iteration history is discarded as after any timeout, so the
+ * next cncpd_step starts Algorithm 1 afresh from the current factors.  The
+ * handle stays usable.  CNCPD_EINVAL for a limit out of range.
+ */
+int cncpd_check_wait_timeout(cncpd_t h, double limit_ms);
+
+/*
  * Allocation-free MTTKRP for callers that must not let this library call
  * cudaMalloc (their device memory is owned by another allocator or a fixed
  * arena, they run under a strict memory budget, or an allocation's implicit
@@ -217,6 +232,7 @@ void cncpd_free_blob(void *blob);
  * last-mode MTTKRP X_(3) (U1 (.) U0) of one third-order FP32 tensor, on
  * `stream` (NULL: legacy default stream), without synchronising it.
  *  X   device, C order I0 x I1 x I2;  U0: device, I0 x R;  U1: device, I1 x R
+ *      (this entry point alone does not accept host memory)
  *  M   device output, I2 x R (row-major);  1 <= R <= 64
  * Scratch: a fixed 8 MiB device array inside the library (2^21 floats),
  * held on every GPU that loads the library until the process exits.
@@ -224,8 +240,13 @@ void cncpd_free_blob(void *blob);
  * needs to start at zero.  All calls share that array, so calls that overlap
  * on the GPU (different streams, or different host threads on one device)
  * race and give wrong results; serialise them.  The first call on each
- * device looks up the array's device address (cudaGetSymbolAddress), so make
- * it before any stream capture.  Calls no allocating routine.
+ * device looks up the array's device address (cudaGetSymbolAddress); under
+ * CUDA's lazy module loading that first lookup is also when the library's
+ * device code is loaded and the 8 MiB are reserved on that device.  So make
+ * one eager warm-up call per device (any valid small problem) before stream
+ * capture or latency-sensitive work.  Calls no allocating routine.  X, U0,
+ * U1 and M must be device (or managed) memory of the current device:
+ * anything else is refused with CNCPD_EINVAL before a kernel is launched.
  */
 int cncpd_mttkrp_last_mode_noalloc(const float *X, int64_t I0, int64_t I1,
                                    int64_t I2, const float *U0,

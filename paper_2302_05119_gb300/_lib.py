@@ -70,6 +70,7 @@ SIGNATURES = {
     "cncpd_free_blob": (None, [_P]),
     "cncpd_mttkrp_last_mode_noalloc": (_I, [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _P, _P,
                                             _I, _P, _P]),
+    "cncpd_check_wait_timeout": (_I, [_P, _D]),
     "cncpd_destroy": (None, [_P]),
     "cncpd_last_error": (ctypes.c_char_p, []),
 }

@@ -220,6 +220,12 @@ class CoupledNCP:
                                        C.CNCPD_F64 if dtype == np.float64 else C.CNCPD_F32))
         return F.value, gU, gC
 
+    def check_wait_timeout(self, limit_ms=1.0):
+        """Run the bounded-wait self-test (cncpd_check_wait_timeout); returns
+        the library's status code (CNCPD_ETIMEOUT = -5 is the expected one)."""
+        code = C.cncpd_check_wait_timeout(self._h, float(limit_ms))
+        return code, C.lib().cncpd_last_error().decode()
+
     def save_state(self):
         p = ctypes.c_void_p()
         n = ctypes.c_size_t()

@@ -1380,6 +1380,19 @@ int cncpd_lipschitz(const double* H, int R, double* lmax) {
   return CNCPD_OK;
 }
 
+int cncpd_check_wait_timeout(cncpd_t h, double limit_ms) {
+  g_err.clear();
+  TRY(check_handle(h));
+  if (!(limit_ms >= 0.001 && limit_ms <= 2000.0)) return set_err(CNCPD_EINVAL, "limit_ms must be in [0.001, 2000]");
+  cncpd_ctx* c = h;
+  TRY(sync(c));
+  CU(launch_wait_selftest(c->stream, &c->sc->timeout, (uint64_t)(limit_ms * 1e6)));
+  TRY(enqueue_readback(c));
+  TRY(sync(c));
+  if (c->hs->timeout) return timeout_error(c);
+  return set_err(CNCPD_ECUDA, "the self-test wait completed although nothing arrived on its barrier");
+}
+
 // ------------------------------------------------------------- LRA -------
 
 int cncpd_lra(cncpd_t h, const int* R_tilde, const void* const* Ut0, cncpd_dtype dtype, cncpd_stats* out) {

@@ -301,6 +301,9 @@ cudaError_t launch_reduce_splits(const LaunchCfg& c, const DevDesc& h_desc, int 
 cudaError_t launch_trailing_tma(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int RP, int st);
 cudaError_t launch_lead_tma(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int RP, int st);
 int lead_tma_rows(int st);
+// One-CTA kernel whose bounded mbarrier wait gets no arrival and gives up
+// after limit_ns, setting *err (the failure-detection self-test).
+cudaError_t launch_wait_selftest(cudaStream_t s, int* err, uint64_t limit_ns);
 // tcgen05 passes for BF16 third-order tensors (ranks up to 32)
 int umma_np(int Rmax);
 cudaError_t launch_split_factor(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int which);

@@ -590,4 +590,24 @@ cudaError_t launch_lead_tma(const LaunchCfg& c, const DevDesc* dd, const DevDesc
   return cudaErrorInvalidValue;
 }
 
+// Self-test of the bounded-wait path: one thread waits on the phase-0
+// completion of an mbarrier that expects one arrival and never gets it, with
+// no copy or MMA in flight, so the wait runs out after `limit_ns` and sets
+// the error word exactly as a stalled pipeline would.
+__global__ void k_wait_selftest(int* err, uint64_t limit_ns) {
+  __shared__ alignas(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait(smem_u32(&bar), 0, err, limit_ns);
+  __syncthreads();
+}
+
+cudaError_t launch_wait_selftest(cudaStream_t s, int* err, uint64_t limit_ns) {
+  k_wait_selftest<<<1, 32, 0, s>>>(err, limit_ns);
+  return cudaGetLastError();
+}
+
 }  // namespace cncpd

@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdio>
 #include <mutex>
 
 #include "../../include/cncpd.h"
@@ -39,11 +40,13 @@ int fail(int code, const char* msg) { return cncpd::set_error(code, msg); }
 // of split s of X[row, j] * U0[i0(row), r] * U1[i1(row), r], row = i0*I1 + i1.
 // Thread (tx, ty): column j = blockIdx.x * 64 + tx, every second row of the
 // split (ty = 0, 1); the two row halves are added through shared memory.
+// RMAXL is the rank bucket (16, 32 or 64): the accumulators are indexed by
+// compile-time constants only, so they stay in registers.
+template <int RMAXL>
 __global__ void __launch_bounds__(128) k_lead_noalloc(const float* __restrict__ X, int64_t I0, int64_t I1,
                                                       int64_t J, const float* __restrict__ U0,
                                                       const float* __restrict__ U1, int R, int64_t split_rows,
                                                       float* __restrict__ partial) {
-  constexpr int RMAXL = 64;
   __shared__ float w[64][RMAXL];
   __shared__ float red[64][RMAXL];
   const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
@@ -52,6 +55,7 @@ __global__ void __launch_bounds__(128) k_lead_noalloc(const float* __restrict__ 
   const int64_t rb = (int64_t)blockIdx.y * split_rows;
   const int64_t re = rb + split_rows < rows ? rb + split_rows : rows;
   float acc[RMAXL];
+#pragma unroll
   for (int r = 0; r < RMAXL; ++r) acc[r] = 0.f;
   for (int64_t r0 = rb; r0 < re; r0 += 64) {
     __syncthreads();
@@ -65,15 +69,23 @@ __global__ void __launch_bounds__(128) k_lead_noalloc(const float* __restrict__ 
     if (j < J)
       for (int i = ty; i < nrow; i += 2) {
         const float x = X[(r0 + i) * J + j];
-        for (int r = 0; r < R; ++r) acc[r] = fmaf(x, w[i][r], acc[r]);
+#pragma unroll
+        for (int r = 0; r < RMAXL; ++r)
+          if (r < R) acc[r] = fmaf(x, w[i][r], acc[r]);
       }
   }
   __syncthreads();
-  if (ty == 1)
-    for (int r = 0; r < R; ++r) red[tx][r] = acc[r];
+  if (ty == 1) {
+#pragma unroll
+    for (int r = 0; r < RMAXL; ++r)
+      if (r < R) red[tx][r] = acc[r];
+  }
   __syncthreads();
-  if (ty == 0 && j < J)
-    for (int r = 0; r < R; ++r) partial[((int64_t)blockIdx.y * J + j) * R + r] = acc[r] + red[tx][r];
+  if (ty == 0 && j < J) {
+#pragma unroll
+    for (int r = 0; r < RMAXL; ++r)
+      if (r < R) partial[((int64_t)blockIdx.y * J + j) * R + r] = acc[r] + red[tx][r];
+  }
 }
 
 // M[j, r] = sum_s partial[s][j][r], splits added in order.
@@ -101,6 +113,32 @@ int scratch_for_current_device(float** out) {
   return CNCPD_OK;
 }
 
+// Every array of this entry point must be device (or managed) memory of the
+// current device: unlike the handle-based calls it copies nothing, so a host
+// pointer is refused here instead of faulting in the kernel.
+// cudaPointerGetAttributes allocates nothing.
+int check_device_pointer(const void* p, int dev, const char* name) {
+  cudaPointerAttributes a{};
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(CNCPD_EINVAL, "pointer attributes not available");
+  }
+  const bool ok = (a.type == cudaMemoryTypeDevice && a.device == dev) || a.type == cudaMemoryTypeManaged;
+  if (!ok) {
+    static thread_local char msg[128];
+    snprintf(msg, sizeof msg, "%s must be device or managed memory of the current device", name);
+    return fail(CNCPD_EINVAL, msg);
+  }
+  return CNCPD_OK;
+}
+
+template <int RB>
+void launch_lead_noalloc(dim3 grid, cudaStream_t s, const float* X, int64_t I0, int64_t I1, int64_t J,
+                         const float* U0, const float* U1, int R, int64_t split_rows, float* partial) {
+  k_lead_noalloc<RB><<<grid, 128, 0, s>>>(X, I0, I1, J, U0, U1, R, split_rows, partial);
+}
+
 }  // namespace
 
 extern "C" int cncpd_mttkrp_last_mode_noalloc(const float* X, int64_t I0, int64_t I1, int64_t I2, const float* U0,
@@ -110,8 +148,16 @@ extern "C" int cncpd_mttkrp_last_mode_noalloc(const float* X, int64_t I0, int64_
   const int64_t per_split = I2 * R;
   if (per_split > kScratchFloats)
     return fail(CNCPD_EINVAL, "I2 * R exceeds the fixed scratch of 2097152 floats (8 MiB)");
+  int dev = 0;
+  cudaError_t de = cudaGetDevice(&dev);
+  if (de != cudaSuccess) return fail(CNCPD_ECUDA, cudaGetErrorString(de));
+  int rc = check_device_pointer(X, dev, "X");
+  if (rc == CNCPD_OK) rc = check_device_pointer(U0, dev, "U0");
+  if (rc == CNCPD_OK) rc = check_device_pointer(U1, dev, "U1");
+  if (rc == CNCPD_OK) rc = check_device_pointer(M, dev, "M");
+  if (rc != CNCPD_OK) return rc;
   float* scratch = nullptr;
-  int rc = scratch_for_current_device(&scratch);
+  rc = scratch_for_current_device(&scratch);
   if (rc != CNCPD_OK) return rc;
   const int64_t rows = I0 * I1;
   // about 600 CTAs in total, at least 64 rows each, within the scratch
@@ -125,8 +171,10 @@ extern "C" int cncpd_mttkrp_last_mode_noalloc(const float* X, int64_t I0, int64_
   const int64_t nsplit = (rows + split_rows - 1) / split_rows;
   if (nsplit > 65535) return fail(CNCPD_EINVAL, "tensor too large for the split grid");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  k_lead_noalloc<<<dim3((unsigned)ctiles, (unsigned)nsplit), 128, 0, s>>>(X, I0, I1, I2, U0, U1, R, split_rows,
-                                                                        scratch);
+  const dim3 grid((unsigned)ctiles, (unsigned)nsplit);
+  if (R <= 16) launch_lead_noalloc<16>(grid, s, X, I0, I1, I2, U0, U1, R, split_rows, scratch);
+  else if (R <= 32) launch_lead_noalloc<32>(grid, s, X, I0, I1, I2, U0, U1, R, split_rows, scratch);
+  else launch_lead_noalloc<64>(grid, s, X, I0, I1, I2, U0, U1, R, split_rows, scratch);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) {
     int grid = (int)((per_split + 255) / 256);

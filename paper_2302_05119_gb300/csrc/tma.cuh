@@ -48,15 +48,17 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
   return t;
 }
 
-// Wait for the phase of `parity` to complete, for at most ~2 s of wall time.
-// On timeout the error word is set and false is returned (the caller then
-// stops issuing work and drains its copies in flight).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
+// Wait for the phase of `parity` to complete, for at most `limit_ns` of wall
+// time (~2 s by default).  On timeout the error word is set and false is
+// returned (the caller then stops issuing work and drains its copies in
+// flight); a wait also gives up at once when another wait set the word.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err,
+                                          uint64_t limit_ns = 2000000000ull) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_timer_ns();
   for (uint32_t n = 1;; ++n) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((n & 31) == 0 && (global_timer_ns() - t0 > 2000000000ull || *((volatile int*)err) != 0)) {
+    if ((n & 31) == 0 && (global_timer_ns() - t0 > limit_ns || *((volatile int*)err) != 0)) {
       atomicExch(err, 1);
       return false;
     }

@@ -22,8 +22,8 @@ def _rng(seed, purpose, *extra):
 class Workload:
     """One synthetic coupled-tensor problem.
 
-    dims: per-block tensor sizes (K tuples of N ints), R: rank, L: coupled
-    columns per mode, snr_db: noise level, dist: factor distribution
+    dims: per-block tensor sizes (K tuples of N ints), R: rank (one int, or
+    K ints for per-block ranks), L: coupled columns per mode, snr_db: noise level, dist: factor distribution
     ("uniform" or "gamma"), sparse_mode: mode whose ground-truth columns are
     sparse (fraction ``density`` nonzero) or None, iters: iteration count
     the workload is run for, R_lra: LRA rank (0: no LRA step).
@@ -52,6 +52,10 @@ class Workload:
     def elements(self):
         return [int(np.prod(d)) for d in self.dims]
 
+    def ranks(self):
+        """Per-block ranks R_k."""
+        return [int(r) for r in self.R] if np.ndim(self.R) else [int(self.R)] * self.K
+
 
 def _eeg_dims(seed, K):
     rng = _rng(seed, "sizes")
@@ -60,10 +64,38 @@ def _eeg_dims(seed, K):
     return [(64, 71, int(a), int(b)) for a, b in zip(i3, i4)]
 
 
+def _ongoing_ranks(seed, K):
+    return [int(r) for r in _rng(seed, "sizes", 1).integers(33, 45, size=K)]
+
+
+# Coupling patterns of the simulation design (Section IV-A, Table III) at
+# R = 10: L = [10,10,10], [5,5,5] (all modes coupled), [10,10,0], [5,5,0]
+# (two), [10,0,0], [5,0,0] (one).
+E1_PATTERNS = {"e1a_l10": [10, 10, 10], "e1a_l5": [5, 5, 5], "e1b_l10": [10, 10, 0],
+               "e1b_l5": [5, 5, 0], "e1c_l10": [10, 0, 0], "e1c_l5": [5, 0, 0]}
+
+
 def workload(name):
     """The named synthetic workloads (shapes and distributions of the paper's
     simulation, face-image and EEG experiments; seeds fixed)."""
     base = 20230210
+    if name.startswith("e1") and name.split("_s")[0] in E1_PATTERNS:
+        # simulation design: S = 20 blocks of 100^3, R = 10, 20 dB; "_s<K>"
+        # takes the first K blocks only (the same data as the full design)
+        pat = name.split("_s")[0]
+        K = int(name.split("_s")[1]) if "_s" in name else 20
+        return Workload(name, [(100, 100, 100)] * K, 10, list(E1_PATTERNS[pat]), 20.0,
+                        base + 10 + sorted(E1_PATTERNS).index(pat), iters=1000)
+    if name == "erp_42x9x71x60":
+        # ERP shape (Section IV-C): 42 blocks of 9 channels x 71 frequency
+        # bins x 60 time points, R = 36, every column shared in every mode
+        # (the blocks differ only by their cores)
+        return Workload(name, [(9, 71, 60)] * 42, 36, [36, 36, 36], 15.0, base + 6, iters=200)
+    if name == "eeg_ongoing_14x46x510x64":
+        # ongoing-EEG shape (Section IV-D): 14 blocks of 46 x 510 x 64,
+        # per-block ranks in [33, 44], L = [26, 26, 0]
+        return Workload(name, [(46, 510, 64)] * 14, _ongoing_ranks(base + 7, 14), [26, 26, 0], 15.0,
+                        base + 7, iters=200)
     if name == "small_40cube":
         return Workload(name, [(40, 40, 40)] * 3, 5, [2, 0, 0], 20.0, base + 1, iters=200)
     if name == "sim_256cube":
@@ -80,7 +112,7 @@ def workload(name):
 
 
 WORKLOADS = ["small_40cube", "sim_256cube", "bf16_512x512x256", "eeg_uneven_4th",
-             "face_lra_1000x1000x400"]
+             "face_lra_1000x1000x400", "erp_42x9x71x60", "eeg_ongoing_14x46x510x64"] + sorted(E1_PATTERNS)
 
 
 def _draw(rng, shape, dist):
@@ -92,9 +124,11 @@ def _draw(rng, shape, dist):
 
 
 def ground_truth(dims, R, L, seed, dist="uniform", sparse_mode=None, density=1.0):
-    """Ground-truth factors A[k][n] (I_n x R): the first L[n] columns of mode
-    n are drawn once and shared by every block; the rest per block."""
+    """Ground-truth factors A[k][n] (I_n x R_k): the first L[n] columns of
+    mode n are drawn once and shared by every block; the rest per block.
+    R is one rank or K per-block ranks."""
     K, N = len(dims), len(dims[0])
+    Rs = [int(r) for r in R] if np.ndim(R) else [int(R)] * K
     common = []
     for n in range(N):
         if L[n] > 0:
@@ -106,13 +140,13 @@ def ground_truth(dims, R, L, seed, dist="uniform", sparse_mode=None, density=1.0
         Ak = []
         for n in range(N):
             I = dims[k][n]
-            M = _draw(_rng(seed, "indiv", k, n), (I, R), dist)
+            M = _draw(_rng(seed, "indiv", k, n), (I, Rs[k]), dist)
             if L[n] > 0:
                 M[:, :L[n]] = common[n]
             if sparse_mode is not None and n == sparse_mode and density < 1.0:
-                keep = np.zeros((I, R), dtype=bool)
+                keep = np.zeros((I, Rs[k]), dtype=bool)
                 nnz = max(1, int(round(density * I)))
-                for r in range(R):
+                for r in range(Rs[k]):
                     src = ("support", 0, r) if r < L[n] else ("support", k + 1, r)
                     rows = _rng(seed, *src).choice(I, size=nnz, replace=False)
                     keep[rows, r] = True
@@ -145,15 +179,22 @@ def make_tensors(w, dtype=np.float64, blocks=None):
     return Xs, A
 
 
+def _ranks(R, K):
+    return [int(r) for r in R] if np.ndim(R) else [int(R)] * K
+
+
 def init_factors(dims, R, seed, tag=0):
-    """Initial factors U0[k][n] ~ Uniform[0, 1] (Section IV settings)."""
-    return [[_rng(seed, "init", tag, k, n).random((d[n], R)) for n in range(len(d))]
+    """Initial factors U0[k][n] ~ Uniform[0, 1] (Section IV settings); R is
+    one rank or per-block ranks."""
+    Rs = _ranks(R, len(dims))
+    return [[_rng(seed, "init", tag, k, n).random((d[n], Rs[k])) for n in range(len(d))]
             for k, d in enumerate(dims)]
 
 
 def init_cores(K, R, seed, tag=0):
     """Initial super-diagonal cores lambda^(k) ~ Uniform[0, 1]."""
-    return [_rng(seed, "core", tag, k).random(R) for k in range(K)]
+    Rs = _ranks(R, K)
+    return [_rng(seed, "core", tag, k).random(Rs[k]) for k in range(K)]
 
 
 def init_lra_factors(dims, R_lra, seed, tag=0):

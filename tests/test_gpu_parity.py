@@ -354,13 +354,15 @@ def test_host_and_device_inputs_agree():
 
 # ------------------------------------------------------------------ LRA ---
 
-@pytest.mark.parametrize("dt,tol,Rt,storage", [(np.float64, 1e-8, 4, None), (np.float64, 1e-8, 3, None),
-                                               (np.float32, 2e-4, 3, None), (np.float32, 2e-4, 3, "bf16")])
+@pytest.mark.parametrize("dt,tol,Rt,storage", [(np.float64, 1e-9, 4, None), (np.float64, 1e-9, 3, None),
+                                               (np.float32, 1e-5, 3, None), (np.float32, 1e-5, 3, "bf16")])
 def test_lra_path_matches_oracle(dt, tol, Rt, storage):
     """lraCoNCPD-APG: ALS low-rank approximation of each block, then the
-    collapsed APG iterations, against the oracle's Algorithm 2.  FP32 is
-    checked at R~ = R (the paper's setting): with R~ above the data's rank
-    ALS is ill-conditioned and amplifies FP32 rounding-order differences."""
+    collapsed APG iterations, against the oracle's Algorithm 2, at the
+    method's tolerances (FP64 1e-9, FP32 1e-5 relative Frobenius): the ALS
+    factors and every APG factor over 10 iterations.  FP32 runs at R~ = R,
+    the paper's setting, on data of rank R with 20 dB noise; FP64 also at
+    R~ above the data's rank."""
     dims = [(14, 12, 10)] * 3
     Xs, _, U0 = coupled_inputs(dims, 3, [2, 0, 0], seed=12)
     Xs = [X.astype(dt) for X in Xs]
@@ -383,15 +385,22 @@ def test_lra_path_matches_oracle(dt, tol, Rt, storage):
     m.set_factors(U0)
     st = m.lra(Rt, Ut0)
     assert st["lra_sweeps"] == max(sweeps)
+    worst_u = worst_x = worst = 0.0
     for k in range(3):
         for n in range(3):
-            assert rel_fro(m.lra_factor(k, n), Uts[k][n]) <= tol * 10
+            worst_u = max(worst_u, rel_fro(m.lra_factor(k, n), Uts[k][n]))
+            assert rel_fro(m.lra_factor(k, n), Uts[k][n]) <= tol
+        worst_x = max(worst_x, rel_fro(O.kruskal(np.ones(Rt), [m.lra_factor(k, n) for n in range(3)]),
+                                       O.kruskal(np.ones(Rt), Uts[k])))
     for it in range(10):
         s = m.step(1)
         assert (s["reupdates"] > 0) == res["hist"]["redo"][it]
         for k in range(3):
             for n in range(3):
-                assert rel_fro(m.factor(k, n), snaps[it][k][n]) <= tol * 10, (it, k, n)
+                worst = max(worst, rel_fro(m.factor(k, n), snaps[it][k][n]))
+                assert rel_fro(m.factor(k, n), snaps[it][k][n]) <= tol, (it, k, n)
+    print(f"LRA noisy ({np.dtype(dt).name}, R~={Rt}, {storage}): sweeps {max(sweeps)}, U~ {worst_u:.3e}, "
+          f"[[U~]] {worst_x:.3e}, APG factors {worst:.3e}")
     gfit = O.fit(X64, res["U"], res["lam"])
     assert abs(m.global_fit() - gfit) <= 1e-4
     m.close()

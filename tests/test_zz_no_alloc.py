@@ -1,6 +1,7 @@
 """The allocation-free MTTKRP entry point (for callers that must not let the
-library call cudaMalloc) against the library's regular MTTKRP entry point,
-through the C ABI, on two calls in a row.  Collected last on purpose."""
+library call cudaMalloc) against the library's regular MTTKRP entry point and
+against the FP64 oracle's MTTKRP, through the C ABI, on two calls in a row.
+Collected last on purpose."""
 
 import ctypes
 
@@ -35,6 +36,8 @@ def test_noalloc_matches_regular_mttkrp_twice(shape, R):
     m.set_factors([U])
     ref = m.mttkrp(0, 2, np.float32)
     m.close()
+    from oracle import cncpd_oracle as O
+    want = O.mttkrp(X.astype(np.float64), [A.astype(np.float64) for A in U], 2)
 
     dev = torch.device("cuda")
     Xd = torch.from_numpy(X).to(dev)
@@ -51,6 +54,7 @@ def test_noalloc_matches_regular_mttkrp_twice(shape, R):
         got = M.cpu().numpy()
         assert np.all(np.isfinite(got))
         assert _rel(got, ref) <= 2e-6
+        assert _rel(got, want) <= 2e-6
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
@@ -63,3 +67,17 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
                                           64, ctypes.c_void_p(x.data_ptr()), None)
     assert rc == -1
     assert b"scratch" in C.lib().cncpd_last_error()
+
+
+def test_noalloc_rejects_host_pointers():
+    """Host memory is refused before any kernel runs (this entry point takes
+    device memory only)."""
+    torch, C = _setup()
+    dev = torch.device("cuda")
+    xd = torch.zeros(64, dtype=torch.float32, device=dev)
+    xh = np.zeros(64, dtype=np.float32)
+    rc = C.cncpd_mttkrp_last_mode_noalloc(ctypes.c_void_p(xh.ctypes.data), 2, 2, 2,
+                                          ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(xd.data_ptr()),
+                                          2, ctypes.c_void_p(xd.data_ptr()), None)
+    assert rc == -1
+    assert b"device" in C.lib().cncpd_last_error()
