@@ -190,6 +190,23 @@ int cncpd_global_fit(cncpd_t h, double *fit);
 int cncpd_objective_grad(cncpd_t h, double *F, void *const *gradU,
                          void *const *gradC, cncpd_dtype dtype);
 
+/*
+ * Objective and gradient as cncpd_objective_grad, but at the factors U
+ * given by the caller instead of the handle's current iterate:
+ *  U        K*N pointers (block-major) to U^(n,k), I_n x R_k row-major, dtype
+ *           udtype (F64 or F32), host or device memory; the shared first L_n
+ *           columns are read from block 0 only (as cncpd_set_factors does)
+ *  F, gradU, gradC, dtype: as cncpd_objective_grad
+ * The handle's iterate, previous iterate, cores, Lipschitz history, momentum
+ * and objective history are left exactly as they were, so evaluating the
+ * loss in the middle of a fit does not restart the APG extrapolation (the
+ * differentiable-loss use).  The first call allocates a copy of the factor
+ * arena that the handle keeps.
+ */
+int cncpd_objective_grad_at(cncpd_t h, const void *const *U, cncpd_dtype udtype,
+                            double *F, void *const *gradU, void *const *gradC,
+                            cncpd_dtype dtype);
+
 /* X_(n)^(k) U^{odot_-n} at the current factors (Eq. solapgU second term,
  * without D), I_n x R_k row-major, into host or device memory. */
 int cncpd_mttkrp(cncpd_t h, int k, int n, void *dst, cncpd_dtype dtype);

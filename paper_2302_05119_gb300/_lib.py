@@ -63,6 +63,7 @@ SIGNATURES = {
     "cncpd_lra_factors": (_I, [_P, _I, _I, _P, _I]),
     "cncpd_global_fit": (_I, [_P, ctypes.POINTER(_D)]),
     "cncpd_objective_grad": (_I, [_P, ctypes.POINTER(_D), _PP, _PP, _I]),
+    "cncpd_objective_grad_at": (_I, [_P, _PP, _I, ctypes.POINTER(_D), _PP, _PP, _I]),
     "cncpd_mttkrp": (_I, [_P, _I, _I, _P, _I]),
     "cncpd_lipschitz": (_I, [ctypes.POINTER(_D), _I, ctypes.POINTER(_D)]),
     "cncpd_save_state": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_size_t)]),

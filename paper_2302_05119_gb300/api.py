@@ -226,6 +226,38 @@ class CoupledNCP:
         code = C.cncpd_check_wait_timeout(self._h, float(limit_ms))
         return code, C.lib().cncpd_last_error().decode()
 
+    def objective_grad_at(self, U, gU=None, gC=None, dtype=np.float64):
+        """F and gradients at the factors U[k][n] (numpy or torch, host or
+        device) without touching the solver's state.  gU[k][n] / gC[n]:
+        preallocated outputs (numpy or torch, host or device; None entries
+        skipped), or None to skip that family."""
+        keep, ptrs = [], []
+        code = None
+        for k in range(self.K):
+            for n in range(self.N):
+                obj, p, c = _prep(U[k][n], None if code is None else (np.float64 if code == C.CNCPD_F64 else np.float32))
+                code = c if code is None else code
+                keep.append(obj)
+                ptrs.append(p.value)
+        Up = (ctypes.c_void_p * (self.K * self.N))(*ptrs)
+
+        def out_ptrs(arrs, count):
+            if arrs is None:
+                return None
+            vals = []
+            for a in arrs:
+                vals.append(None if a is None else (a.data_ptr() if _is_torch(a) else a.ctypes.data))
+            assert len(vals) == count
+            return (ctypes.c_void_p * count)(*vals)
+
+        pu = out_ptrs(None if gU is None else [gU[k][n] for k in range(self.K) for n in range(self.N)],
+                      self.K * self.N)
+        pc = out_ptrs(gC, self.N)
+        F = ctypes.c_double()
+        C.check(C.cncpd_objective_grad_at(self._h, Up, code, ctypes.byref(F), pu, pc,
+                                          C.CNCPD_F64 if dtype in (np.float64, "float64") else C.CNCPD_F32))
+        return F.value
+
     def save_state(self):
         p = ctypes.c_void_p()
         n = ctypes.c_size_t()
@@ -262,27 +294,35 @@ def _autograd_function():
         gradient (Eq. solbpgU) are computed by the library at these factors.
         As in ``set_factors``, the shared first L_n columns come from block
         0: their gradient is the sum over blocks (App. A) and lands on block
-        0's columns; the other blocks' copies get zero.
+        0's columns; the other blocks' copies get zero.  The factors may be
+        CPU or CUDA tensors; the gradients are written by the library into
+        tensors on the same device, and the model's own iterate and APG
+        history are not changed (``cncpd_objective_grad_at``).
         """
 
         @staticmethod
         def forward(ctx, model, *factors):
             K, N = model.K, model.N
-            U = [[factors[k * N + n].detach().to("cpu", torch.float64).numpy() for n in range(N)]
-                 for k in range(K)]
-            model.set_factors(U)
-            F, gU, gC = model.objective_grad()
+            U = [[factors[k * N + n].detach().contiguous() for n in range(N)] for k in range(K)]
+            dt = factors[0].dtype
+            if dt not in (torch.float32, torch.float64):
+                raise TypeError(f"factors must be float32 or float64, not {dt}")
+            # gradients written by the library straight into tensors on the
+            # factors' device; the solver state of `model` is left untouched
+            gU = [[torch.empty_like(U[k][n]) for n in range(N)] for k in range(K)]
+            gC = [torch.empty((model.dims[0][n], model.L[n]), dtype=dt, device=factors[0].device)
+                  if model.L[n] else None for n in range(N)]
+            F = model.objective_grad_at(U, gU, gC, np.float64 if dt == torch.float64 else np.float32)
             grads = []
             for k in range(K):
                 for n in range(N):
-                    g = gU[k][n].copy()
+                    g = gU[k][n]
                     Ln = model.L[n]
                     if Ln:
                         g[:, :Ln] = gC[n] if k == 0 else 0.0
-                    f = factors[k * N + n]
-                    grads.append(torch.from_numpy(g).to(f.device, f.dtype))
+                    grads.append(g)
             ctx.save_for_backward(*grads)
-            return torch.tensor(F, dtype=factors[0].dtype, device=factors[0].device)
+            return torch.tensor(F, dtype=dt, device=factors[0].device)
 
         @staticmethod
         def backward(ctx, gF):

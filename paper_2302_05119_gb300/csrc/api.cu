@@ -10,6 +10,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -83,6 +84,8 @@ struct cncpd_ctx {
   size_t arena_elems = 0;
   std::vector<size_t> foff;  // K*N element offsets
   char *A1 = nullptr, *A2 = nullptr, *AS = nullptr;
+  char* A_eval = nullptr;        // cncpd_objective_grad_at: the iterate kept aside (allocated on first use)
+  char* sc_eval = nullptr;       // and the solver scalars
 
   DevDesc hd{};
   DevDesc* dd = nullptr;
@@ -1209,8 +1212,13 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
   return CNCPD_OK;
 }
 
-int cncpd_set_factors(cncpd_t h, int k, int n, const void* U, cncpd_dtype dtype) {
-  TRY(check_handle(h));
+}  // extern "C"
+
+namespace {
+
+// Write U^(n,k) (host or device, F64 or F32) into the current-iterate arena;
+// the shared first L_n columns only from block 0 (copied to every block).
+int write_factor(cncpd_t h, int k, int n, const void* U, cncpd_dtype dtype) {
   if (k < 0 || k >= h->K || n < 0 || n >= h->N || !U) return set_err(CNCPD_EINVAL, "bad block/mode or NULL data");
   if (dtype != CNCPD_F64 && dtype != CNCPD_F32) return set_err(CNCPD_EINVAL, "factor dtype must be F64 or F32");
   const int64_t I = h->dim(k, n);
@@ -1238,6 +1246,57 @@ int cncpd_set_factors(cncpd_t h, int k, int n, const void* U, cncpd_dtype dtype)
   if (k == 0) TRY(propagate_common(h, h->A1));
   CU(cudaFreeAsync(tmp, h->stream));
   if (tmp2) CU(cudaFreeAsync(tmp2, h->stream));
+  return CNCPD_OK;
+}
+
+// Objective and gradient at the factors in the current-iterate arena (no
+// extrapolation); gradients into host or device memory.
+int eval_objective_grad(cncpd_t h, double* F, void* const* gradU, void* const* gradC, cncpd_dtype dtype) {
+  LaunchCfg lc{h->stream, h->num_sms};
+  CU(launch_gram(lc, h->dd, h->hd, h->fp64, 0, h->N, 0));
+  if (h->lra) {
+    CU(launch_cross_gram(lc, h->dd, h->hd, h->fp64, 0, h->N));
+    CU(launch_lra_objective(lc, h->dd, h->hd, h->fp64, h->opts.use_core));
+    for (int n = 0; n < h->N; ++n) CU(launch_collapsed_m(lc, h->dd, h->hd, h->fp64, n));
+  } else {
+    TRY(all_modes_m(h));
+    CU(launch_objective(lc, h->dd, h->hd, h->fp64, h->RP, 1, 0));
+  }
+  TRY(enqueue_readback(h));
+  TRY(sync(h));
+  if (F) *F = h->hs->F;
+  const int dst_f64 = dtype == CNCPD_F64;
+  for (int n = 0; n < h->N; ++n) {
+    CU(launch_grad(lc, h->dd, h->hd, h->fp64, h->RP, n, h->opts.use_core));
+    if (gradU)
+      for (int k = 0; k < h->K; ++k)
+        if (gradU[(size_t)k * h->N + n])
+          TRY(copy_matrix_out(h, h->hd.M[k][n], h->fp64, h->dim(k, n) * h->R[k], gradU[(size_t)k * h->N + n], dtype));
+    if (gradC && gradC[n] && h->L[n] > 0) {
+      const size_t bytes = (size_t)h->dim(0, n) * h->L[n] * (dst_f64 ? 8 : 4);
+      void* tmp = nullptr;
+      CU(cudaMallocAsync(&tmp, bytes + 16, h->stream));
+      CU(launch_common_grad(h->stream, h->dd, h->hd, h->fp64, n, tmp, dst_f64));
+      CU(cudaMemcpyAsync(gradC[n], tmp, bytes, cudaMemcpyDefault, h->stream));
+      CU(cudaFreeAsync(tmp, h->stream));
+    }
+    TRY(sync(h));
+  }
+  return CNCPD_OK;
+}
+
+// Bytes of DevScalars that describe the solver state: everything before the
+// publish sequence number, which must keep counting up so that the host's
+// wait for the next objective sees a new value.
+constexpr size_t kStateScalarBytes = offsetof(DevScalars, seq);
+
+}  // namespace
+
+extern "C" {
+
+int cncpd_set_factors(cncpd_t h, int k, int n, const void* U, cncpd_dtype dtype) {
+  TRY(check_handle(h));
+  TRY(write_factor(h, k, n, U, dtype));
   TRY(sync(h));
   h->dirty = true;
   return CNCPD_OK;
@@ -1300,49 +1359,34 @@ int cncpd_objective_grad(cncpd_t h, double* F, void* const* gradU, void* const* 
   TRY(check_handle(h));
   if (dtype != CNCPD_F64 && dtype != CNCPD_F32) return set_err(CNCPD_EINVAL, "dtype must be F64 or F32");
   if (h->dirty) TRY(initialise(h));
+  return eval_objective_grad(h, F, gradU, gradC, dtype);
+}
+
+int cncpd_objective_grad_at(cncpd_t h, const void* const* U, cncpd_dtype udtype, double* F, void* const* gradU,
+                            void* const* gradC, cncpd_dtype dtype) {
+  TRY(check_handle(h));
+  if (!U) return set_err(CNCPD_EINVAL, "U is NULL");
+  if (dtype != CNCPD_F64 && dtype != CNCPD_F32) return set_err(CNCPD_EINVAL, "dtype must be F64 or F32");
+  if (h->dirty) TRY(initialise(h));
+  const size_t ab = arena_bytes(h);
+  if (!h->A_eval) TRY(dalloc(h, (void**)&h->A_eval, ab));
+  if (!h->sc_eval) TRY(dalloc(h, (void**)&h->sc_eval, kStateScalarBytes));
+  // keep the current iterate and solver scalars; evaluate at U; put them back
+  CU(cudaMemcpyAsync(h->A_eval, h->A1, ab, cudaMemcpyDeviceToDevice, h->stream));
+  CU(cudaMemcpyAsync(h->sc_eval, h->sc, kStateScalarBytes, cudaMemcpyDeviceToDevice, h->stream));
+  int r = CNCPD_OK;
+  for (int k = 0; k < h->K && r == CNCPD_OK; ++k)
+    for (int n = 0; n < h->N && r == CNCPD_OK; ++n) r = write_factor(h, k, n, U[(size_t)k * h->N + n], udtype);
+  if (r == CNCPD_OK) r = eval_objective_grad(h, F, gradU, gradC, dtype);
+  const std::string msg = g_err;
+  CU(cudaMemcpyAsync(h->A1, h->A_eval, ab, cudaMemcpyDeviceToDevice, h->stream));
+  CU(cudaMemcpyAsync(h->sc, h->sc_eval, kStateScalarBytes, cudaMemcpyDeviceToDevice, h->stream));
   LaunchCfg lc{h->stream, h->num_sms};
   CU(launch_gram(lc, h->dd, h->hd, h->fp64, 0, h->N, 0));
-  if (h->lra) {
-    CU(launch_cross_gram(lc, h->dd, h->hd, h->fp64, 0, h->N));
-    CU(launch_lra_objective(lc, h->dd, h->hd, h->fp64, h->opts.use_core));
-    for (int n = 0; n < h->N; ++n) CU(launch_collapsed_m(lc, h->dd, h->hd, h->fp64, n));
-  } else {
-    TRY(all_modes_m(h));
-    CU(launch_objective(lc, h->dd, h->hd, h->fp64, h->RP, 1, 0));
-  }
-  TRY(enqueue_readback(h));
+  if (h->lra) CU(launch_cross_gram(lc, h->dd, h->hd, h->fp64, 0, h->N));
   TRY(sync(h));
-  if (F) *F = h->hs->F;
-  const int dst_f64 = dtype == CNCPD_F64;
-  for (int n = 0; n < h->N; ++n) {
-    CU(launch_grad(lc, h->dd, h->hd, h->fp64, h->RP, n, h->opts.use_core));
-    TRY(sync(h));
-    if (gradU)
-      for (int k = 0; k < h->K; ++k)
-        if (gradU[(size_t)k * h->N + n])
-          TRY(copy_matrix_out(h, h->hd.M[k][n], h->fp64, h->dim(k, n) * h->R[k], gradU[(size_t)k * h->N + n], dtype));
-    if (gradC && gradC[n] && h->L[n] > 0) {
-      const int Ln = h->L[n];
-      const int64_t I = h->dim(0, n);
-      std::vector<double> acc((size_t)I * Ln, 0.0);
-      for (int k = 0; k < h->K; ++k) {
-        std::vector<double> g((size_t)I * h->R[k]);
-        TRY(copy_matrix_out(h, h->hd.M[k][n], h->fp64, I * h->R[k], g.data(), CNCPD_F64));
-        for (int64_t i = 0; i < I; ++i)
-          for (int r = 0; r < Ln; ++r) acc[(size_t)i * Ln + r] += g[(size_t)i * h->R[k] + r];
-      }
-      if (dst_f64) {
-        CU(cudaMemcpyAsync(gradC[n], acc.data(), acc.size() * 8, cudaMemcpyDefault, h->stream));
-      } else {
-        std::vector<float> f(acc.begin(), acc.end());
-        CU(cudaMemcpyAsync(gradC[n], f.data(), f.size() * 4, cudaMemcpyDefault, h->stream));
-        TRY(sync(h));
-        continue;
-      }
-      TRY(sync(h));
-    }
-  }
-  return CNCPD_OK;
+  if (r != CNCPD_OK) g_err = msg;
+  return r;
 }
 
 int cncpd_global_fit(cncpd_t h, double* fit) {
@@ -1632,7 +1676,8 @@ int cncpd_load_state(cncpd_t h, const void* blob, size_t nbytes) {
   const char* p = (const char*)blob + sizeof hdr;
   CU(cudaMemcpyAsync(h->A1, p, ab, cudaMemcpyHostToDevice, h->stream));
   CU(cudaMemcpyAsync(h->A2, p + ab, ab, cudaMemcpyHostToDevice, h->stream));
-  CU(cudaMemcpyAsync(h->sc, p + 2 * ab, sizeof(DevScalars), cudaMemcpyHostToDevice, h->stream));
+  // the publish sequence number keeps its current value (see kStateScalarBytes)
+  CU(cudaMemcpyAsync(h->sc, p + 2 * ab, kStateScalarBytes, cudaMemcpyHostToDevice, h->stream));
   LaunchCfg lc{h->stream, h->num_sms};
   CU(launch_gram(lc, h->dd, h->hd, h->fp64, 0, h->N, 0));
   if (h->lra) CU(launch_cross_gram(lc, h->dd, h->hd, h->fp64, 0, h->N));

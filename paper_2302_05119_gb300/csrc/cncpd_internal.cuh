@@ -346,6 +346,9 @@ cudaError_t launch_convert(cudaStream_t s, const void* src, int src_f64, void* d
 cudaError_t launch_uniform_init(cudaStream_t s, void* dst, int fp64, int64_t n, uint64_t seed);
 cudaError_t launch_lmax_host(const double* d_H, int R, double* d_out, cudaStream_t s);
 cudaError_t launch_grad(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int RP, int n, int use_core);
+// Sum over blocks of the first L_n gradient columns (after launch_grad of mode n) into out (I_n x L_n).
+cudaError_t launch_common_grad(cudaStream_t s, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int n, void* out,
+                               int out_f64);
 // LRA
 cudaError_t launch_cross_gram(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int n_begin, int n_end);
 cudaError_t launch_collapsed_m(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int n);

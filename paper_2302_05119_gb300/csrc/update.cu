@@ -1623,6 +1623,37 @@ __global__ void k_grad(const DevDesc* __restrict__ d, int n, int use_core) {
   }
 }
 
+// Gradient of the shared columns U_C^(n) (App. A): out[i, r] = sum_k of
+// column r < L_n of block k's gradient (left in M[k][n] by k_grad), the
+// blocks added in order in FP64, written as O.
+template <typename T, typename O>
+__global__ void k_common_grad(const DevDesc* __restrict__ d, int n, O* __restrict__ out) {
+  const int Ln = d->L[n];
+  const int64_t total = d->dims[0][n] * Ln;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / Ln;
+    const int r = (int)(e % Ln);
+    double s = 0.0;
+    for (int k = 0; k < d->K; ++k) s += (double)reinterpret_cast<const T*>(d->M[k][n])[i * d->R[k] + r];
+    out[e] = (O)s;
+  }
+}
+
+cudaError_t launch_common_grad(cudaStream_t s, const DevDesc* dd, const DevDesc& hd, int fp64, int n, void* out,
+                               int out_f64) {
+  const int64_t total = hd.dims[0][n] * hd.L[n];
+  if (total == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)std::min<int64_t>(1024, (total + 255) / 256);
+  if (fp64) {
+    if (out_f64) k_common_grad<double, double><<<grid, 256, 0, s>>>(dd, n, static_cast<double*>(out));
+    else k_common_grad<double, float><<<grid, 256, 0, s>>>(dd, n, static_cast<float*>(out));
+  } else {
+    if (out_f64) k_common_grad<float, double><<<grid, 256, 0, s>>>(dd, n, static_cast<double*>(out));
+    else k_common_grad<float, float><<<grid, 256, 0, s>>>(dd, n, static_cast<float*>(out));
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_grad(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd, int fp64, int RP, int n,
                         int use_core) {
   int64_t imax = 0;

@@ -422,3 +422,84 @@ def test_bf16_storage_error_vs_fp64_oracle(storage, tol):
             for n in range(3):
                 assert rel_fro(snaps_g[it][0][k][n], snaps_o[it][0][k][n]) <= tol, (it, k, n)
     m.close()
+
+
+@pytest.mark.parametrize("tdt", ["float64", "float32"])
+def test_autograd_loss_on_cuda_tensors(tdt):
+    """CoupledCPLoss with CUDA factors: the gradients come back as CUDA
+    tensors written by the library (no host round trip of the factors) and
+    match the oracle's gradient (Eq. solbpgU; App. A for the shared
+    columns)."""
+    torch = pytest.importorskip("torch")
+    dt = getattr(torch, tdt)
+    dims = [(12, 10, 8)] * 2
+    L = [2, 1, 0]
+    Xs, _, U0 = coupled_inputs(dims, 3, L, seed=19)
+    P = _P()
+    m = P.CoupledNCP([X.astype(np.float32 if tdt == "float32" else np.float64) for X in Xs], 3, L)
+    fac = [torch.tensor(U0[k][n], dtype=dt, device="cuda", requires_grad=True) for k in range(2) for n in range(3)]
+    F = P.CoupledCPLoss.apply(m, *fac)
+    grads = torch.autograd.grad(F, fac)
+    assert F.is_cuda and all(g.is_cuda and g.dtype == dt for g in grads)
+    X64 = [X.astype(np.float32).astype(np.float64) if tdt == "float32" else X for X in Xs]
+    Ucast = [[np.asarray(A, dtype=np.float32 if tdt == "float32" else np.float64).astype(np.float64) for A in Uk]
+             for Uk in U0]
+    prob = O.Problem(X64, [3, 3], L)
+    Uc = O.couple_initial(prob, Ucast)
+    lam = [np.ones(3)] * 2
+    tol = 1e-10 if tdt == "float64" else 2e-5
+    assert float(F.detach()) == pytest.approx(prob.objective_fn(Uc, lam), rel=tol)
+    for k in range(2):
+        for n in range(3):
+            want = O.gradient(prob, Uc, lam, k, n).copy()
+            if L[n]:
+                want[:, :L[n]] = sum(O.gradient(prob, Uc, lam, kk, n)[:, :L[n]] for kk in range(2)) if k == 0 else 0.0
+            assert rel_fro(grads[k * 3 + n].cpu().numpy(), want) <= tol, (k, n)
+    m.close()
+
+
+def test_loss_evaluation_leaves_the_solver_state_alone():
+    """Evaluating the loss and its gradient at other factors in the middle of
+    a fit does not change the iterates that follow (the APG extrapolation
+    and its history are kept)."""
+    torch = pytest.importorskip("torch")
+    dims = [(16, 12, 10)] * 3
+    Xs, _, U0 = coupled_inputs(dims, 4, [2, 0, 0], seed=20)
+    X32 = [X.astype(np.float32) for X in Xs]
+    P = _P()
+    a = P.CoupledNCP(X32, 4, [2, 0, 0])
+    a.set_factors(U0)
+    a.step(6)
+    rng = np.random.default_rng(3)
+    other = [torch.tensor(rng.random((d, 4)), dtype=torch.float32, device="cuda", requires_grad=True)
+             for _ in range(3) for d in dims[0]]
+    F = P.CoupledCPLoss.apply(a, *other)
+    torch.autograd.grad(F, other)
+    a.step(6)
+    b = P.CoupledNCP(X32, 4, [2, 0, 0])
+    b.set_factors(U0)
+    b.step(12)
+    for k in range(3):
+        for n in range(3):
+            assert np.array_equal(a.factor(k, n, np.float32), b.factor(k, n, np.float32)), (k, n)
+    a.close()
+    b.close()
+
+
+def test_load_state_on_the_same_handle():
+    """Save, step, load the saved state back into the same handle, step
+    again: the iterate equals the one the first step produced."""
+    dims = [(14, 11, 9)] * 2
+    Xs, _, U0 = coupled_inputs(dims, 4, [2, 0, 0], seed=25)
+    m = _P().CoupledNCP([X.astype(np.float32) for X in Xs], 4, [2, 0, 0])
+    m.set_factors(U0)
+    m.step(5)
+    blob = m.save_state()
+    m.step(1)
+    U6 = m.factors(np.float32)
+    m.load_state(blob)
+    m.step(1)
+    for k in range(2):
+        for n in range(3):
+            assert np.array_equal(m.factor(k, n, np.float32), U6[k][n])
+    m.close()
