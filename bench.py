@@ -337,12 +337,13 @@ def run_ours(args):
         if ws > 1:
             torch.distributed.barrier()
 
-    # clocks are sampled over an untimed load phase of about 0.4 s just
-    # before the timed region and over the timed region itself (a timed
+    # clocks are sampled over an untimed load phase (--clock-load-s, 0.4 s by
+    # default) just before the timed region and over the timed region itself (a timed
     # region of a few milliseconds is shorter than one nvidia-smi sample)
     clocks = ClockSampler(local)
     clocks.start()
-    m.step(max(1, min(20000, int(0.4 / max(t_iter, 1e-5)))))
+    if args.clock_load_s > 0:
+        m.step(max(1, min(20000, int(args.clock_load_s / max(t_iter, 1e-5)))))
     barrier()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -464,6 +465,9 @@ def main():
     ap.add_argument("--lra", action="store_true", help="run the LRA step (lraCoNCPD-APG) before the timed steps")
     ap.add_argument("--time-to-fit", action="store_true",
                     help="time to reach the converged FP64 fit within 1e-4, FP32 vs mixed precision")
+    ap.add_argument("--clock-load-s", type=float, default=0.4,
+                    help="seconds of untimed iterations run just before the timed region while the "
+                         "clocks are sampled (0 under a profiler)")
     ap.add_argument("--no-time-to-fit", action="store_true",
                     help="leave the time-to-fit record out of the default line")
     args = ap.parse_args()

@@ -74,8 +74,9 @@ typedef struct {
   int storage;       /* cncpd_dtype of X on the device, or -1 = same as the input
                         (F64 input -> F64 path; anything else -> F32 factors) */
   int use_graph;     /* 1: replay each sweep as a CUDA graph */
-  int profile;       /* 1: time the tensor-streaming kernels with CUDA events on every
-                        8th iteration (and every re-update); the other iterations
+  int profile;       /* 1: time the tensor-streaming kernels with CUDA events on the
+                        first iteration of each cncpd_step / cncpd_fit call and every
+                        8th one after it (and every re-update); the other iterations
                         replay a graph without event nodes */
   int tensor_cores;  /* 1: BF16-stored third-order tensors with ranks up to 32 stream
                         through tcgen05 tensor-core passes; 0: CUDA-core passes only */

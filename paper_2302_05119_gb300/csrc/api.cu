@@ -522,6 +522,11 @@ bool fused_last_reduce(const cncpd_ctx* c) { return !c->lra && c->N - c->h == 1;
 // (tensor-pass path, block-parallel update with room for the rows of M).
 bool fused_objective(const cncpd_ctx* c) { return !c->lra && update_fuses_objective(c->hd, c->fp64, c->RP); }
 
+// Mode of the Gram the first Lipschitz launch of a sweep sums from its
+// chunks: with the fused objective and no cores, the last mode's Gram is
+// left in chunks by its update (the objective does not need the sum).
+int first_prev(const cncpd_ctx* c) { return (fused_objective(c) && !c->opts.use_core) ? c->N - 1 : -1; }
+
 // Launch H / L of mode n (with the Gram of mode n-1) on the side stream so
 // that it runs concurrently with the tensor pass enqueued next on the main
 // stream; the main stream joins before the update of mode n.
@@ -549,10 +554,10 @@ int enqueue_sweep(cncpd_ctx* c, int use_w, int begin) {
       // the iteration bookkeeping) in one launch
       TRY(enqueue_trailing(c, c->dd, c->hd, c->RP));
       if (level2_is_pair(c->hd, n)) {
-        CU(launch_mode_prep(lc, c->dd, c->hd, c->fp64, n, core, -1, 1, beg));
+        CU(launch_mode_prep(lc, c->dd, c->hd, c->fp64, n, core, first_prev(c), 1, beg));
       } else {
         TRY(enqueue_mode_m(c, n));
-        CU(launch_lipschitz(lc, c->dd, c->hd, c->fp64, n, core, -1, beg));
+        CU(launch_lipschitz(lc, c->dd, c->hd, c->fp64, n, core, first_prev(c), beg));
       }
     } else if (!c->lra && n == c->h) {
       // the lead pass needs the factors updated so far; H / L of mode h only
@@ -802,6 +807,7 @@ int run_iterations(cncpd_ctx* c, int n_iters, bool use_eps, cncpd_stats* out) {
   const double t0 = now_s();
   if (c->dirty) TRY(initialise(c));
   const double pb = c->lra ? 0.0 : 2.0 * pass_bytes(c);
+  c->prof_runs = 0;  // the first sweep of every call records its pass times
   int pending = -1;  // event set of a main replay whose pass times are not read yet
   for (int it = 0; it < n_iters; ++it) {
     const unsigned int s0 = c->hm->seq;
@@ -1122,6 +1128,7 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
   const size_t rr = (size_t)c->Rmax * c->Rmax;
   CTRY(dalloc(c, (void**)&d.Gbase, (size_t)K * N * rr * sizeof(double)));
   CTRY(dalloc(c, &d.Hbase, (size_t)K * rr * c->fsz));
+  CTRY(dalloc(c, (void**)&d.H64base, (size_t)K * rr * sizeof(double)));
   for (int n = 0; n < N; ++n) {
     int64_t imax = 0;
     for (int k = 0; k < K; ++k) imax = std::max<int64_t>(imax, c->dim(k, n));
@@ -1131,6 +1138,7 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
   }
   // per-CTA <M, U_new> sums of the objective fused into the last update
   CTRY(dalloc(c, &d.dotp, (size_t)d.gnc[N - 1] * K * c->RP * c->fsz));
+  CTRY(dalloc(c, (void**)&d.xxp, (size_t)d.gnc[N - 1] * K * sizeof(double)));
   for (int k = 0; k < K; ++k)
     for (int n = 0; n < N; ++n) {
       d.U1[k][n] = c->U1p(k, n);
@@ -1460,6 +1468,7 @@ int cncpd_lra(cncpd_t h, const int* R_tilde, const void* const* Ut0, cncpd_dtype
   // ALS Grams are formed by one CTA per factor (no chunk partials, no arenas)
   a.Gbase = nullptr;
   a.Hbase = nullptr;
+  a.H64base = nullptr;
   for (int n = 0; n < N; ++n) {
     a.Gp[n] = nullptr;
     a.gr[n] = a.gnc[n] = 0;

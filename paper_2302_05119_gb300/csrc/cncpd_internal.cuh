@@ -128,6 +128,9 @@ struct DevDesc {
   // Grams and H live in arenas: G^(m,k) = Gbase + (k*N + m)*Rmax^2, H^(k) = Hbase + k*Rmax^2
   double* Gbase;
   void* Hbase;
+  // H^(k) of the mode being updated also in FP64 (the objective of the last
+  // mode takes ||X_hat||^2 = <H^(N-1,k), G^(N-1,k)> from it): H64base + k*Rmax^2
+  double* H64base;
   // Gram partials of each mode (null: Grams are formed by one CTA per factor).
   // Rows of U^(n,k) are cut into chunks of gr[n] rows; chunk c of block k
   // holds its partial sums, in the factor type, at Gp[n] + (k*gnc[n] + c)*Rmax^2.
@@ -145,6 +148,7 @@ struct DevDesc {
   // objective fused into the last mode's update: per-CTA sums of <M, U_new>,
   // [chunk CTA][block][RP] in the factor type (null: separate objective kernel)
   void* dotp;
+  double* xxp;                          // per-CTA shares of ||X_hat^(k)||^2 of that objective: [chunk CTA][block]
   int use_umma, umma_np;
   void* Bt[CNCPD_KMAX];
   void* Bl[CNCPD_KMAX];
@@ -276,6 +280,36 @@ inline void carve() {
                            (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
     cudaGetLastError();
   done.fetch_or(bit);
+}
+
+// ------------------------------------------- programmatic dependent launch --
+// The kernels of a sweep are launched with programmatic stream serialisation:
+// a kernel may be launched while its predecessor on the stream is still
+// finishing.  Each such kernel calls pdl_wait() before it reads anything an
+// earlier kernel of the sweep wrote and before it writes anything (the wait
+// returns once the predecessor grid has completed and its memory is
+// visible; without a programmatic predecessor it returns at once).  The
+// small kernels call pdl_trigger() right after their wait, which lets their
+// successor be launched; the tensor passes leave that to their exit.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// kernel<<<grid, block, smem, stream>>>(args...) with programmatic stream
+// serialisation allowed (the kernel must call pdl_wait() as described above).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
 // ----------------------------------------------------- launch wrappers ----

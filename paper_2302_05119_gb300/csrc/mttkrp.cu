@@ -330,6 +330,8 @@ struct SplitArgs {
 // One thread per output element, the splits added in order (sum_splits).
 template <typename T>
 __global__ void __launch_bounds__(256) k_reduce_splits(const __grid_constant__ SplitArgs<T> a) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x;
   const int64_t total = a.prefix[a.K];
   if (e >= total) return;
@@ -445,7 +447,8 @@ static cudaError_t reduce_splits_impl(const LaunchCfg& c, const DevDesc& hd) {
   const int64_t blocks = (a.prefix[hd.K] + 255) / 256;
   if (blocks == 0) return cudaSuccess;
   carve<k_reduce_splits<T>>();
-  k_reduce_splits<T><<<(unsigned)blocks, 256, 0, c.stream>>>(a);
+  cudaError_t e = launch_pdl(k_reduce_splits<T>, dim3((unsigned)blocks), dim3(256), 0, c.stream, a);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -173,6 +173,7 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
 
   if (warp >= TT_CONS) {
     // ------------------------------------------------- Khatri-Rao warps
+    pdl_wait();  // the factors come from the previous kernel of the sweep
     const int kw = warp - TT_CONS;
     uint32_t it = 0;
     bool ok = true;
@@ -217,6 +218,7 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
   }
 
   // -------------------------------------------------------------- consumers
+  pdl_wait();
   uint32_t it = 0;
   const int li = lane & 7, cq = lane >> 3;  // row offset, column quarter
   constexpr int RH = RP / 2;
@@ -389,6 +391,7 @@ __global__ void __launch_bounds__((LT_CONS + NKR + 1) * 32, 1) k_lead_tma(const 
 
   if (warp >= LT_CONS) {
     // ------------------------------------------------- Khatri-Rao warps
+    pdl_wait();  // the factors come from the previous kernel of the sweep
     const int kw = warp - LT_CONS;
     uint32_t it = 0;
     bool ok = true;
@@ -436,6 +439,7 @@ __global__ void __launch_bounds__((LT_CONS + NKR + 1) * 32, 1) k_lead_tma(const 
   }
 
   // -------------------------------------------------------------- consumers
+  pdl_wait();
   const int ch = warp & 1, rq = warp >> 1;  // column half (128 columns, 4 per lane), row quarter (8 rows)
   const int colw = ch * 128 + 4 * lane;    // first of this lane's four columns within the tile
   uint32_t it = 0;
@@ -543,7 +547,10 @@ static cudaError_t trailing_tma_impl(const LaunchCfg& c, const DevDesc* dd, cons
   cudaError_t e = cudaFuncSetAttribute(k_trailing_tma<RP, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = hd.lt_sched ? hd.lt_grid : (total < c.num_sms ? total : c.num_sms);
-  k_trailing_tma<RP, XT><<<grid, (TT_CONS + NKR + 1) * 32, smem, c.stream>>>(dd);
+  // the issuer streams X (constant) from the start; the other warps wait for
+  // the previous kernel of the sweep (programmatic dependent launch)
+  e = launch_pdl(k_trailing_tma<RP, XT>, dim3(grid), dim3((TT_CONS + NKR + 1) * 32), smem, c.stream, dd);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -555,7 +562,8 @@ static cudaError_t lead_tma_impl(const LaunchCfg& c, const DevDesc* dd, const De
   cudaError_t e = cudaFuncSetAttribute(k_lead_tma<RP, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = hd.tt_sched ? hd.tt_grid : (total < c.num_sms ? total : c.num_sms);
-  k_lead_tma<RP, XT><<<grid, (LT_CONS + NKR + 1) * 32, smem, c.stream>>>(dd);
+  e = launch_pdl(k_lead_tma<RP, XT>, dim3(grid), dim3((LT_CONS + NKR + 1) * 32), smem, c.stream, dd);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -130,6 +130,8 @@ __device__ __forceinline__ void tmem_parts16(uint32_t t, int c0, float (&v)[16])
 // h-1 for the lead pass.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_split_factor(const DevDesc* __restrict__ d, int which) {
+  pdl_wait();
+  pdl_trigger();
   const int k = blockIdx.y;
   const int m = which ? d->h - 1 : d->N - 1;
   const int NP = d->umma_np;
@@ -164,6 +166,7 @@ __global__ void __launch_bounds__(U_THREADS, 1) k_trailing_umma(const DevDesc* _
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const UmmaBars bars = umma_setup<S>(base);
+  pdl_wait();  // the split factor and the factors come from earlier kernels of the sweep
   const uint32_t tmem = *bars.tmem_slot;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int* err = &d->sc->timeout;
@@ -292,6 +295,7 @@ __global__ void __launch_bounds__(U_THREADS, 1) k_lead_umma(const DevDesc* __res
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const UmmaBars bars = umma_setup<S>(base);
+  pdl_wait();  // the split factor and the factors come from earlier kernels of the sweep
   const uint32_t tmem = *bars.tmem_slot;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int* err = &d->sc->timeout;
@@ -449,7 +453,8 @@ cudaError_t launch_split_factor(const LaunchCfg& c, const DevDesc* dd, const Dev
   int64_t imax = 1;
   for (int k = 0; k < hd.K; ++k) imax = hd.dims[k][m] > imax ? hd.dims[k][m] : imax;
   const unsigned gx = (unsigned)((imax + 255) / 256);
-  k_split_factor<<<dim3(gx, hd.K), 256, 0, c.stream>>>(dd, which);
+  cudaError_t e = launch_pdl(k_split_factor, dim3(gx, hd.K), dim3(256), 0, c.stream, dd, which);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -461,7 +466,8 @@ static cudaError_t trailing_umma_impl(const LaunchCfg& c, const DevDesc* dd, con
   cudaError_t e = cudaFuncSetAttribute(k_trailing_umma<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = hd.lt_sched ? hd.lt_grid : (total < c.num_sms ? total : c.num_sms);
-  k_trailing_umma<NP><<<grid, U_THREADS, smem, c.stream>>>(dd);
+  e = launch_pdl(k_trailing_umma<NP>, dim3(grid), dim3(U_THREADS), smem, c.stream, dd);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -473,7 +479,8 @@ static cudaError_t lead_umma_impl(const LaunchCfg& c, const DevDesc* dd, const D
   cudaError_t e = cudaFuncSetAttribute(k_lead_umma<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = hd.tt_sched ? hd.tt_grid : (total < c.num_sms ? total : c.num_sms);
-  k_lead_umma<NP><<<grid, U_THREADS, smem, c.stream>>>(dd);
+  e = launch_pdl(k_lead_umma<NP>, dim3(grid), dim3(U_THREADS), smem, c.stream, dd);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -22,6 +22,7 @@ struct LipArgs {            // H^(n,k) and L^(n,k) for every block
   DevScalars* sc;
   double* G;                // Gram arena: G^(m,k) at G + (k*N + m)*rr
   T* H;                     // H arena: H^(k) at H + k*rr
+  double* H64;              // the same in FP64
   const T* Gp_prev;         // partials of mode prev
   int R[CNCPD_KMAX];
   int Iprev[CNCPD_KMAX];
@@ -60,7 +61,10 @@ struct UpdArgs {            // fused APG update of mode n
   int obj, N;
   double inv_K;
   T* dotp;
+  double* xxp;              // per-CTA <H^(n,k), chunk of G^(n,k)> in FP64: xxp[cta][k]
+  int gram_last;            // 1: the tail also stores G^(n) (summed from its chunks)
   double* G;
+  const double* H64;        // H^(n,k) in FP64 (written by the Lipschitz kernel of mode n)
   HostMirror* hm;
 };
 
@@ -436,6 +440,7 @@ __device__ void lip_body(const LipArgs<T>& a, int k, unsigned char* smem) {
     if constexpr (sizeof(T) == 8) Hs[p] = h;
     ls->Hf[p] = (float)h;
     a.H[(size_t)k * rr + p] = (T)h;
+    a.H64[(size_t)k * rr + p] = h;
   }
   if (!a.want_L) return;
   const double L = lmax_rp<T, RP>(Hs, R, ls);
@@ -447,6 +452,8 @@ __device__ void lip_body(const LipArgs<T>& a, int k, unsigned char* smem) {
 
 template <typename T, int RP>
 __global__ void __launch_bounds__(256) k_lipschitz(const __grid_constant__ LipArgs<T> a) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   lip_body<T, RP>(a, blockIdx.x, smem_raw);
 }
@@ -542,6 +549,8 @@ __device__ void pair_body(const PairArgs<T>& a, int b, T* red) {
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_level2_pair(const __grid_constant__ PairArgs<T> a) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ T red[8 * 256];
   pair_body<T>(a, blockIdx.x, red);
 }
@@ -550,6 +559,8 @@ __global__ void __launch_bounds__(256) k_level2_pair(const __grid_constant__ Pai
 template <typename T, int RP>
 __global__ void __launch_bounds__(256) k_mode_prep(const __grid_constant__ LipArgs<T> la,
                                                    const __grid_constant__ PairArgs<T> pa) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if ((int)blockIdx.x < la.K) lip_body<T, RP>(la, blockIdx.x, smem_raw);
   else pair_body<T>(pa, blockIdx.x - la.K, reinterpret_cast<T*>(smem_raw));
@@ -574,6 +585,7 @@ static LipArgs<T> lip_args(const DevDesc& hd, int n, int use_core, int prev, int
   a.sc = hd.sc;
   a.G = hd.Gbase;
   a.H = reinterpret_cast<T*>(hd.Hbase);
+  a.H64 = hd.H64base;
   if (a.prev >= 0) {
     a.Gp_prev = reinterpret_cast<const T*>(hd.Gp[prev]);
     a.gnc_prev = hd.gnc[prev];
@@ -637,7 +649,8 @@ static cudaError_t mode_prep_impl(const LaunchCfg& c, const DevDesc& hd, int n, 
   if (with_level2 == 2) {
     if (ctas == 0) return cudaSuccess;
     carve<k_level2_pair<T>>();
-    k_level2_pair<T><<<ctas, 256, 0, c.stream>>>(pa);
+    cudaError_t el = launch_pdl(k_level2_pair<T>, dim3(ctas), dim3(256), 0, c.stream, pa);
+    if (el != cudaSuccess) return el;
     return cudaGetLastError();
   }
   LipArgs<T> la = lip_args<T>(hd, n, use_core, prev, 1, begin);
@@ -646,13 +659,15 @@ static cudaError_t mode_prep_impl(const LaunchCfg& c, const DevDesc& hd, int n, 
     cudaError_t e = allow_smem(k_lipschitz<T, RP>, sm);
     if (e != cudaSuccess) return e;
     carve<k_lipschitz<T, RP>>();
-    k_lipschitz<T, RP><<<hd.K, RP <= 16 ? 128 : 256, sm, c.stream>>>(la);
+    e = launch_pdl(k_lipschitz<T, RP>, dim3(hd.K), dim3(RP <= 16 ? 128 : 256), sm, c.stream, la);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
   }
   cudaError_t e = allow_smem(k_mode_prep<T, RP>, sm);
   if (e != cudaSuccess) return e;
   carve<k_mode_prep<T, RP>>();
-  k_mode_prep<T, RP><<<hd.K + ctas, 256, sm, c.stream>>>(la, pa);
+  e = launch_pdl(k_mode_prep<T, RP>, dim3(hd.K + ctas), dim3(256), sm, c.stream, la, pa);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -725,6 +740,8 @@ struct UpdCfg {
 
 template <typename T, int RP>
 __global__ void __launch_bounds__(128) k_update(const __grid_constant__ UpdArgs<T> a) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int TY = UpdCfg<T, RP>::ROWS;
   constexpr int KC = UpdCfg<T, RP>::KC;
   constexpr int NT = RP * TY;
@@ -891,62 +908,95 @@ __global__ void __launch_bounds__(128) k_update(const __grid_constant__ UpdArgs<
 // lanes sum the Gram of mode n from its chunks (stored as G^(n,k)), the
 // lambda^T (*_m G^(m)) lambda terms and lambda^T c with c the column sums of
 // <M, U_new> (the next core term); warp 0 then adds the blocks up in order.
+// Objective of Eq. costfunc after the last mode's update, run by the last
+// CTA of that update to finish (every CTA has left its <M, U_new> column
+// sums and its share of ||X_hat||^2):
+//   ||X_hat^(k)||^2 = <H^(n,k), G^(n,k)> = sum over CTAs c of
+//     <H^(n,k), chunk c of G^(n,k)>, H^(n,k) = D (*_{m != n} G^(m,k)) D in
+//     FP64 from the Lipschitz kernel of this mode, the shares added in CTA
+//     order;
+//   <X^(k), X_hat^(k)> = sum_r lambda_r (M^(n,k)^T U^(n,k))_{rr}, the column
+//     sums added in CTA order (also kept as the core term);
+//   F_k = (||X||^2 - 2 <X, X_hat> + ||X_hat||^2) / 2, RelErr_k = sqrt(2 F_k) / ||X||.
+// Each block's terms are added by one warp in a fixed order, so the result
+// does not depend on timing.  G^(n) itself is summed from its chunks by the
+// next sweep's first Lipschitz launch, or here when the cores are updated
+// (their update at the start of the next sweep reads it).
 template <typename T, int RP>
-__device__ void update_objective_tail(const UpdArgs<T>& a, int tid, int NT) {
+__device__ void update_objective_tail(const UpdArgs<T>& a, int tid, int NT, unsigned char* smem) {
+  constexpr int RR = RP * RP;
   const int K = a.K, N = a.N, n = a.n, rr = a.rr;
   DevScalars* sc = a.sc;
-  const int warp = tid >> 5, lane = tid & 31, nw = NT >> 5;
-  const int wpb = nw / K;  // whole warps per block (at least 2: checked on the host)
-  __shared__ double pxx[32], pip[32];
-  if (warp < K * wpb) {
-    const int kk = warp / wpb, gl = (warp % wpb) * 32 + lane, G = wpb * 32;
-    const int Rk = a.R[kk];
-    const int nch = (int)((a.I[kk] + a.gr - 1) / a.gr);
-    double* Gk = a.G + (size_t)kk * N * rr;
-    const T* gp = a.Gp + (size_t)kk * a.gnc * rr;
-    double xx = 0.0;
-    for (int p = gl; p < Rk * Rk; p += G) {
-      const double g = gram_sum<T, true>(gp, nch, rr, p);
-      Gk[(size_t)n * rr + p] = g;
-      double t = sc->lam1[kk][p / Rk] * sc->lam1[kk][p % Rk] * g;
-      for (int m = 0; m < N; ++m)
-        if (m != n) t *= Gk[(size_t)m * rr + p];
-      xx += t;
+  double* xb = reinterpret_cast<double*>(smem);  // [K][RR]: H * G_new
+  double* ib = xb + (size_t)K * RR;              // [K][RP]: lambda * core term
+  double* fk = ib + (size_t)K * RP;              // [K]
+  double* rk = fk + K;                           // [K]
+  double x2 = 0.0, ix2 = 0.0;
+  if (tid < K) {
+    x2 = sc->xnorm2[tid];
+    ix2 = sc->inv_xnorm2[tid];
+  }
+  if (a.gram_last) {
+    // G^(n) for the next sweep's core update, summed from its chunks
+    for (int e = tid; e < K * RR; e += NT) {
+      const int kk = e / RR, q = e % RR, ra = q / RP, rb = q % RP;
+      const int Rk = a.R[kk];
+      if (ra < Rk && rb < Rk) {
+        const int p = ra * Rk + rb;
+        const int nch = (a.I[kk] + a.gr - 1) / a.gr;
+        a.G[((size_t)kk * N + n) * rr + p] = gram_sum<T, true>(a.Gp + (size_t)kk * a.gnc * rr, nch, rr, p);
+      }
     }
-    double ip = 0.0;
-    for (int cc = gl; cc < Rk; cc += G) {
+  }
+  // ||X_hat^(k)||^2: the CTAs' shares in CTA order (a warp per block below)
+  const int nct = (int)gridDim.x;
+  for (int e = tid; e < K * RR; e += NT) {
+    const int kk = e / RR, c0 = e % RR;
+    xb[e] = c0 < nct ? __ldcg(a.xxp + (size_t)c0 * K + kk) : 0.0;
+  }
+  for (int e = tid; e < K * RP; e += NT) {
+    const int kk = e / RP, cc = e % RP;
+    double v = 0.0;
+    if (cc < a.R[kk]) {
+      const double lam = sc->lam1[kk][cc];
       const double cr = gram_sum<T, true>(a.dotp + (size_t)kk * RP, (int)gridDim.x, K * RP, cc);
       sc->cterm[kk][cc] = cr;
-      ip += sc->lam1[kk][cc] * cr;
+      v = lam * cr;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      xx += __shfl_xor_sync(0xffffffffu, xx, o);
-      ip += __shfl_xor_sync(0xffffffffu, ip, o);
-    }
-    if (lane == 0) {
-      pxx[warp] = xx;
-      pip[warp] = ip;
+    ib[e] = v;
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31, nw = NT >> 5;  // whole warps only
+  if (warp < nw) {
+    for (int kk = warp; kk < K; kk += nw) {
+      double xx = 0.0, ip = 0.0;
+      for (int q = lane; q < min(RR, nct); q += 32) xx += xb[(size_t)kk * RR + q];
+      for (int q = lane; q < RP; q += 32) ip += ib[(size_t)kk * RP + q];
+      for (int o = 16; o > 0; o >>= 1) {
+        xx += __shfl_xor_sync(0xffffffffu, xx, o);
+        ip += __shfl_xor_sync(0xffffffffu, ip, o);
+      }
+      if (lane == 0) {
+        fk[kk] = xx;
+        rk[kk] = ip;
+      }
     }
   }
   __syncthreads();
   if (tid < K) {
-    // the block's warp sums in order
-    double xx = 0.0, ip = 0.0;
-    for (int q = 0; q < wpb; ++q) {
-      xx += pxx[tid * wpb + q];
-      ip += pip[tid * wpb + q];
-    }
-    const double Fk = 0.5 * (sc->xnorm2[tid] + xx - 2.0 * ip);
+    const double Fk = 0.5 * (x2 + fk[tid] - 2.0 * rk[tid]);
+    const double rel = sqrt(fmax(2.0 * Fk, 0.0) * ix2);
     sc->Fk[tid] = Fk;
-    sc->relk[tid] = sqrt(fmax(2.0 * Fk, 0.0) * sc->inv_xnorm2[tid]);
+    sc->relk[tid] = rel;
+    fk[tid] = Fk;
+    rk[tid] = rel;
   }
-  __threadfence_block();
   __syncthreads();
   if (tid < 32) {
     double F = 0.0, rel = 0.0;
     for (int q = tid; q < K; q += 32) {
-      F += sc->Fk[q];
-      rel += sc->relk[q];
+      F += fk[q];
+      rel += rk[q];
     }
     for (int o = 16; o > 0; o >>= 1) {
       F += __shfl_xor_sync(0xffffffffu, F, o);
@@ -973,12 +1023,19 @@ __device__ void update_objective_tail(const UpdArgs<T>& a, int tid, int NT) {
   }
 }
 
+// Shared memory the objective tail needs (it reuses the update's).
+__host__ __device__ constexpr size_t objective_tail_smem(int K, int RP) {
+  return ((size_t)K * RP * RP + (size_t)K * RP + 2 * (size_t)K) * sizeof(double);
+}
+
 // The same update with one thread per (column c, block k, row y): the loads
 // of a pass are issued together, the shared-column gradient sum is formed in
 // shared memory in block order, and the CTA's new rows stay in shared memory
 // for the Gram chunk values.
 template <typename T, int RP>
 __global__ void __launch_bounds__(512) k_update_kp(const __grid_constant__ UpdArgs<T> a) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int K = a.K, Ln = a.Ln, n = a.n;
   const int c = threadIdx.x, k = threadIdx.y, y = threadIdx.z, TY = blockDim.z;
@@ -989,6 +1046,8 @@ __global__ void __launch_bounds__(512) k_update_kp(const __grid_constant__ UpdAr
   T* gC = uh + (size_t)TY * K * RP;           // [TY][K][RP]
   T* nvs = gC + (size_t)TY * K * RP;          // [K][gr][RP]
   T* mvs = nvs + (size_t)K * a.gr * RP;        // [K][gr][RP], with the fused objective
+  // with the fused objective: H^(n,k) in FP64, then H * (this CTA's Gram chunk)
+  double* xsb = reinterpret_cast<double*>(mvs + (size_t)K * a.gr * RP);  // [K][RP][RP]
   __shared__ T wsh[CNCPD_KMAX + 1];
   __shared__ T Lsh[CNCPD_KMAX];
   __shared__ T LCsh;
@@ -998,6 +1057,19 @@ __global__ void __launch_bounds__(512) k_update_kp(const __grid_constant__ UpdAr
   const int R = a.R[k];
   const int64_t I = a.I[k];
 
+  // the rows of the first pass, loaded before anything else (the stores of
+  // the staging below would otherwise keep these loads behind them)
+  T u1_0 = T(0), u2_0 = T(0), mv_0 = T(0);
+  {
+    const int64_t i = row0 + y;
+    if (y < a.gr && i < I && c < R) {
+      const size_t off = (size_t)i * R + c;
+      u1_0 = a.U1[k][off];
+      u2_0 = a.U2[k][off];
+      mv_0 = a.part[0] ? sum_splits<T>(a.part[k] + off, a.nsplit[k], I * R) : a.M[k][off];
+    }
+  }
+
   // H of every block (zero-padded to RP x RP)
 #pragma unroll 4
   for (int e = tid; e < K * RP * RP; e += NT) {
@@ -1005,6 +1077,7 @@ __global__ void __launch_bounds__(512) k_update_kp(const __grid_constant__ UpdAr
     const int ra = q / RP, rb = q % RP;
     const int Rk = a.R[kk];
     Hs[e] = (ra < Rk && rb < Rk) ? a.H[kk][ra * Rk + rb] : T(0);
+    if (a.obj) xsb[e] = (ra < Rk && rb < Rk) ? a.H64[(size_t)kk * a.rr + ra * Rk + rb] : 0.0;
   }
   // extrapolation weights (Eqs. eqextrawu and reading R3), one per block
   if (tid <= K) {
@@ -1032,17 +1105,18 @@ __global__ void __launch_bounds__(512) k_update_kp(const __grid_constant__ UpdAr
     const int64_t i = row0 + p0 + y;
     const bool valid = inchunk && i < I && c < R;
     const size_t off = valid ? (size_t)i * R + c : 0;
-    const T u1 = valid ? a.U1[k][off] : T(0);
-    const T u2 = valid ? a.U2[k][off] : T(0);
-    T mv = T(0);
-    if (a.part[0]) {
-      if (valid) {
-        mv = sum_splits<T>(a.part[k] + off, a.nsplit[k], I * R);
-        a.M[k][off] = mv;
-      }
+    T u1, u2, mv;
+    if (p0 == 0) {
+      u1 = u1_0;
+      u2 = u2_0;
+      mv = mv_0;
     } else {
-      mv = valid ? a.M[k][off] : T(0);
+      u1 = valid ? a.U1[k][off] : T(0);
+      u2 = valid ? a.U2[k][off] : T(0);
+      mv = T(0);
+      if (valid) mv = a.part[0] ? sum_splits<T>(a.part[k] + off, a.nsplit[k], I * R) : a.M[k][off];
     }
+    if (a.part[0] && valid) a.M[k][off] = mv;
     if (a.obj && inchunk) mvs[((size_t)k * a.gr + p0 + y) * RP + c] = mv;
     __syncthreads();  // weights and H staged; the previous pass is done with uh / gC
     const T w = (c < Ln) ? wsh[K] : wsh[k];
@@ -1103,6 +1177,9 @@ __global__ void __launch_bounds__(512) k_update_kp(const __grid_constant__ UpdAr
       T gv = T(0);
       for (int ii = 0; ii < rows; ++ii) gv = fma(Uk[ii * RP + ra], Uk[ii * RP + rb], gv);
       a.Gp[((size_t)kk * a.gnc + blockIdx.x) * a.rr + ra * Rk + rb] = gv;
+      if (a.obj) xsb[e] *= (double)gv;
+    } else if (a.obj) {
+      xsb[e] = 0.0;
     }
   }
   if (!a.obj) return;
@@ -1127,13 +1204,26 @@ __global__ void __launch_bounds__(512) k_update_kp(const __grid_constant__ UpdAr
     }
     a.dotp[((size_t)blockIdx.x * K + k) * RP + c] = s;
   }
+  {
+    // this CTA's share of ||X_hat^(k)||^2 = <H^(n,k), G^(n,k)>, one warp per
+    // block in a fixed order (xsb was completed before the barrier above)
+    const int warp = tid >> 5, lane = tid & 31, nw = NT >> 5;
+    if (warp < nw) {
+      for (int kk = warp; kk < K; kk += nw) {
+        double v = 0.0;
+        for (int q = lane; q < RP * RP; q += 32) v += xsb[(size_t)kk * RP * RP + q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) a.xxp[(size_t)blockIdx.x * K + kk] = v;
+      }
+    }
+  }
   __threadfence();
   __syncthreads();
   if (tid == 0) is_last = (atomicAdd(&sc->done_counter[1], 1) == (int)gridDim.x - 1);
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  update_objective_tail<T, RP>(a, tid, NT);
+  update_objective_tail<T, RP>(a, tid, NT, sm_raw);
 }
 
 // Shared memory of the block-parallel update with the fused objective (the
@@ -1151,7 +1241,11 @@ static size_t fused_objective_smem(const DevDesc& hd, int RP) {
   // the last CTA evaluates the objective with at least two whole warps per
   // block; with fewer the separate objective kernel (one CTA per block) is faster
   if ((RP * hd.K * geo.ty) / 32 < 2 * hd.K) return 0;
-  const size_t smem = geo.smem + (size_t)hd.K * geo.gr * RP * sizeof(T);
+  // the tail reads the CTAs' shares through a K x RP^2 buffer
+  if (hd.gnc[n] > RP * RP) return 0;
+  const size_t smem = std::max<size_t>(geo.smem + (size_t)hd.K * geo.gr * RP * sizeof(T) +
+                                           (size_t)hd.K * RP * RP * sizeof(double),
+                                       objective_tail_smem(hd.K, RP));
   return smem <= 200 * 1024 ? smem : 0;
 }
 
@@ -1203,7 +1297,10 @@ static cudaError_t update_impl(const LaunchCfg& c, const DevDesc& hd, int n, int
     a.N = hd.N;
     a.inv_K = 1.0 / hd.K;
     a.dotp = reinterpret_cast<T*>(hd.dotp);
+    a.xxp = hd.xxp;
+    a.gram_last = use_core;
     a.G = hd.Gbase;
+    a.H64 = hd.H64base;
     a.hm = hd.hm;
   }
   if (geo.kp) {
@@ -1211,7 +1308,8 @@ static cudaError_t update_impl(const LaunchCfg& c, const DevDesc& hd, int n, int
     cudaError_t e = allow_smem(k_update_kp<T, RP>, smem);
     if (e != cudaSuccess) return e;
     carve<k_update_kp<T, RP>>();
-    k_update_kp<T, RP><<<grid, dim3(RP, hd.K, geo.ty), smem, c.stream>>>(a);
+    e = launch_pdl(k_update_kp<T, RP>, dim3(grid), dim3(RP, hd.K, geo.ty), smem, c.stream, a);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
   }
   size_t dyn = 0;
@@ -1223,7 +1321,8 @@ static cudaError_t update_impl(const LaunchCfg& c, const DevDesc& hd, int n, int
   cudaError_t e = allow_smem(k_update<T, RP>, dyn);
   if (e != cudaSuccess) return e;
   carve<k_update<T, RP>>();
-  k_update<T, RP><<<grid, dim3(RP, UpdCfg<T, RP>::ROWS), dyn, c.stream>>>(a);
+  e = launch_pdl(k_update<T, RP>, dim3(grid), dim3(RP, UpdCfg<T, RP>::ROWS), dyn, c.stream, a);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -1252,6 +1351,8 @@ cudaError_t launch_update(const LaunchCfg& c, const DevDesc* dd, const DevDesc& 
 // ---------------------------------------------------------------------------
 template <typename T, int RP>
 __global__ void __launch_bounds__(256) k_objective(const __grid_constant__ ObjArgs<T> a) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int Y = 256 / RP;
   constexpr int NT = RP * Y;
   const int tid = threadIdx.x;
@@ -1442,7 +1543,10 @@ static cudaError_t objective_impl(const LaunchCfg& c, const DevDesc& hd, int com
     a.U[k] = reinterpret_cast<const T*>(hd.U1[k][n]);
   }
   carve<k_objective<T, RP>>();
-  k_objective<T, RP><<<hd.K, 256, 0, c.stream>>>(a);
+  {
+    cudaError_t eo = launch_pdl(k_objective<T, RP>, dim3(hd.K), dim3(256), 0, c.stream, a);
+    if (eo != cudaSuccess) return eo;
+  }
   return cudaGetLastError();
 }
 
@@ -1464,6 +1568,8 @@ cudaError_t launch_objective(const LaunchCfg& c, const DevDesc* dd, const DevDes
 // ---------------------------------------------------------------------------
 template <int RP>
 __global__ void __launch_bounds__(256) k_core_update(const DevDesc* __restrict__ d, int use_w, double delta_w) {
+  pdl_wait();
+  pdl_trigger();
   const int k = blockIdx.x;
   const int R = d->R[k], N = d->N;
   DevScalars* sc = d->sc;
@@ -1529,6 +1635,8 @@ struct IterArgs {
 };
 
 __global__ void __launch_bounds__(1024) k_iter_begin(const __grid_constant__ IterArgs a) {
+  pdl_wait();
+  pdl_trigger();
   DevScalars* sc = a.sc;
   const int K = a.K, N = a.N;
   const int tid = threadIdx.x;
@@ -1561,6 +1669,8 @@ __global__ void __launch_bounds__(1024) k_iter_begin(const __grid_constant__ Ite
 }
 
 __global__ void k_redo_prepare(const DevDesc* __restrict__ d) {
+  pdl_wait();
+  pdl_trigger();
   DevScalars* sc = d->sc;
   const int K = d->K;
   for (int e = threadIdx.x; e < K * CNCPD_RMAX; e += blockDim.x) {
