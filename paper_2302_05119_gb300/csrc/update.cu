@@ -117,17 +117,12 @@ __device__ double lmax_rp(const double* Hs, int R, LmaxSmem<RP>* s) {
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
   const int nt = blockDim.x * blockDim.y;
   __syncthreads();
-  if (tid == 0) {  // one thread forms the trace and its inverse
-    float t = 0.f;
-    for (int i = 0; i < R; ++i) t += s->Hf[i * R + i];
-    s->red[0] = t;
-    s->red[1] = (t > 0.f && isfinite(t)) ? 1.f / t : 0.f;
-  }
-  __syncthreads();
-  const float tr = s->red[0];
+  // every thread forms the trace (the same sum in the same order) and its inverse
+  float tr = 0.f;
+  for (int i = 0; i < R; ++i) tr += s->Hf[i * R + i];
   if (!isfinite(tr)) return (double)tr;
   if (!(tr > 0.f)) return 0.0;
-  const float itr = s->red[1];
+  const float itr = 1.f / tr;
   for (int e = tid; e < RR; e += nt) {
     const int i = e / RP, j = e % RP;
     s->A[e] = (i < R && j < R) ? s->Hf[i * R + j] * itr : 0.f;
@@ -557,7 +552,7 @@ __global__ void __launch_bounds__(256) k_level2_pair(const __grid_constant__ Pai
 
 // CTAs [0, K): H and L of mode n, block blockIdx.x; the rest: level 2.
 template <typename T, int RP>
-__global__ void __launch_bounds__(256) k_mode_prep(const __grid_constant__ LipArgs<T> la,
+__global__ void __launch_bounds__(256, 4) k_mode_prep(const __grid_constant__ LipArgs<T> la,
                                                    const __grid_constant__ PairArgs<T> pa) {
   pdl_wait();
   pdl_trigger();
@@ -1052,21 +1047,31 @@ __global__ void __launch_bounds__(512) k_update_kp(const __grid_constant__ UpdAr
   __shared__ T Lsh[CNCPD_KMAX];
   __shared__ T LCsh;
   __shared__ int is_last;
+  double LCd = 0.0;  // sum_k L^(n,k), held by thread K until the end of the kernel
   DevScalars* sc = a.sc;
   const int64_t row0 = (int64_t)blockIdx.x * a.gr;
   const int R = a.R[k];
   const int64_t I = a.I[k];
 
-  // the rows of the first pass, loaded before anything else (the stores of
-  // the staging below would otherwise keep these loads behind them)
+  // The rows of the first pass are loaded before anything else, and with at
+  // most 32 split-K partials those are loaded too (added after the staging
+  // below, so that every load of the prologue is in flight at once).
   T u1_0 = T(0), u2_0 = T(0), mv_0 = T(0);
-  {
-    const int64_t i = row0 + y;
-    if (y < a.gr && i < I && c < R) {
-      const size_t off = (size_t)i * R + c;
-      u1_0 = a.U1[k][off];
-      u2_0 = a.U2[k][off];
-      mv_0 = a.part[0] ? sum_splits<T>(a.part[k] + off, a.nsplit[k], I * R) : a.M[k][off];
+  T pv[32];
+  const int64_t i_0 = row0 + y;
+  const bool valid_0 = y < a.gr && i_0 < I && c < R;
+  const size_t off_0 = valid_0 ? (size_t)i_0 * R + c : 0;
+  const int ns_0 = a.part[0] ? a.nsplit[k] : 0;
+  if (valid_0) {
+    u1_0 = a.U1[k][off_0];
+    u2_0 = a.U2[k][off_0];
+    if (!a.part[0]) {
+      mv_0 = a.M[k][off_0];
+    } else if (ns_0 <= 32) {
+      const T* pp = a.part[k] + off_0;
+      const int64_t stride = I * R;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) pv[j] = pp[(int64_t)min(j, ns_0 - 1) * stride];  // clamped: no predicate
     }
   }
 
@@ -1093,13 +1098,21 @@ __global__ void __launch_bounds__(512) k_update_kp(const __grid_constant__ UpdAr
       for (int kk = 0; kk < K; ++kk) LC += sc->Lcur_u[n][kk];
       wsh[K] = extrap_weight<T>(w_hat, have_prev, sc->LCprev[n], LC, a.delta_w);
       LCsh = LC > 0.0 ? (T)LC : T(0);
-      if (blockIdx.x == 0) {
-        sc->LCcur[n] = LC;
-        sc->have_cur = 1;
-      }
+      LCd = LC;
     }
   }
   const T lam = (a.use_core && c < R) ? (T)sc->lam1[k][c] : T(1);
+  if (valid_0 && a.part[0]) {
+    if (ns_0 <= 32) {
+      T acc = T(0);
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j < ns_0) acc += pv[j];
+      mv_0 = acc;
+    } else {
+      mv_0 = sum_splits<T>(a.part[k] + off_0, ns_0, I * R);
+    }
+  }
   for (int p0 = 0; p0 < a.gr; p0 += TY) {
     const bool inchunk = p0 + y < a.gr;
     const int64_t i = row0 + p0 + y;
@@ -1163,6 +1176,10 @@ __global__ void __launch_bounds__(512) k_update_kp(const __grid_constant__ UpdAr
         nvs[((size_t)kk * a.gr + p0 + y) * RP + c] = nv;
       }
     }
+  }
+  if (blockIdx.x == 0 && tid == K) {  // the sweep's record of sum_k L (read by later kernels only)
+    sc->LCcur[n] = LCd;
+    sc->have_cur = 1;
   }
   if (!a.Gp) return;
   __syncthreads();
