@@ -209,11 +209,15 @@ int dalloc(cncpd_ctx* c, void** p, size_t bytes) {
 int setup_umma(cncpd_ctx* c, DevDesc& d, int Rmax) {
   d.use_umma = 0;
   d.umma_np = 0;
+  d.umma_planes = 1;
   const int np = umma_np(Rmax);
-  if (!c->opts.tensor_cores || c->st != ST_BF16 || d.N != 3 || d.h != 2 || np == 0 || !d.tmap_trail ||
+  const bool x2 = c->st == ST_BF16X2;
+  if (!c->opts.tensor_cores || !(c->st == ST_BF16 || x2) || d.N != 3 || d.h != 2 || np == 0 ||
       !tensor_map_encoder())
     return CNCPD_OK;
-  std::vector<CUtensorMap> maps(3 * CNCPD_KMAX);
+  if (!x2 && !d.tmap_trail) return CNCPD_OK;
+  // [lead3 | Bt | Bl | trail hi | trail lo | lead3 lo] (the last three with hi + lo storage)
+  std::vector<CUtensorMap> maps(6 * CNCPD_KMAX);
   for (int k = 0; k < d.K; ++k) {
     const int64_t J = d.trail_cols[k], I1 = d.dims[k][1], I0 = d.dims[k][0];
     d.bt_pitch[k] = (J + 7) / 8 * 8;
@@ -226,6 +230,12 @@ int setup_umma(cncpd_ctx* c, DevDesc& d, int Rmax) {
         !encode_map(&maps[2 * CNCPD_KMAX + k], d.Bl[k], ST_BF16, 3 * np, I1, d.bl_pitch[k], 64, 3 * np,
                     CU_TENSOR_MAP_SWIZZLE_128B))
       return CNCPD_OK;
+    if (x2 && (!encode_map(&maps[3 * CNCPD_KMAX + k], d.X[k], ST_BF16, d.lead_rows[k], J, d.pitch[k], 64, 256,
+                           CU_TENSOR_MAP_SWIZZLE_128B) ||
+               !encode_map(&maps[4 * CNCPD_KMAX + k], d.Xlo[k], ST_BF16, d.lead_rows[k], J, d.pitch[k], 64, 256,
+                           CU_TENSOR_MAP_SWIZZLE_128B) ||
+               !encode_x3(&maps[5 * CNCPD_KMAX + k], d.Xlo[k], J, I1, I0, d.pitch[k])))
+      return CNCPD_OK;
   }
   CUtensorMap* dm = nullptr;
   TRY(dalloc(c, (void**)&dm, maps.size() * sizeof(CUtensorMap)));
@@ -234,6 +244,12 @@ int setup_umma(cncpd_ctx* c, DevDesc& d, int Rmax) {
   d.tmap_lead3 = dm;
   d.tmap_bt = dm + CNCPD_KMAX;
   d.tmap_bl = dm + 2 * CNCPD_KMAX;
+  if (x2) {
+    d.tmap_trail = dm + 3 * CNCPD_KMAX;
+    d.tmap_trail_lo = dm + 4 * CNCPD_KMAX;
+    d.tmap_lead3_lo = dm + 5 * CNCPD_KMAX;
+    d.umma_planes = 2;
+  }
   d.umma_np = np;
   d.use_umma = 1;
   return CNCPD_OK;

@@ -157,6 +157,11 @@ struct DevDesc {
   const CUtensorMap* tmap_lead3;
   const CUtensorMap* tmap_bt;
   const CUtensorMap* tmap_bl;
+  // BF16 hi + lo storage: the lo planes' maps; both planes stream through the
+  // same MMAs (the lo plane's K chunks follow the hi plane's, same B operand)
+  const CUtensorMap* tmap_trail_lo;
+  const CUtensorMap* tmap_lead3_lo;
+  int umma_planes, pad4;               // 1 (BF16) or 2 (BF16 hi + lo)
 };
 
 constexpr int CROSS_ROWS = 32;

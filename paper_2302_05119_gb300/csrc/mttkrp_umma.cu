@@ -17,6 +17,10 @@
 // each slab by U0[i0, :] and add the slabs of a unit in registers, in slab
 // order, and write the unit's split-K partial.
 //
+// BF16 hi + lo storage (two planes, x = hi + lo) runs the same MMAs over
+// twice the K chunks: the lo plane's chunks follow the hi plane's with the
+// same B operand, into the same accumulator.
+//
 // Warp roles (192 threads): 0 TMA producer, 1 MMA issuer and TMEM owner,
 // 2-5 epilogue (warp w reads TMEM lanes 32 (w mod 4) .. + 31).  Each mbarrier
 // is waited on by one role that sees every phase in order, so a parity wait
@@ -171,6 +175,7 @@ __global__ void __launch_bounds__(U_THREADS, 1) k_trailing_umma(const DevDesc* _
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int* err = &d->sc->timeout;
   const int K = d->K;
+  const int planes = d->umma_planes;
   const UUnits us(d->lt_sched, d->lt_prefix[K]);
 
   if (warp == 0) {
@@ -186,15 +191,18 @@ __global__ void __launch_bounds__(U_THREADS, 1) k_trailing_umma(const DevDesc* _
         const int row0 = (g - d->lt_prefix[k]) * 256;
         const int nch = (int)((d->trail_cols[k] + 63) / 64);
         prefetch_tmap(&d->tmap_trail[k]);
+        if (planes > 1) prefetch_tmap(&d->tmap_trail_lo[k]);
         prefetch_tmap(&d->tmap_bt[k]);
-        for (int c = 0; c < nch; ++c, ++it) {
+        // hi + lo storage: the lo plane's chunks follow the hi plane's
+        for (int c = 0; c < planes * nch; ++c, ++it) {
           const int s = it % ST;
+          const int cc = c < nch ? c : c - nch;
           if (!mbar_wait(smem_u32(&bars.empty[s]), ((it / ST) & 1) ^ 1, err)) { ok = false; break; }
           const uint32_t sa = smem_u32(base + s * S::STAGE);
           const uint32_t fb = smem_u32(&bars.full[s]);
           mbar_arrive_expect_tx(fb, S::STAGE);
-          tma_load_2d_hint(sa, &d->tmap_trail[k], fb, c * 64, row0, pol);
-          tma_load_2d(sa + S::A_BYTES, &d->tmap_bt[k], fb, c * 64, 0);
+          tma_load_2d_hint(sa, c < nch ? &d->tmap_trail[k] : &d->tmap_trail_lo[k], fb, cc * 64, row0, pol);
+          tma_load_2d(sa + S::A_BYTES, &d->tmap_bt[k], fb, cc * 64, 0);
         }
       }
       for (uint32_t i = it > (uint32_t)ST ? it - ST : 0; i < it; ++i)
@@ -214,7 +222,7 @@ __global__ void __launch_bounds__(U_THREADS, 1) k_trailing_umma(const DevDesc* _
         const int b = tc & 1;
         if (!mbar_wait(smem_u32(&bars.tempty[b]), ((tc >> 1) & 1) ^ 1, err)) { ok = false; break; }
         tc_fence_after();
-        for (int c = 0; c < nch; ++c, ++it) {
+        for (int c = 0; c < planes * nch; ++c, ++it) {
           const int s = it % ST;
           if (!mbar_wait(smem_u32(&bars.full[s]), (it / ST) & 1, err)) { ok = false; break; }
           tc_fence_after();
@@ -300,6 +308,7 @@ __global__ void __launch_bounds__(U_THREADS, 1) k_lead_umma(const DevDesc* __res
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int* err = &d->sc->timeout;
   const int K = d->K;
+  const int planes = d->umma_planes;
   const UUnits us(d->tt_sched, d->tt_prefix[K]);
 
   if (warp == 0) {
@@ -320,18 +329,21 @@ __global__ void __launch_bounds__(U_THREADS, 1) k_lead_umma(const DevDesc* __res
         const int a0 = split * per, a1 = min(I0, a0 + per);
         const int nst = (I1 + 63) / 64;
         prefetch_tmap(&d->tmap_lead3[k]);
+        if (planes > 1) prefetch_tmap(&d->tmap_lead3_lo[k]);
         prefetch_tmap(&d->tmap_bl[k]);
         for (int i0 = a0; i0 < a1 && ok; ++i0)
-          for (int st = 0; st < nst; ++st, ++it) {
+          for (int st = 0; st < planes * nst; ++st, ++it) {  // hi + lo: the lo plane's stages follow
             const int s = it % ST;
+            const int ss = st < nst ? st : st - nst;
+            const CUtensorMap* xm = st < nst ? &d->tmap_lead3[k] : &d->tmap_lead3_lo[k];
             if (!mbar_wait(smem_u32(&bars.empty[s]), ((it / ST) & 1) ^ 1, err)) { ok = false; break; }
             const uint32_t sa = smem_u32(base + s * S::STAGE);
             const uint32_t fb = smem_u32(&bars.full[s]);
             mbar_arrive_expect_tx(fb, S::STAGE);
 #pragma unroll
             for (int qb = 0; qb < 4; ++qb)
-              tma_load_3d_hint(sa + qb * 8192, &d->tmap_lead3[k], fb, ctile * 256 + qb * 64, st * 64, i0, pol);
-            tma_load_2d(sa + S::A_BYTES, &d->tmap_bl[k], fb, st * 64, 0);
+              tma_load_3d_hint(sa + qb * 8192, xm, fb, ctile * 256 + qb * 64, ss * 64, i0, pol);
+            tma_load_2d(sa + S::A_BYTES, &d->tmap_bl[k], fb, ss * 64, 0);
           }
       }
       for (uint32_t i = it > (uint32_t)ST ? it - ST : 0; i < it; ++i)
@@ -357,7 +369,7 @@ __global__ void __launch_bounds__(U_THREADS, 1) k_lead_umma(const DevDesc* __res
           const int b = sc & 1;
           if (!mbar_wait(smem_u32(&bars.tempty[b]), ((sc >> 1) & 1) ^ 1, err)) { ok = false; break; }
           tc_fence_after();
-          for (int st = 0; st < nst; ++st, ++it) {
+          for (int st = 0; st < planes * nst; ++st, ++it) {
             const int s = it % ST;
             if (!mbar_wait(smem_u32(&bars.full[s]), (it / ST) & 1, err)) { ok = false; break; }
             tc_fence_after();

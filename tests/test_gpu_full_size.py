@@ -106,17 +106,21 @@ def test_full_size_objective_and_invariants_sim_256cube():
     assert s["F"] == pytest.approx(F, rel=2e-5)
 
 
+_ORACLE_RUNS = {}
+
+
 @pytest.mark.parametrize("name,storage,tol", [
     ("sim_256cube", "f32", 1e-5),
     ("bf16_512x512x256", "bf16", 3e-3),
+    ("bf16_512x512x256", "bf16x2", 3e-4),
 ])
 def test_full_size_first_iterations_match_oracle(name, storage, tol):
     """The first 10 iterations at the benchmark's full size, in its launch
     configuration (graphs, profile events, TMA or tensor-core passes):
     every factor after every iteration within the stated relative Frobenius
-    error of the FP64 oracle (FP32 storage: 1e-5; BF16 storage: 3e-3, the
-    oracle running on the unquantised FP32 data), and the same re-update
-    decisions."""
+    error of the FP64 oracle (FP32 storage: 1e-5; BF16 storage: 3e-3; BF16
+    hi + lo storage: 3e-4; the oracle running on the unquantised FP32 data),
+    and the same re-update decisions."""
     import torch
 
     import synth
@@ -133,9 +137,12 @@ def test_full_size_first_iterations_match_oracle(name, storage, tol):
         snaps_g.append(m.factors(np.float64))
     m.close()
     torch.cuda.empty_cache()
-    X64 = [X.astype(np.float64) for X in Xs]
-    del Xs
-    snaps_o, res_o = run_oracle_steps(X64, [w.R] * w.K, w.L, U0, 10)
+    if name not in _ORACLE_RUNS:  # the BF16 and hi + lo arms share the oracle's run on the FP32 data
+        X64 = [X.astype(np.float64) for X in Xs]
+        del Xs
+        _ORACLE_RUNS[name] = run_oracle_steps(X64, [w.R] * w.K, w.L, U0, 10)
+        del X64
+    snaps_o, res_o = _ORACLE_RUNS[name]
     assert redo_g == res_o["hist"]["redo"]
     worst = 0.0
     for it in range(10):

@@ -503,3 +503,40 @@ def test_load_state_on_the_same_handle():
         for n in range(3):
             assert np.array_equal(m.factor(k, n, np.float32), U6[k][n])
     m.close()
+
+
+def _bf16x2_exact(a, rng):
+    """Values x = hi + lo with hi a BF16 number and lo a BF16 number below a
+    quarter of hi's last place, so the hi + lo storage split reproduces x
+    exactly (and the lo plane is not zero)."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    hi = _to_bf16(a)
+    lo = _to_bf16(0.25 * (a - hi))
+    return (hi + lo).astype(np.float32)
+
+
+@pytest.mark.parametrize("dims,R", [
+    ([(70, 37, 150), (9, 64, 130)], 10),
+    ([(33, 41, 200)], 20),
+    ([(300, 260, 136)], 12),
+    ([(5, 6, 7, 8)], 12),
+])
+@pytest.mark.parametrize("tensor_cores", [True, False])
+def test_mttkrp_bf16x2_storage_exact_inputs(dims, R, tensor_cores):
+    """BF16 hi + lo storage of values whose split is exact: the MTTKRP (both
+    planes, FP32 accumulation; on the tcgen05 passes for third-order tensors
+    with R <= 32, the lo plane's K chunks after the hi plane's) matches the
+    FP64 oracle to FP32 accumulation accuracy."""
+    rng = np.random.default_rng(R * 11 + len(dims))
+    Xs = [_bf16x2_exact(rng.random(d), rng) for d in dims]
+    assert any(np.any(X != _to_bf16(X)) for X in Xs)  # the lo plane carries something
+    N = len(dims[0])
+    U = [[rng.random((I, R)).astype(np.float32) for I in d] for d in dims]
+    m = _P().CoupledNCP(Xs, R, [0] * N, storage="bf16x2", tensor_cores=tensor_cores)
+    m.set_factors(U)
+    for k in range(len(dims)):
+        for n in range(N):
+            got = m.mttkrp(k, n)
+            want = O.mttkrp(Xs[k].astype(np.float64), [A.astype(np.float64) for A in U[k]], n)
+            assert rel_fro(got, want) <= 2e-6, (k, n)
+    m.close()
