@@ -80,7 +80,12 @@ typedef struct {
                         replay a graph without event nodes */
   int tensor_cores;  /* 1: BF16-stored third-order tensors with ranks up to 32 stream
                         through tcgen05 tensor-core passes; 0: CUDA-core passes only */
-  int reserved[5];
+  int autotune;      /* 1: the first cncpd_step / cncpd_fit of a handle times every
+                        candidate split-K plan of the lead-mode pass (1, 2, 3, 4, 6 or 8
+                        units per SM) with CUDA events and keeps the fastest; the winner
+                        is cached per problem shape for later handles of the process.
+                        0: the plan of the cost model only */
+  int reserved[4];
 } cncpd_opts;
 
 /* Results of a solver call. */
@@ -102,7 +107,10 @@ typedef struct {
   double trail_ms;    /* part of stream_ms spent in the trailing-mode contraction */
   double lead_ms;     /* part of stream_ms spent in the lead-mode contraction */
   long long launches; /* kernels launched by this call */
-  int reserved[4];
+  int lead_plan;      /* lead-pass units per SM in use (chosen by the measuring tuner when
+                         opts.autotune is set; 0: not a persistent-pass problem) */
+  int lead_plan_tuned;/* 1 if that plan was measured (this call or a cached earlier one) */
+  int reserved[2];
 } cncpd_stats;
 
 /* Fill *opts with the defaults listed above. */

@@ -15,6 +15,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <functional>
+#include <map>
+#include <mutex>
 #include <queue>
 #include <string>
 #include <vector>
@@ -120,6 +122,12 @@ struct cncpd_ctx {
   HostMirror* hm_dev = nullptr;
   cudaStream_t side = nullptr;                // branch for work independent of a tensor pass
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+
+  // lead-pass split plan: units per SM in use, whether it was measured, and
+  // the partial-sum capacity (elements) every candidate plan fits in
+  int lead_mult = 0;
+  bool lead_tuned = false;
+  size_t partial_cap = 0;
 
   // LRA
   bool lra = false;
@@ -368,14 +376,16 @@ std::vector<int64_t> lead_unit_costs(const cncpd_ctx* c, const DevDesc& d) {
 // a longest-first unit list) the plan is the one, among about 1, 2, 3, 4, 6
 // or 8 units per SM, whose list has the smallest largest load; ties go to
 // fewer units (fewer split-K partials to add up).
-void plan_lead_splits(cncpd_ctx* c, DevDesc& d, int RP, int fp64, size_t* partial_elems) {
+constexpr int kLeadMults[] = {1, 2, 3, 4, 6, 8};
+
+int plan_lead_splits(cncpd_ctx* c, DevDesc& d, int RP, int fp64, size_t* partial_elems) {
   if (!d.use_tma && !d.use_umma) {
     plan_lead_units(c, d, RP, fp64, (int64_t)c->num_sms * 2, partial_elems);
-    return;
+    return 0;
   }
   int best = 1;
   int64_t best_span = -1;
-  for (int mult : {1, 2, 3, 4, 6, 8}) {
+  for (int mult : kLeadMults) {
     plan_lead_units(c, d, RP, fp64, (int64_t)c->num_sms * mult, partial_elems);
     const std::vector<int64_t> cost = lead_unit_costs(c, d);
     const int P = std::min<int>((int)cost.size(), c->num_sms);
@@ -386,6 +396,21 @@ void plan_lead_splits(cncpd_ctx* c, DevDesc& d, int RP, int fp64, size_t* partia
     }
   }
   plan_lead_units(c, d, RP, fp64, (int64_t)c->num_sms * best, partial_elems);
+  return best;
+}
+
+// Partial-sum elements of the largest candidate lead plan.
+size_t lead_partial_cap(cncpd_ctx* c, DevDesc d, int RP, int fp64) {
+  size_t cap = 0, pel = 0;
+  if (!d.use_tma && !d.use_umma) {
+    plan_lead_units(c, d, RP, fp64, (int64_t)c->num_sms * 2, &pel);
+    return pel;
+  }
+  for (int mult : kLeadMults) {
+    plan_lead_units(c, d, RP, fp64, (int64_t)c->num_sms * mult, &pel);
+    cap = std::max(cap, pel);
+  }
+  return cap;
 }
 
 void plan_trailing_tiles(DevDesc& d) {
@@ -818,9 +843,95 @@ int read_profile(cncpd_ctx* c, cncpd_stats* st, int set) {
   return CNCPD_OK;
 }
 
+// Measured choice of the lead pass's split-K plan.  Every candidate (1, 2,
+// 3, 4, 6 or 8 units per SM) is planned, its balanced unit list uploaded, and
+// the pass alone (no split reduction) run once to warm up and then three
+// times between CUDA events on the handle's stream; the fastest plan wins
+// (ties: fewer units).  The winner is cached per problem shape for the
+// process.  Runs before any graph is captured (graphs bake in the plan).
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune_cache;
+
+std::string shape_key(const cncpd_ctx* c) {
+  std::string k = std::to_string(c->st) + "/" + std::to_string(c->fp64) + "/" + std::to_string(c->num_sms) + "/" +
+                  std::to_string(c->hd.use_umma) + "/" + std::to_string(c->RP);
+  for (int b = 0; b < c->K; ++b) {
+    k += ";" + std::to_string(c->R[b]);
+    for (int n = 0; n < c->N; ++n) k += "," + std::to_string(c->dim(b, n));
+  }
+  return k;
+}
+
+int apply_lead_plan(cncpd_ctx* c, int mult) {
+  size_t pel = 0;
+  plan_lead_units(c, c->hd, c->RP, c->fp64, (int64_t)c->num_sms * mult, &pel);
+  if (pel > c->partial_cap) return set_err(CNCPD_ESTATE, "lead plan exceeds the partial-sum buffer");
+  TRY(plan_tma_schedules(c, c->hd));
+  TRY(upload_desc(c));
+  c->lead_mult = mult;
+  return CNCPD_OK;
+}
+
+int tune_lead(cncpd_ctx* c) {
+  c->lead_tuned = true;
+  if (!c->opts.autotune || c->lra || (!c->hd.use_tma && !c->hd.use_umma)) return CNCPD_OK;
+  const std::string key = shape_key(c);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) return apply_lead_plan(c, it->second);
+  }
+  destroy_graphs(c);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  int best = c->lead_mult;
+  float best_ms = -1.f;
+  int rc = CNCPD_OK;
+  for (int mult : kLeadMults) {
+    size_t pel = 0;
+    DevDesc probe = c->hd;
+    plan_lead_units(c, probe, c->RP, c->fp64, (int64_t)c->num_sms * mult, &pel);
+    if (pel > c->partial_cap) continue;
+    rc = apply_lead_plan(c, mult);
+    if (rc != CNCPD_OK) break;
+    float ms = 0.f;
+    for (int rep = 0; rep < 4 && rc == CNCPD_OK; ++rep) {
+      if (rep == 1 && cudaEventRecord(e0, c->stream) != cudaSuccess) rc = set_err(CNCPD_ECUDA, "event record failed");
+      if (rc == CNCPD_OK) rc = enqueue_lead(c, c->dd, c->hd, c->RP, c->d_red_prefix, 0);
+    }
+    if (rc != CNCPD_OK) break;
+    if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      rc = set_err(CNCPD_ECUDA, "autotune timing failed: %s", cudaGetErrorString(cudaGetLastError()));
+      break;
+    }
+    if (c->hs && c->sc) {  // a pass that timed out must not win
+      rc = enqueue_readback(c);
+      if (rc == CNCPD_OK) rc = sync(c);
+      if (rc == CNCPD_OK && c->hs->timeout) {
+        rc = timeout_error(c);
+        break;
+      }
+    }
+    if (best_ms < 0.f || ms < best_ms * 0.995f) {
+      best_ms = ms;
+      best = mult;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  TRY(rc);
+  TRY(apply_lead_plan(c, best));
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache[key] = best;
+  return CNCPD_OK;
+}
+
 int run_iterations(cncpd_ctx* c, int n_iters, bool use_eps, cncpd_stats* out) {
   cncpd_stats st{};
   const double t0 = now_s();
+  if (!c->lead_tuned) TRY(tune_lead(c));
   if (c->dirty) TRY(initialise(c));
   const double pb = c->lra ? 0.0 : 2.0 * pass_bytes(c);
   c->prof_runs = 0;  // the first sweep of every call records its pass times
@@ -874,6 +985,8 @@ int run_iterations(cncpd_ctx* c, int n_iters, bool use_eps, cncpd_stats* out) {
   TRY(sync(c));
   if (pending >= 0) TRY(read_profile(c, &st, pending));
   st.total_iters = c->total_iters;
+  st.lead_plan = c->lead_mult;
+  st.lead_plan_tuned = (c->opts.autotune && c->lead_mult > 0) ? 1 : 0;
   st.F = c->F_prev;
   st.relerr = c->rel_prev;
   st.fit = 1.0 - c->rel_prev;
@@ -938,6 +1051,7 @@ void cncpd_default_opts(cncpd_opts* o) {
   o->use_graph = 1;
   o->profile = 0;
   o->tensor_cores = 1;
+  o->autotune = 1;
 }
 
 const char* cncpd_last_error(void) { return g_err.c_str(); }
@@ -1200,10 +1314,11 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
   d.use_tma = (d.tmap_trail != nullptr) && tma_rank_supported(c->RP);
   CTRY(setup_umma(c, d, c->Rmax));
   size_t pel = 0;
-  plan_lead_splits(c, d, c->RP, c->fp64, &pel);
+  c->lead_mult = plan_lead_splits(c, d, c->RP, c->fp64, &pel);
   plan_trailing_tiles(d);
   CTRY(plan_tma_schedules(c, d));
-  CTRY(dalloc(c, &d.partial, pel * c->fsz));
+  c->partial_cap = std::max(pel, lead_partial_cap(c, d, c->RP, c->fp64));
+  CTRY(dalloc(c, &d.partial, c->partial_cap * c->fsz));
 
   {
     std::vector<int64_t> pre(K + 1, 0);
@@ -1528,7 +1643,7 @@ int cncpd_lra(cncpd_t h, const int* R_tilde, const void* const* Ut0, cncpd_dtype
   size_t pel = 0;
   a.use_tma = (a.tmap_trail != nullptr) && tma_rank_supported(h->RPt);
   TRY(setup_umma(h, a, rtmax));
-  plan_lead_splits(h, a, h->RPt, h->fp64, &pel);
+  (void)plan_lead_splits(h, a, h->RPt, h->fp64, &pel);
   plan_trailing_tiles(a);
   TRY(plan_tma_schedules(h, a));
   TRY(dalloc(h, &a.partial, pel * h->fsz));

@@ -42,6 +42,7 @@ def test_struct_layouts():
     assert (o.eps, o.max_it, o.lra_eps, o.lra_max_it) == (1e-8, 1000, 1e-4, 200)
     assert o.delta_w == 0.9999 and o.reupdate == 1 and o.storage == -1 and o.use_core == 0
     assert ctypes.sizeof(_lib.cncpd_opts) == 8 + 8 + 8 + 8 + 8 + 4 * 6 + 4 * 6
+    assert o.autotune == 1
 
 
 def test_argument_errors_without_gpu(lib):
