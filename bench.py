@@ -433,6 +433,7 @@ def run_ours(args):
             "reupdates": s["reupdates"], "fit": s["fit"], "lra": lra,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": s["launches"], "clocks": clk, "time_to_fit": ttf,
+            "lead_plan": {"units_per_sm": s["lead_plan"], "measured": bool(s["lead_plan_tuned"])},
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
