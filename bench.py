@@ -13,7 +13,10 @@ Prints one JSON line (rank 0).  The default line also carries a
 "time_to_fit" record on the precision workload (4 x 512 x 512 x 256, R = 20):
 seconds from cncpd_create on device-resident FP32 tensors until the global
 Fit, evaluated on the original FP32 tensors, is within 1e-4 of the FP64
-oracle's converged Fit, for FP32, BF16 and BF16 hi+lo storage.  The tensors (5 x 67 MB) exceed the 129 MB
+oracle's converged Fit, for FP32, BF16 and BF16 hi+lo storage, and a
+"workloads" record: iterations/s and the dominant pass's roofline on that
+workload in BF16 and BF16 hi+lo storage and on the 16 uneven fourth-order
+EEG-shaped blocks (FP32).  The tensors (5 x 67 MB) exceed the 129 MB
 L2, so no flush is needed between iterations.  --lra runs the low-rank
 approximation step of lraCoNCPD-APG (rank R~ of the workload) before the
 timed iterations, which then use the collapsed products.  --time-to-fit
@@ -168,7 +171,54 @@ def _fit_target(w):
     return rec
 
 
-def time_to_fit(name, arms, check_every=10, cap=2000, lra_check_every=100):
+def _pass_roofline(w, storage, s):
+    """(dominant pass, its algorithmic GB/s, fraction of the measured HBM peak)
+    from the CUDA-event pass times of a profiled step call."""
+    es = {"f32": 4, "bf16": 2, "bf16x2": 4}[storage]
+    h = (w.N + 1) // 2
+    R = w.ranks()
+    x_bytes = sum(w.elements()) * es
+    trail = x_bytes + sum((int(np.prod(d[:h])) + sum(d[h:])) * r * 4 for d, r in zip(w.dims, R))
+    lead = x_bytes + sum((int(np.prod(d[h:])) + sum(d[:h])) * r * 4 for d, r in zip(w.dims, R))
+    nl = max(1, s["stream_launches"] // 2)
+    t_trail, t_lead = s["trail_ms"] / nl, s["lead_ms"] / nl
+    kern, t, b = ("lead_contract", t_lead, lead) if t_lead >= t_trail else ("trailing_contract", t_trail, trail)
+    if s["stream_launches"] == 0 or t <= 0:
+        return None
+    peak, _ = _peaks()
+    gbs = b / (t / 1e3) / 1e9
+    return {"kernel": kern, "achieved_gbs": gbs, "frac": gbs / peak, "pass_ms": t, "algorithmic_bytes": b}
+
+
+def measure_workload(name, storage, Xd=None, steps=200, warmup=5):
+    """iterations/s (CUDA events around `steps` graph-replayed iterations) and
+    the dominant pass's roofline on one workload, inputs resident on the GPU."""
+    import torch
+    import paper_2302_05119_gb300 as P
+    import synth
+    w = _workload(name)
+    if Xd is None:
+        Xs, _ = synth.make_tensors(w, dtype=np.float32)
+        Xd = [torch.from_numpy(X).cuda() for X in Xs]
+        del Xs
+    m = P.CoupledNCP(Xd, w.R, w.L, profile=True, storage=storage)
+    m.set_factors(synth.init_factors(w.dims, w.R, w.seed))
+    m.step(warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    s = m.step(steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    m.close()
+    return {"workload": w.name, "storage": storage, "K": w.K, "R": w.R, "L": w.L,
+            "value": steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+            "roofline": _pass_roofline(w, storage, s), "lead_plan": s["lead_plan"]}
+
+
+def time_to_fit(name, arms, check_every=10, cap=2000, lra_check_every=100, Xd=None):
     """Wall time from cncpd_create on device-resident FP32 tensors to the
     first check at which the global Fit of the arm's factors, evaluated on
     the original FP32 tensors, is within 1e-4 of the target: the FP64
@@ -182,10 +232,11 @@ def time_to_fit(name, arms, check_every=10, cap=2000, lra_check_every=100):
     import paper_2302_05119_gb300 as P
     import synth
     w = _workload(name)
-    Xs, _ = synth.make_tensors(w, dtype=np.float32)
     U0 = synth.init_factors(w.dims, w.R, w.seed)
-    Xd = [torch.from_numpy(X).cuda() for X in Xs]
-    del Xs
+    if Xd is None:
+        Xs, _ = synth.make_tensors(w, dtype=np.float32)
+        Xd = [torch.from_numpy(X).cuda() for X in Xs]
+        del Xs
     rec = _fit_target(w)
     if rec is not None:
         target = {"fit": rec["fit"], "source": "FP64 oracle (tests/golden/fit_targets.json)",
@@ -236,7 +287,6 @@ def time_to_fit(name, arms, check_every=10, cap=2000, lra_check_every=100):
         out["arms"][key] = {"seconds": dt, "iterations": it, "fit_fp32_data": f, "fit_stored": f_stored,
                             "reached": bool(f >= bar), "lra_seconds": lra_s, "check_every": every}
     judge.close()
-    del Xd
     torch.cuda.empty_cache()
     base = out["arms"].get("f32")
     if base and base["reached"]:
@@ -382,7 +432,7 @@ def run_ours(args):
                 "other_kernel_ms": t_trail if kern == "lead_contract" else t_lead,
                 "algorithmic_bytes_per_launch": pass_bytes,
                 "timed_launches": nl,
-                "timing": "CUDA events on the launching stream around each pass, every 8th iteration of the timed region"}
+                "timing": "CUDA events on the launching stream around each pass of the first iteration of the timed region and every 8th one after it"}
     else:  # after the LRA step no iteration reads X
         roof = {"bound": "latency", "kernel": None, "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
                 "peak_source": peak_kind, "traffic": None,
@@ -409,10 +459,22 @@ def run_ours(args):
            "scope": "cncpd_create from pinned host tensors + set_factors + steps + factor copy-out, per job"}
 
     ttf = None
+    others = None
     if rank == 0 and ws == 1 and not args.no_time_to_fit:
         # the metric's second part: mixed precision against plain FP32 on the
-        # precision workload (512 x 512 x 256 x 4, R = 20), judged on the FP32 data
-        ttf = time_to_fit("bf16_512x512x256", [("f32", False), ("bf16", False), ("bf16x2", False)])
+        # precision workload (512 x 512 x 256 x 4, R = 20), judged on the FP32
+        # data; then the same data in BF16 and BF16 hi+lo storage, and the
+        # uneven fourth-order EEG-shaped blocks, for iterations/s and roofline
+        wp = _workload("bf16_512x512x256")
+        Xp, _ = synth.make_tensors(wp, dtype=np.float32)
+        Xpd = [torch.from_numpy(X).cuda() for X in Xp]
+        del Xp
+        ttf = time_to_fit(wp.name, [("f32", False), ("bf16", False), ("bf16x2", False)], Xd=Xpd)
+        others = [measure_workload(wp.name, st, Xd=Xpd) for st in ("bf16", "bf16x2")]
+        del Xpd
+        torch.cuda.empty_cache()
+        others.append(measure_workload("eeg_uneven_4th", "f32"))
+        torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -432,7 +494,7 @@ def run_ours(args):
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "reupdates": s["reupdates"], "fit": s["fit"], "lra": lra,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": s["launches"], "clocks": clk, "time_to_fit": ttf,
+            "gpu_launches": s["launches"], "clocks": clk, "time_to_fit": ttf, "workloads": others,
             "lead_plan": {"units_per_sm": s["lead_plan"], "measured": bool(s["lead_plan_tuned"])},
         }
         print(json.dumps(line), flush=True)

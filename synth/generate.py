@@ -86,6 +86,11 @@ def workload(name):
         K = int(name.split("_s")[1]) if "_s" in name else 20
         return Workload(name, [(100, 100, 100)] * K, 10, list(E1_PATTERNS[pat]), 20.0,
                         base + 10 + sorted(E1_PATTERNS).index(pat), iters=1000)
+    if name == "face_lra_400x400x160":
+        # the face shape scaled down (each mode by 2.5) so that the FP64 oracle
+        # can be run to convergence for its time-to-fit target
+        return Workload(name, [(400, 400, 160)] * 8, 20, [8, 0, 0], 20.0, base + 8,
+                        sparse_mode=0, density=0.1, iters=200, R_lra=30)
     if name == "erp_42x9x71x60":
         # ERP shape (Section IV-C): 42 blocks of 9 channels x 71 frequency
         # bins x 60 time points, R = 36, every column shared in every mode
@@ -112,7 +117,7 @@ def workload(name):
 
 
 WORKLOADS = ["small_40cube", "sim_256cube", "bf16_512x512x256", "eeg_uneven_4th",
-             "face_lra_1000x1000x400", "erp_42x9x71x60", "eeg_ongoing_14x46x510x64"] + sorted(E1_PATTERNS)
+             "face_lra_1000x1000x400", "face_lra_400x400x160", "erp_42x9x71x60", "eeg_ongoing_14x46x510x64"] + sorted(E1_PATTERNS)
 
 
 def _draw(rng, shape, dist):
