@@ -407,7 +407,9 @@ __device__ void lip_body(const LipArgs<T>& a, int k, unsigned char* smem) {
       }
       for (int m = tid; m < N; m += nt)
         if (have_cur) sc->LCprev[m] = sc->LCcur[m];
-      if (tid == 0) {
+      // the last thread (idle in the H loop below while R^2 < nt) takes the
+      // momentum step, off the critical path of thread 0
+      if (tid == nt - 1) {
         const double t = sc->t;
         const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
         sc->w_hat = (t - 1.0) / tn;
@@ -931,6 +933,15 @@ __device__ void update_objective_tail(const UpdArgs<T>& a, int tid, int NT, unsi
     x2 = sc->xnorm2[tid];
     ix2 = sc->inv_xnorm2[tid];
   }
+  // what the publish at the end reads, loaded now: the flags are only set by
+  // earlier kernels (and below, by this thread, when F is not finite)
+  unsigned int seq0 = 0;
+  int nonfinite0 = 0, timeout0 = 0;
+  if (tid == 0) {
+    seq0 = *((volatile unsigned int*)&sc->seq);
+    nonfinite0 = *((volatile int*)&sc->nonfinite);
+    timeout0 = *((volatile int*)&sc->timeout);
+  }
   if (a.gram_last) {
     // G^(n) for the next sweep's core update, summed from its chunks
     for (int e = tid; e < K * RR; e += NT) {
@@ -999,18 +1010,19 @@ __device__ void update_objective_tail(const UpdArgs<T>& a, int tid, int NT, unsi
     }
     if (tid == 0) {
       const double relerr = rel * a.inv_K;
+      const int nonfinite = nonfinite0 | (isfinite(F) ? 0 : 1);
       sc->F = F;
       sc->relerr = relerr;
-      if (!isfinite(F)) sc->nonfinite = 1;
+      if (nonfinite) sc->nonfinite = 1;
       sc->done_counter[1] = 0;
+      const unsigned int q = seq0 + 1;
+      sc->seq = q;
       if (a.hm) {
         HostMirror* hm = a.hm;
         hm->F = F;
         hm->relerr = relerr;
-        hm->nonfinite = *((volatile int*)&sc->nonfinite);
-        hm->timeout = *((volatile int*)&sc->timeout);
-        const unsigned int q = sc->seq + 1;
-        sc->seq = q;
+        hm->nonfinite = nonfinite;
+        hm->timeout = timeout0;
         __threadfence_system();
         hm->seq = q;
       }
