@@ -226,8 +226,8 @@ def time_to_fit(name, arms, check_every=10, cap=2000, lra_check_every=100, Xd=No
     cached for this workload and seed, else the library's own FP64 path run
     to convergence (labelled as such).  ``arms`` lists (storage, lra) pairs.
     Every arm pays the same check: its factors are copied (on the device)
-    into an FP32-storage handle of the original tensors, whose global Fit is
-    the judge."""
+    into an FP32-storage handle of the original tensors, whose global Fit
+    decides."""
     import torch
     import paper_2302_05119_gb300 as P
     import synth
@@ -250,7 +250,7 @@ def time_to_fit(name, arms, check_every=10, cap=2000, lra_check_every=100, Xd=No
                   "iterations": sf["total_iters"], "seconds": time.perf_counter() - t0}
         ref.close()
     bar = target["fit"] - 1e-4
-    judge = P.CoupledNCP(Xd, w.R, w.L, storage="f32")
+    ref32 = P.CoupledNCP(Xd, w.R, w.L, storage="f32")
     Ub = [[torch.empty((w.dims[k][n], w.ranks()[k]), dtype=torch.float32, device="cuda") for n in range(w.N)]
           for k in range(w.K)]
 
@@ -258,8 +258,8 @@ def time_to_fit(name, arms, check_every=10, cap=2000, lra_check_every=100, Xd=No
         for k in range(w.K):
             for n in range(w.N):
                 m.factor(k, n, out=Ub[k][n])
-        judge.set_factors(Ub)
-        return judge.global_fit()
+        ref32.set_factors(Ub)
+        return ref32.global_fit()
 
     out = {"workload": w.name, "metric": "seconds to a global Fit within 1e-4 of the target, on the FP32 data",
            "unit": "s", "target": target, "arms": {}}
@@ -286,7 +286,7 @@ def time_to_fit(name, arms, check_every=10, cap=2000, lra_check_every=100, Xd=No
         key = storage + ("+lra" if lra else "")
         out["arms"][key] = {"seconds": dt, "iterations": it, "fit_fp32_data": f, "fit_stored": f_stored,
                             "reached": bool(f >= bar), "lra_seconds": lra_s, "check_every": every}
-    judge.close()
+    ref32.close()
     torch.cuda.empty_cache()
     base = out["arms"].get("f32")
     if base and base["reached"]:
