@@ -16,7 +16,9 @@ Fit, evaluated on the original FP32 tensors, is within 1e-4 of the FP64
 oracle's converged Fit, for FP32, BF16 and BF16 hi+lo storage, and a
 "workloads" record: iterations/s and the dominant pass's roofline on that
 workload in BF16 and BF16 hi+lo storage and on the 16 uneven fourth-order
-EEG-shaped blocks (FP32).  The tensors (5 x 67 MB) exceed the 129 MB
+EEG-shaped blocks (FP32), and "time_to_fit_lra": the same measurement on the
+face shape (8 x 400x400x160, sparse first mode) for FP32, BF16 and BF16 with
+the LRA step of lraCoNCPD-APG (R~ = 30).  The tensors (5 x 67 MB) exceed the 129 MB
 L2, so no flush is needed between iterations.  --lra runs the low-rank
 approximation step of lraCoNCPD-APG (rank R~ of the workload) before the
 timed iterations, which then use the collapsed products.  --time-to-fit
@@ -459,6 +461,7 @@ def run_ours(args):
            "scope": "cncpd_create from pinned host tensors + set_factors + steps + factor copy-out, per job"}
 
     ttf = None
+    ttf_lra = None
     others = None
     if rank == 0 and ws == 1 and not args.no_time_to_fit:
         # the metric's second part: mixed precision against plain FP32 on the
@@ -474,6 +477,10 @@ def run_ours(args):
         del Xpd
         torch.cuda.empty_cache()
         others.append(measure_workload("eeg_uneven_4th", "f32"))
+        torch.cuda.empty_cache()
+        # lraCoNCPD-APG against the plain method on the face shape (scaled so
+        # that the FP64 oracle's converged fit could be computed for it)
+        ttf_lra = time_to_fit("face_lra_400x400x160", [("f32", False), ("bf16", False), ("bf16", True)])
         torch.cuda.empty_cache()
 
     cpu = None
@@ -494,7 +501,8 @@ def run_ours(args):
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "reupdates": s["reupdates"], "fit": s["fit"], "lra": lra,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": s["launches"], "clocks": clk, "time_to_fit": ttf, "workloads": others,
+            "gpu_launches": s["launches"], "clocks": clk, "time_to_fit": ttf, "time_to_fit_lra": ttf_lra,
+            "workloads": others,
             "lead_plan": {"units_per_sm": s["lead_plan"], "measured": bool(s["lead_plan_tuned"])},
         }
         print(json.dumps(line), flush=True)
