@@ -217,7 +217,8 @@ def measure_workload(name, storage, Xd=None, steps=200, warmup=5):
     m.close()
     return {"workload": w.name, "storage": storage, "K": w.K, "R": w.R, "L": w.L,
             "value": steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
-            "roofline": _pass_roofline(w, storage, s), "lead_plan": s["lead_plan"]}
+            "roofline": _pass_roofline(w, storage, s), "lead_plan": s["lead_plan"],
+            "trail_ranges": s["trail_ranges"]}
 
 
 def time_to_fit(name, arms, check_every=10, cap=2000, lra_check_every=100, Xd=None):

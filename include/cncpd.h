@@ -110,7 +110,10 @@ typedef struct {
   int lead_plan;      /* lead-pass units per SM in use (chosen by the measuring tuner when
                          opts.autotune is set; 0: not a persistent-pass problem) */
   int lead_plan_tuned;/* 1 if that plan was measured (this call or a cached earlier one) */
-  int reserved[2];
+  int trail_ranges;   /* most column ranges any block's rows are cut into by the trailing
+                         FP32/BF16 pass (1: whole rows; the ranges' partial products are
+                         added in range order by one extra launch per sweep) */
+  int reserved[1];
 } cncpd_stats;
 
 /* Fill *opts with the defaults listed above. */

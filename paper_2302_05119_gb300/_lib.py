@@ -32,7 +32,8 @@ class cncpd_stats(ctypes.Structure):
                 ("lra_sweeps", ctypes.c_int), ("lra_relerr", ctypes.c_double),
                 ("trail_ms", ctypes.c_double), ("lead_ms", ctypes.c_double),
                 ("launches", ctypes.c_longlong), ("lead_plan", ctypes.c_int),
-                ("lead_plan_tuned", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("lead_plan_tuned", ctypes.c_int), ("trail_ranges", ctypes.c_int),
+                ("reserved", ctypes.c_int * 1)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

@@ -413,10 +413,76 @@ size_t lead_partial_cap(cncpd_ctx* c, DevDesc d, int RP, int fp64) {
   return cap;
 }
 
-void plan_trailing_tiles(DevDesc& d) {
+// Units of the trailing contraction: 256-row tiles (64 for the generic
+// kernel).  On the FP32/BF16 CUDA-core pass (allow_split) a tile holding
+// more than half of a CTA's share of X (X over the SM count) is cut along its
+// columns into ranges of whole stages, so that one long-row block (say 4544
+// x 19200) cannot outlast the others; each range leaves a partial Pl that a
+// small kernel adds up in range order.  Returns the partial elements needed.
+size_t plan_trailing_tiles(DevDesc& d, int num_sms, int st, int allow_split) {
   d.lt_rows = (d.use_tma || d.use_umma) ? 256 : 64;
   d.lt_prefix[0] = 0;
-  for (int k = 0; k < d.K; ++k) d.lt_prefix[k + 1] = d.lt_prefix[k] + (int)((d.lead_rows[k] + d.lt_rows - 1) / d.lt_rows);
+  d.trail_split = 0;
+  d.Pl_part = nullptr;
+  int64_t xtot = 0;
+  for (int k = 0; k < d.K; ++k) xtot += d.lead_rows[k] * d.trail_cols[k];
+  const int64_t cap = std::max<int64_t>(1, xtot / std::max(1, num_sms) / 2);
+  const int64_t bc = st == ST_BF16 ? 64 : 32;  // columns of one 128-byte stage
+  size_t off = 0;
+  for (int k = 0; k < d.K; ++k) {
+    const int64_t J = d.trail_cols[k];
+    int js = 1;
+    int64_t jc = J;
+    if (allow_split && d.use_tma && !d.use_umma && (int64_t)d.lt_rows * J > cap) {
+      const int64_t want = std::min<int64_t>(16, ((int64_t)d.lt_rows * J + cap - 1) / cap);
+      jc = ((J + want - 1) / want + bc - 1) / bc * bc;
+      js = (int)((J + jc - 1) / jc);
+    }
+    d.lt_js[k] = js;
+    d.lt_jc[k] = (int)jc;
+    d.plp_off[k] = (int64_t)off;
+    if (js > 1) {
+      d.trail_split = 1;
+      off += (size_t)js * d.lead_rows[k] * d.R[k];
+    }
+    d.lt_prefix[k + 1] = d.lt_prefix[k] + js * (int)((d.lead_rows[k] + d.lt_rows - 1) / d.lt_rows);
+  }
+  return off;
+}
+
+// Unit costs of the current trailing plan (unit order of lt_prefix).
+std::vector<int64_t> trailing_unit_costs(const cncpd_ctx* c, const DevDesc& d) {
+  std::vector<int64_t> lt;
+  for (int k = 0; k < d.K; ++k) {
+    const int64_t rows = d.lead_rows[k], J = d.trail_cols[k];
+    const int js = d.lt_js[k];
+    for (int g = d.lt_prefix[k]; g < d.lt_prefix[k + 1]; ++g) {
+      const int local = g - d.lt_prefix[k];
+      const int64_t r0 = (int64_t)(local / js) * d.lt_rows;
+      const int64_t jb = (int64_t)(local % js) * d.lt_jc[k];
+      const int64_t cols = std::min<int64_t>(J, jb + d.lt_jc[k]) - jb;
+      lt.push_back(unit_cost(d, c->st, std::min<int64_t>(d.lt_rows, rows - r0) * cols, (int64_t)d.lt_rows * cols));
+    }
+  }
+  return lt;
+}
+
+// Trailing plan with column splits where they shorten the longest unit list
+// by more than the extra launch that adds the ranges up costs (about 3 us,
+// one SM's share of DRAM time for 128 KiB); else whole rows.  Returns the
+// partial elements of the chosen plan.
+size_t choose_trailing_plan(const cncpd_ctx* c, DevDesc& d, int allow_split) {
+  const size_t plp = plan_trailing_tiles(d, c->num_sms, c->st, allow_split);
+  if (!plp) return 0;
+  auto span = [&](const DevDesc& x) {
+    const std::vector<int64_t> cost = trailing_unit_costs(c, x);
+    return lpt_makespan(cost, std::min<int>((int)cost.size(), c->num_sms));
+  };
+  DevDesc whole = d;
+  plan_trailing_tiles(whole, c->num_sms, c->st, 0);
+  if (span(d) + 4 * 32768 < span(whole)) return plp;
+  d = whole;
+  return 0;
 }
 
 // Balanced unit lists of the two TMA passes.  A unit's cost is the number of
@@ -426,14 +492,7 @@ int plan_tma_schedules(cncpd_ctx* c, DevDesc& d) {
   d.lt_sched = d.tt_sched = nullptr;
   d.lt_grid = d.tt_grid = 0;
   if (!d.use_tma && !d.use_umma) return CNCPD_OK;
-  std::vector<int64_t> lt;
-  for (int k = 0; k < d.K; ++k) {
-    const int64_t rows = d.lead_rows[k], J = d.trail_cols[k];
-    for (int g = d.lt_prefix[k]; g < d.lt_prefix[k + 1]; ++g) {
-      const int64_t r0 = (int64_t)(g - d.lt_prefix[k]) * d.lt_rows;
-      lt.push_back(unit_cost(d, c->st, std::min<int64_t>(d.lt_rows, rows - r0) * J, (int64_t)d.lt_rows * J));
-    }
-  }
+  const std::vector<int64_t> lt = trailing_unit_costs(c, d);
   const std::vector<int64_t> tt = lead_unit_costs(c, d);
   const std::vector<int64_t>* costs[2] = {&lt, &tt};
   for (int which = 0; which < 2; ++which) {
@@ -522,9 +581,14 @@ int enqueue_trailing(cncpd_ctx* c, const DevDesc* dd, const DevDesc& hd, int RP)
   LaunchCfg lc{c->stream, c->num_sms};
   if (hd.use_umma) CU(launch_split_factor(lc, dd, hd, 0));
   TRY(record(c, 0));
-  if (hd.use_umma) CU(launch_trailing_umma(lc, dd, hd));
-  else if (hd.use_tma) CU(launch_trailing_tma(lc, dd, hd, RP, c->st));
-  else CU(launch_trailing_contract(lc, dd, hd, c->st, RP));
+  if (hd.use_umma) {
+    CU(launch_trailing_umma(lc, dd, hd));
+  } else if (hd.use_tma) {
+    CU(launch_trailing_tma(lc, dd, hd, RP, c->st));
+    CU(launch_reduce_trail_splits(lc, dd, hd));
+  } else {
+    CU(launch_trailing_contract(lc, dd, hd, c->st, RP));
+  }
   TRY(record(c, 1));
   return CNCPD_OK;
 }
@@ -816,6 +880,7 @@ long long kernels_per_replay(cncpd_ctx* c, int redo) {
   if (redo) n += 1 + 2 + (c->lra ? 2 : 0);                // restore, Grams (chunks + sums), cross Grams (same)
   if (!c->lra) n += 2 + (fused_last_reduce(c) ? 0 : 1);  // both tensor passes (+ split reduction)
   if (!c->lra && c->hd.use_umma) n += 2;                  // split factors of the tensor-core passes
+  if (!c->lra && c->hd.trail_split) n += 1;               // column ranges of the trailing pass added up
   for (int m = 0; m < c->N; ++m) {
     n += 2;                                               // Lipschitz (alone or with level 2), update
     if (c->lra) {
@@ -987,6 +1052,8 @@ int run_iterations(cncpd_ctx* c, int n_iters, bool use_eps, cncpd_stats* out) {
   st.total_iters = c->total_iters;
   st.lead_plan = c->lead_mult;
   st.lead_plan_tuned = (c->opts.autotune && c->lead_mult > 0) ? 1 : 0;
+  st.trail_ranges = 1;
+  for (int k = 0; k < c->K; ++k) st.trail_ranges = std::max(st.trail_ranges, c->hd.lt_js[k]);
   st.F = c->F_prev;
   st.relerr = c->rel_prev;
   st.fit = 1.0 - c->rel_prev;
@@ -1315,7 +1382,8 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
   CTRY(setup_umma(c, d, c->Rmax));
   size_t pel = 0;
   c->lead_mult = plan_lead_splits(c, d, c->RP, c->fp64, &pel);
-  plan_trailing_tiles(d);
+  const size_t plp = choose_trailing_plan(c, d, 1);
+  if (plp) CTRY(dalloc(c, &d.Pl_part, plp * sizeof(float)));
   CTRY(plan_tma_schedules(c, d));
   c->partial_cap = std::max(pel, lead_partial_cap(c, d, c->RP, c->fp64));
   CTRY(dalloc(c, &d.partial, c->partial_cap * c->fsz));
@@ -1644,7 +1712,7 @@ int cncpd_lra(cncpd_t h, const int* R_tilde, const void* const* Ut0, cncpd_dtype
   a.use_tma = (a.tmap_trail != nullptr) && tma_rank_supported(h->RPt);
   TRY(setup_umma(h, a, rtmax));
   (void)plan_lead_splits(h, a, h->RPt, h->fp64, &pel);
-  plan_trailing_tiles(a);
+  (void)plan_trailing_tiles(a, h->num_sms, h->st, 0);
   TRY(plan_tma_schedules(h, a));
   TRY(dalloc(h, &a.partial, pel * h->fsz));
   std::vector<int64_t> pre(K + 1, 0);

@@ -108,7 +108,17 @@ struct DevDesc {
   int tt_cols;                          // columns per tile of the lead contraction
   int pad2;
   int64_t pitch[CNCPD_KMAX];            // row pitch of X^(k) in elements (multiple of 16)
-  int lt_prefix[CNCPD_KMAX + 1];       // cumulative 64-row tiles of the trailing-mode contraction
+  int lt_prefix[CNCPD_KMAX + 1];       // cumulative units (row tiles x column splits) of the trailing-mode contraction
+  // column splits of the trailing TMA pass: block k's 256-row tiles are cut
+  // into lt_js[k] ranges of lt_jc[k] columns (a multiple of one stage); with
+  // lt_js[k] > 1 each range leaves a partial Pl at Pl_part + plp_off[k] +
+  // split * lead_rows * R, added in split order by k_reduce_trail_splits
+  int lt_js[CNCPD_KMAX];
+  int lt_jc[CNCPD_KMAX];
+  void* Pl_part;
+  int64_t plp_off[CNCPD_KMAX];
+  int trail_split;                     // 1: some block has lt_js > 1
+  int pad6;
   int tt_prefix[CNCPD_KMAX + 1];       // cumulative (column tile x split) units of the lead-mode contraction
   int tt_ctiles[CNCPD_KMAX];           // column tiles per block
   int tt_cpt;                          // columns per thread of that kernel
@@ -338,6 +348,8 @@ bool tma_rank_supported(int RP);
 cudaError_t launch_reduce_splits(const LaunchCfg& c, const DevDesc& h_desc, int fp64);
 // TMA-staged passes for FP32 (st = ST_F32) and BF16 (st = ST_BF16) storage
 cudaError_t launch_trailing_tma(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int RP, int st);
+// Pl of every block with column splits = the sum of its partials, in split order.
+cudaError_t launch_reduce_trail_splits(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc);
 cudaError_t launch_lead_tma(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int RP, int st);
 int lead_tma_rows(int st);
 // One-CTA kernel whose bounded mbarrier wait gets no arrival and gives up

@@ -11,6 +11,8 @@
 // work units.  Every mbarrier wait is bounded in time: on expiry the kernel
 // sets the error word, stops issuing copies, waits for the copies already in
 // flight and returns.
+#include <algorithm>
+
 #include "cncpd_internal.cuh"
 #include "tma.cuh"
 
@@ -44,6 +46,23 @@ struct Units {
     }
   }
   __device__ __forceinline__ int unit(int j) const { return ids ? __ldg(ids + j) : j; }
+};
+
+// Unit g of the trailing pass: block k, first row, and the column range
+// [jb, je) of its split (the whole row when the block is not split).
+struct TrailUnit {
+  int k, row0, jb, je, split;
+  __device__ __forceinline__ TrailUnit(const DevDesc* d, int g, int rows_per_tile) {
+    k = 0;
+    while (d->lt_prefix[k + 1] <= g) ++k;
+    const int local = g - d->lt_prefix[k];
+    const int js = d->lt_js[k];
+    split = local % js;
+    row0 = (local / js) * rows_per_tile;
+    const int J = (int)d->trail_cols[k];
+    jb = split * d->lt_jc[k];
+    je = min(J, jb + d->lt_jc[k]);
+  }
 };
 
 // Sixteen bytes of X as FP32 values: four FP32 or eight BF16 elements.
@@ -150,19 +169,17 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
     uint32_t it = 0;
     bool ok = true;
     for (int j = us.first; j < us.end && ok; j += us.step) {
-      const int g = us.unit(j);
-      int k = 0;
-      while (d->lt_prefix[k + 1] <= g) ++k;
-      const int row0 = (g - d->lt_prefix[k]) * TT_ROWS;
-      const int J = (int)d->trail_cols[k];
-      const int nch = (J + TT_BC - 1) / TT_BC;
+      const TrailUnit tu(d, us.unit(j), TT_ROWS);
+      const int k = tu.k;
+      const int nch = (tu.je - tu.jb + TT_BC - 1) / TT_BC;
       prefetch_tmap(&maps[k]);
       for (int c = 0; c < nch; ++c, ++it) {
         const int s = it % TST;
         const uint32_t ph = (it / TST) & 1;
         if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, err)) { ok = false; break; }
         mbar_arrive_expect_tx(smem_u32(&full[s]), S::X_BYTES);
-        tma_load_2d_hint(smem_u32(xs + s * S::X_BYTES), &maps[k], smem_u32(&full[s]), c * TT_BC, row0, pol);
+        tma_load_2d_hint(smem_u32(xs + s * S::X_BYTES), &maps[k], smem_u32(&full[s]), tu.jb + c * TT_BC, tu.row0,
+                         pol);
       }
     }
     // copies still in flight land before the CTA leaves
@@ -178,12 +195,11 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
     uint32_t it = 0;
     bool ok = true;
     for (int jn = us.first; jn < us.end && ok; jn += us.step) {
-      const int g = us.unit(jn);
-      int k = 0;
-      while (d->lt_prefix[k + 1] <= g) ++k;
-      const int J = (int)d->trail_cols[k];
+      const TrailUnit tu(d, us.unit(jn), TT_ROWS);
+      const int k = tu.k;
+      const int J = tu.je;  // columns past the split's end (or past J) get zero rows
       const int R = d->R[k];
-      const int nch = (J + TT_BC - 1) / TT_BC;
+      const int nch = (tu.je - tu.jb + TT_BC - 1) / TT_BC;
       for (int c = 0; c < nch; ++c, ++it) {
         if ((int)(it % NKR) != kw) continue;
         const int s = it % TST;
@@ -192,7 +208,7 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
         // Khatri-Rao rows of the trailing factors for the columns of this stage
 #pragma unroll
         for (int jj = lane; jj < TT_BC; jj += 32) {
-          const int j = c * TT_BC + jj;
+          const int j = tu.jb + c * TT_BC + jj;
           float w[S::WST];
 #pragma unroll
           for (int r = 0; r < S::WST; ++r) w[r] = (j < J && r < R) ? 1.f : 0.f;
@@ -223,13 +239,11 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
   const int li = lane & 7, cq = lane >> 3;  // row offset, column quarter
   constexpr int RH = RP / 2;
   for (int jn = us.first; jn < us.end; jn += us.step) {
-    const int g = us.unit(jn);
-    int k = 0;
-    while (d->lt_prefix[k + 1] <= g) ++k;
-    const int row0 = (g - d->lt_prefix[k]) * TT_ROWS;
-    const int J = (int)d->trail_cols[k];
+    const TrailUnit tu(d, us.unit(jn), TT_ROWS);
+    const int k = tu.k;
+    const int row0 = tu.row0;
     const int R = d->R[k];
-    const int nch = (J + TT_BC - 1) / TT_BC;
+    const int nch = (tu.je - tu.jb + TT_BC - 1) / TT_BC;
     uint64_t acc[4][RH];  // [row t][pair of ranks]
 #pragma unroll
     for (int t = 0; t < 4; ++t)
@@ -299,7 +313,10 @@ __global__ void __launch_bounds__((TT_CONS + NKR + 1) * 32, 1) k_trailing_tma(co
     const int64_t rows = d->lead_rows[k];
     const int nrow = rows - wrow0 < 32 ? (int)(rows - wrow0) : 32;
     const int ne = nrow > 0 ? nrow * R : 0;
-    float* dst = reinterpret_cast<float*>(d->Pl[k]) + wrow0 * R;
+    // a split block's unit leaves its partial rows for k_reduce_trail_splits
+    float* dst = (d->lt_js[k] > 1 ? reinterpret_cast<float*>(d->Pl_part) + d->plp_off[k] + (int64_t)tu.split * rows * R
+                                  : reinterpret_cast<float*>(d->Pl[k])) +
+                 wrow0 * R;
     if (R == RP) {
       for (int e = lane; e < ne; e += 32) dst[e] = stg[(e / RP) * (RP + 1) + e % RP];
     } else {
@@ -596,6 +613,39 @@ cudaError_t launch_lead_tma(const LaunchCfg& c, const DevDesc* dd, const DevDesc
   switch (RP) { CNCPD_TMA_RP(TCASE) }
 #undef TCASE
   return cudaErrorInvalidValue;
+}
+
+// Pl^(k) = sum over the column splits of block k's partial rows, added in
+// split order (blocks without splits are skipped).  One thread per element.
+__global__ void __launch_bounds__(256) k_reduce_trail_splits(const DevDesc* __restrict__ d) {
+  pdl_wait();
+  pdl_trigger();
+  const int k = blockIdx.y;
+  const int js = d->lt_js[k];
+  if (js <= 1) return;
+  const int64_t n = d->lead_rows[k] * d->R[k];
+  const float* __restrict__ part = reinterpret_cast<const float*>(d->Pl_part) + d->plp_off[k];
+  float* Pl = reinterpret_cast<float*>(d->Pl[k]);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    float v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = part[(int64_t)min(q, js - 1) * n + e];  // clamped: every load issues at once
+    float sum = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (q < js) sum += v[q];
+    for (int q = 8; q < js; ++q) sum += part[(int64_t)q * n + e];
+    Pl[e] = sum;
+  }
+}
+
+cudaError_t launch_reduce_trail_splits(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd) {
+  if (!hd.trail_split) return cudaSuccess;
+  int64_t nmax = 0;
+  for (int k = 0; k < hd.K; ++k)
+    if (hd.lt_js[k] > 1) nmax = std::max<int64_t>(nmax, hd.lead_rows[k] * hd.R[k]);
+  const unsigned gx = (unsigned)std::min<int64_t>(256, (nmax + 255) / 256);
+  return launch_pdl(k_reduce_trail_splits, dim3(gx, hd.K), dim3(256), 0, c.stream, dd);
 }
 
 // Self-test of the bounded-wait path: one thread waits on the phase-0
