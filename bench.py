@@ -372,7 +372,8 @@ def run_ours(args):
     Xd = [torch.from_numpy(X).cuda() for X in Xs]
     torch.cuda.synchronize()
 
-    m = P.CoupledNCP(Xd, w.R, w.L, profile=True, storage=args.storage)
+    m = P.CoupledNCP(Xd, w.R, w.L, profile=True, storage=args.storage, tf32=args.tf32,
+                     autotune=not args.no_autotune)
     m.set_factors(U0)
     lra = None
     if args.lra:
@@ -447,7 +448,7 @@ def run_ours(args):
     Xh = [torch.from_numpy(X).pin_memory() for X in Xs]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    m2 = P.CoupledNCP(Xh, w.R, w.L, storage=args.storage)
+    m2 = P.CoupledNCP(Xh, w.R, w.L, storage=args.storage, tf32=args.tf32, autotune=not args.no_autotune)
     m2.set_factors(U0)
     if args.lra:
         m2.lra(lra["R_tilde"], synth.init_lra_factors(w.dims, lra["R_tilde"], w.seed))
@@ -497,7 +498,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded Uniform[0,1] factors, 10 dB Gaussian noise, clipped)",
             "config": {"workload": w.name, "K": w.K, "dims": list(w.dims[0]), "R": w.R, "L": w.L,
-                       "storage": args.storage,
+                       "storage": args.storage, **({"tf32_trailing": True} if args.tf32 else {}),
                        "l2": f"inputs larger than L2 ({x_bytes / 1e6:.0f} MB of stored tensors)",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "reupdates": s["reupdates"], "fit": s["fit"], "lra": lra,
@@ -542,6 +543,11 @@ def main():
                          "clocks are sampled (0 under a profiler)")
     ap.add_argument("--no-time-to-fit", action="store_true",
                     help="leave the time-to-fit record out of the default line")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="lead-pass plan from the cost model instead of the measuring tuner (for profiler "
+                         "runs, whose serialised launches would bias the tuner's choice)")
+    ap.add_argument("--tf32", action="store_true",
+                    help="FP32 third-order data: trailing pass on the TF32 tensor cores (opt-in, slower)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

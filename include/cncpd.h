@@ -85,7 +85,13 @@ typedef struct {
                         units per SM) with CUDA events and keeps the fastest; the winner
                         is cached per problem shape for later handles of the process.
                         0: the plan of the cost model only */
-  int reserved[4];
+  int tf32;          /* 1 (with tensor_cores): FP32-stored third-order tensors with ranks
+                        up to 32 take the trailing-mode pass on the TF32 tensor cores, X
+                        and the factor each split into two TF32 parts (FP32-accurate:
+                        MTTKRP within 3e-7 of FP64 on uniform data).  Off by default: on
+                        GB300 it is slower than the CUDA-core pass (96 against 63 us on
+                        5 x 256^3, R = 10) */
+  int reserved[3];
 } cncpd_opts;
 
 /* Results of a solver call. */
@@ -113,7 +119,8 @@ typedef struct {
   int trail_ranges;   /* most column ranges any block's rows are cut into by the trailing
                          FP32/BF16 pass (1: whole rows; the ranges' partial products are
                          added in range order by one extra launch per sweep) */
-  int reserved[1];
+  int trail_tensor_cores; /* 1 if the trailing pass runs on the tensor cores (BF16 storage,
+                         or FP32 storage split into two TF32 parts, third order, R <= 32) */
 } cncpd_stats;
 
 /* Fill *opts with the defaults listed above. */

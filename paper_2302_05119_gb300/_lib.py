@@ -20,7 +20,8 @@ class cncpd_opts(ctypes.Structure):
                 ("delta_w", ctypes.c_double), ("use_core", ctypes.c_int),
                 ("reupdate", ctypes.c_int), ("storage", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("profile", ctypes.c_int),
-                ("tensor_cores", ctypes.c_int), ("autotune", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("tensor_cores", ctypes.c_int), ("autotune", ctypes.c_int), ("tf32", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
 
 
 class cncpd_stats(ctypes.Structure):
@@ -33,7 +34,7 @@ class cncpd_stats(ctypes.Structure):
                 ("trail_ms", ctypes.c_double), ("lead_ms", ctypes.c_double),
                 ("launches", ctypes.c_longlong), ("lead_plan", ctypes.c_int),
                 ("lead_plan_tuned", ctypes.c_int), ("trail_ranges", ctypes.c_int),
-                ("reserved", ctypes.c_int * 1)]
+                ("trail_tensor_cores", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

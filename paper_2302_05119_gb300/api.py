@@ -75,7 +75,7 @@ class CoupledNCP:
 
     def __init__(self, tensors, R, L, nonneg=None, storage=None, use_core=False, reupdate=True,
                  eps=1e-8, max_it=1000, lra_eps=1e-4, lra_max_it=200, delta_w=0.9999,
-                 use_graph=True, profile=False, tensor_cores=True, autotune=True, stream=None):
+                 use_graph=True, profile=False, tensor_cores=True, autotune=True, tf32=False, stream=None):
         self.K = len(tensors)
         self.N = len(tensors[0].shape)
         self.R = [int(r) for r in (R if np.ndim(R) else [R] * self.K)]
@@ -88,6 +88,7 @@ class CoupledNCP:
         o.use_graph, o.profile = int(use_graph), int(profile)
         o.tensor_cores = int(tensor_cores)
         o.autotune = int(autotune)
+        o.tf32 = int(tf32)
         self.opts = o
         code0 = None
         keep, ptrs = [], []

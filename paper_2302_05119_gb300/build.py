@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcncpd.so")
-SOURCES = ["mttkrp.cu", "mttkrp_tma.cu", "mttkrp_umma.cu", "update.cu", "lra.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["mttkrp.cu", "mttkrp_tma.cu", "mttkrp_umma.cu", "mttkrp_tf32.cu", "update.cu", "lra.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-diag-suppress", "177"]
 

@@ -263,6 +263,39 @@ int setup_umma(cncpd_ctx* c, DevDesc& d, int Rmax) {
   return CNCPD_OK;
 }
 
+// TF32 trailing pass of an FP32 third-order problem with ranks up to 32: the
+// buffers of the factor's two TF32 parts (the B operand) and their TMA
+// descriptors.  d.use_tf32 stays 0 when the problem does not qualify.
+int setup_tf32(cncpd_ctx* c, DevDesc& d, int Rmax) {
+  d.use_tf32 = 0;
+  const int np = umma_np(Rmax);
+  if (d.use_umma || !d.use_tma || !c->opts.tensor_cores || !c->opts.tf32 || c->st != ST_F32 || d.N != 3 ||
+      d.h != 2 || np == 0 ||
+      !d.tmap_trail || !tensor_map_encoder())
+    return CNCPD_OK;
+  // the kernel's split of X (Veltkamp, x * (2^13 + 1)) needs |x| < 2^114:
+  // guaranteed when every ||X^(k)||^2 is below 2^228
+  CU(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < d.K; ++k)
+    if (!(c->xnorm2[k] < std::ldexp(1.0, 228))) return CNCPD_OK;
+  std::vector<CUtensorMap> maps(CNCPD_KMAX);
+  for (int k = 0; k < d.K; ++k) {
+    const int64_t J = d.trail_cols[k];
+    d.bt_pitch[k] = (J + 31) / 32 * 32;
+    TRY(dalloc(c, &d.Bt[k], (size_t)2 * np * d.bt_pitch[k] * sizeof(float)));
+    if (!encode_map(&maps[k], d.Bt[k], ST_F32, 2 * np, J, d.bt_pitch[k], 32, 2 * np, CU_TENSOR_MAP_SWIZZLE_128B))
+      return CNCPD_OK;
+  }
+  CUtensorMap* dm = nullptr;
+  TRY(dalloc(c, (void**)&dm, maps.size() * sizeof(CUtensorMap)));
+  CU(cudaMemcpyAsync(dm, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  d.tmap_bt = dm;
+  d.umma_np = np;
+  d.use_tf32 = 1;
+  return CNCPD_OK;
+}
+
 // Assign units of cost cost[u] to P persistent CTAs, longest first, each to
 // the CTA with the least work so far (ties: lowest index); every CTA then
 // walks its units in increasing id.  Returns P + 1 start offsets followed by
@@ -313,9 +346,9 @@ int64_t lpt_makespan(const std::vector<int64_t>& cost, int P) {
 // full tile on the tensor cores; plus four 32 KiB stages for the unit's
 // epilogue and pipeline refill (measured on the 256^3 workload: 1, 2, 4 and 8
 // lead units per SM took 56, 60, 67 and 74 us).
-int64_t unit_cost(const DevDesc& d, int st, int64_t valid, int64_t tile) {
+int64_t unit_cost(const DevDesc& d, int st, int64_t valid, int64_t tile, bool tensor_cores) {
   const int64_t es = st == ST_BF16 ? 2 : 4;
-  const int64_t work = d.use_umma ? tile / 2 : tile * d.Rmax * 16 / 100;
+  const int64_t work = tensor_cores ? tile / 2 : tile * d.Rmax * 16 / 100;
   return std::max(valid * es, work) + 4 * 32768;
 }
 
@@ -364,7 +397,7 @@ std::vector<int64_t> lead_unit_costs(const cncpd_ctx* c, const DevDesc& d) {
       const int64_t re = std::min<int64_t>(rows, rb + d.split_rows[k]);
       for (int t = 0; t < d.tt_ctiles[k]; ++t) {
         const int64_t cols = std::min<int64_t>(d.tt_cols, J - (int64_t)t * d.tt_cols);
-        tt.push_back(unit_cost(d, c->st, (re - rb) * cols, (re - rb) * d.tt_cols));
+        tt.push_back(unit_cost(d, c->st, (re - rb) * cols, (re - rb) * d.tt_cols, d.use_umma));
       }
     }
   }
@@ -420,7 +453,7 @@ size_t lead_partial_cap(cncpd_ctx* c, DevDesc d, int RP, int fp64) {
 // x 19200) cannot outlast the others; each range leaves a partial Pl that a
 // small kernel adds up in range order.  Returns the partial elements needed.
 size_t plan_trailing_tiles(DevDesc& d, int num_sms, int st, int allow_split) {
-  d.lt_rows = (d.use_tma || d.use_umma) ? 256 : 64;
+  d.lt_rows = (d.use_tma || d.use_umma || d.use_tf32) ? 256 : 64;
   d.lt_prefix[0] = 0;
   d.trail_split = 0;
   d.Pl_part = nullptr;
@@ -433,7 +466,7 @@ size_t plan_trailing_tiles(DevDesc& d, int num_sms, int st, int allow_split) {
     const int64_t J = d.trail_cols[k];
     int js = 1;
     int64_t jc = J;
-    if (allow_split && d.use_tma && !d.use_umma && (int64_t)d.lt_rows * J > cap) {
+    if (allow_split && d.use_tma && !d.use_umma && !d.use_tf32 && (int64_t)d.lt_rows * J > cap) {
       const int64_t want = std::min<int64_t>(16, ((int64_t)d.lt_rows * J + cap - 1) / cap);
       jc = ((J + want - 1) / want + bc - 1) / bc * bc;
       js = (int)((J + jc - 1) / jc);
@@ -461,7 +494,8 @@ std::vector<int64_t> trailing_unit_costs(const cncpd_ctx* c, const DevDesc& d) {
       const int64_t r0 = (int64_t)(local / js) * d.lt_rows;
       const int64_t jb = (int64_t)(local % js) * d.lt_jc[k];
       const int64_t cols = std::min<int64_t>(J, jb + d.lt_jc[k]) - jb;
-      lt.push_back(unit_cost(d, c->st, std::min<int64_t>(d.lt_rows, rows - r0) * cols, (int64_t)d.lt_rows * cols));
+      lt.push_back(unit_cost(d, c->st, std::min<int64_t>(d.lt_rows, rows - r0) * cols, (int64_t)d.lt_rows * cols,
+                             d.use_umma || d.use_tf32));
     }
   }
   return lt;
@@ -580,9 +614,12 @@ int enqueue_mode_m(cncpd_ctx* c, int n) {
 int enqueue_trailing(cncpd_ctx* c, const DevDesc* dd, const DevDesc& hd, int RP) {
   LaunchCfg lc{c->stream, c->num_sms};
   if (hd.use_umma) CU(launch_split_factor(lc, dd, hd, 0));
+  if (hd.use_tf32) CU(launch_split_factor_tf32(lc, dd, hd));
   TRY(record(c, 0));
   if (hd.use_umma) {
     CU(launch_trailing_umma(lc, dd, hd));
+  } else if (hd.use_tf32) {
+    CU(launch_trailing_tf32(lc, dd, hd));
   } else if (hd.use_tma) {
     CU(launch_trailing_tma(lc, dd, hd, RP, c->st));
     CU(launch_reduce_trail_splits(lc, dd, hd));
@@ -880,6 +917,7 @@ long long kernels_per_replay(cncpd_ctx* c, int redo) {
   if (redo) n += 1 + 2 + (c->lra ? 2 : 0);                // restore, Grams (chunks + sums), cross Grams (same)
   if (!c->lra) n += 2 + (fused_last_reduce(c) ? 0 : 1);  // both tensor passes (+ split reduction)
   if (!c->lra && c->hd.use_umma) n += 2;                  // split factors of the tensor-core passes
+  if (!c->lra && c->hd.use_tf32) n += 1;                  // TF32 parts of the trailing factor
   if (!c->lra && c->hd.trail_split) n += 1;               // column ranges of the trailing pass added up
   for (int m = 0; m < c->N; ++m) {
     n += 2;                                               // Lipschitz (alone or with level 2), update
@@ -1052,6 +1090,7 @@ int run_iterations(cncpd_ctx* c, int n_iters, bool use_eps, cncpd_stats* out) {
   st.total_iters = c->total_iters;
   st.lead_plan = c->lead_mult;
   st.lead_plan_tuned = (c->opts.autotune && c->lead_mult > 0) ? 1 : 0;
+  st.trail_tensor_cores = (c->hd.use_umma || c->hd.use_tf32) ? 1 : 0;
   st.trail_ranges = 1;
   for (int k = 0; k < c->K; ++k) st.trail_ranges = std::max(st.trail_ranges, c->hd.lt_js[k]);
   st.F = c->F_prev;
@@ -1380,6 +1419,7 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
   }
   d.use_tma = (d.tmap_trail != nullptr) && tma_rank_supported(c->RP);
   CTRY(setup_umma(c, d, c->Rmax));
+  CTRY(setup_tf32(c, d, c->Rmax));
   size_t pel = 0;
   c->lead_mult = plan_lead_splits(c, d, c->RP, c->fp64, &pel);
   const size_t plp = choose_trailing_plan(c, d, 1);
@@ -1711,6 +1751,7 @@ int cncpd_lra(cncpd_t h, const int* R_tilde, const void* const* Ut0, cncpd_dtype
   size_t pel = 0;
   a.use_tma = (a.tmap_trail != nullptr) && tma_rank_supported(h->RPt);
   TRY(setup_umma(h, a, rtmax));
+  TRY(setup_tf32(h, a, rtmax));
   (void)plan_lead_splits(h, a, h->RPt, h->fp64, &pel);
   (void)plan_trailing_tiles(a, h->num_sms, h->st, 0);
   TRY(plan_tma_schedules(h, a));

@@ -160,6 +160,10 @@ struct DevDesc {
   void* dotp;
   double* xxp;                          // per-CTA shares of ||X_hat^(k)||^2 of that objective: [chunk CTA][block]
   int use_umma, umma_np;
+  // FP32 storage, third order, R <= 32: the trailing pass runs on the TF32
+  // tensor cores (Bt holds the factor's two TF32 parts, tmap_bt their map);
+  // the lead pass stays on the CUDA cores
+  int use_tf32, pad7;
   void* Bt[CNCPD_KMAX];
   void* Bl[CNCPD_KMAX];
   int64_t bt_pitch[CNCPD_KMAX];
@@ -359,6 +363,10 @@ cudaError_t launch_wait_selftest(cudaStream_t s, int* err, uint64_t limit_ns);
 int umma_np(int Rmax);
 cudaError_t launch_split_factor(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int which);
 cudaError_t launch_trailing_umma(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc);
+// TF32 tensor-core trailing pass of FP32 third-order tensors (use_tf32): the
+// factor's two TF32 parts, then the pass.
+cudaError_t launch_split_factor_tf32(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc);
+cudaError_t launch_trailing_tf32(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc);
 cudaError_t launch_lead_umma(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc);
 cudaError_t launch_level2(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int RP, int n);
 cudaError_t launch_gram(const LaunchCfg& c, const DevDesc* d_desc, const DevDesc& h_desc, int fp64, int n_begin, int n_end, int which);

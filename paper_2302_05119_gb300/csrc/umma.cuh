@@ -1,7 +1,8 @@
 // Fifth-generation tensor-core helpers (tcgen05) for sm_103a, written as
 // inline PTX: shared-memory matrix descriptors, the instruction descriptor of
-// a BF16 x BF16 -> FP32 MMA, TMEM allocation, the MMA itself, its commit to
-// an mbarrier, and loads of the accumulator from TMEM.
+// a BF16 x BF16 -> FP32 MMA and of a TF32 one, TMEM allocation, the MMAs
+// (A from shared or from tensor memory), their commit to an mbarrier, and
+// stores to and loads from TMEM.
 #pragma once
 
 #include <stdint.h>
@@ -32,6 +33,45 @@ __device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr, uint32_t lbo
 __host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N, int a_mn, int b_mn) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
          ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Instruction descriptor of tcgen05.mma .kind::tf32 (TF32 A and B, FP32
+// accumulator), both operands K-major.
+__host__ __device__ constexpr uint32_t umma_idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// D[tmem] (+)= A * B^T with A read from tensor memory (row m of A in lane m,
+// one TF32 value per column), B from shared memory; issued by one thread.
+__device__ __forceinline__ void umma_tf32_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t db, uint32_t idesc,
+                                             uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(db), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// 32 consecutive 32-bit columns of the warp's 32 TMEM lanes (one lane per
+// thread) from registers; tmem_wait_st makes them visible to later tcgen05
+// operations ordered after it.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+      "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+      "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// FP32 value rounded to the nearest TF32 value (11 significant bits, ties to
+// even), returned as its FP32 bit pattern with the low 13 bits zero.  Finite
+// inputs below 2^128 (1 - 2^-12) stay finite.
+__host__ __device__ __forceinline__ uint32_t tf32_round_bits(uint32_t u) {
+  return (u + 0xFFFu + ((u >> 13) & 1u)) & 0xFFFFE000u;
 }
 
 // D[tmem] (+)= A * B^T, issued by one thread; accumulate = 0 overwrites D.
