@@ -432,7 +432,8 @@ def run_ours(args):
         achieved = pass_bytes / (tk / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind,
-                "traffic": _traffic(kern, w.name, args.storage),
+                "traffic": _traffic("trailing_tf32" if (kern == "trailing_contract" and s["trail_tensor_cores"]
+                                                        and args.storage == "f32") else kern, w.name, args.storage),
                 "other_kernel_ms": t_trail if kern == "lead_contract" else t_lead,
                 "algorithmic_bytes_per_launch": pass_bytes,
                 "timed_launches": nl,
