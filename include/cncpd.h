@@ -142,7 +142,9 @@ void cncpd_default_opts(cncpd_opts *opts);
  *  stream   cudaStream_t whose prior work the copy of X waits for (NULL:
  *           the legacy default stream)
  * X is quantised into library-owned device memory in opts->storage and
- * ||X^(k)||^2 taken in FP64 of the stored values.  Initial factors are
+ * ||X^(k)||^2 taken in FP64 of the stored values.  Page-locked host memory
+ * is read in place by the quantising kernel (no staging copy); other host
+ * memory goes through a device staging buffer.  Initial factors are
  * Uniform[0,1] from a fixed counter-based generator until
  * cncpd_set_factors overrides them; cores start at 1.
  */
@@ -157,6 +159,12 @@ int cncpd_create(cncpd_t *out, int K, int N, const int64_t *dims,
  * individual columns.  Resets the iteration history (Sec. IV: the factors
  * are the algorithm's initialisation). */
 int cncpd_set_factors(cncpd_t h, int k, int n, const void *U, cncpd_dtype dtype);
+
+/* cncpd_set_factors for every block and mode in one call: U holds K*N
+ * pointers, block-major (U[k*N + n]), all of one dtype; the same rules for
+ * the shared columns (block 0's are written first).  One synchronisation at
+ * the end instead of one per factor. */
+int cncpd_set_factors_all(cncpd_t h, const void *const *U, cncpd_dtype dtype);
 
 /* Set the initial core lambda^(k) (R_k doubles, host memory). */
 int cncpd_set_core(cncpd_t h, int k, const double *lambda);

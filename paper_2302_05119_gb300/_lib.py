@@ -57,6 +57,7 @@ SIGNATURES = {
                           ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_ubyte),
                           ctypes.POINTER(cncpd_opts), _P]),
     "cncpd_set_factors": (_I, [_P, _I, _I, _P, _I]),
+    "cncpd_set_factors_all": (_I, [_P, _P, _I]),
     "cncpd_set_core": (_I, [_P, _I, ctypes.POINTER(_D)]),
     "cncpd_lra": (_I, [_P, ctypes.POINTER(_I), _PP, _I, ctypes.POINTER(cncpd_stats)]),
     "cncpd_step": (_I, [_P, _I, ctypes.POINTER(cncpd_stats)]),

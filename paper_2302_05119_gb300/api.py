@@ -133,11 +133,20 @@ class CoupledNCP:
         self.close()
 
     def set_factors(self, U):
-        """U[k][n]: initial factor of block k, mode n (I_n x R_k)."""
+        """U[k][n]: initial factor of block k, mode n (I_n x R_k), all in
+        one call (every factor in the first one's element type)."""
+        keep, ptrs, code0 = [], [], None
         for k in range(self.K):
             for n in range(self.N):
                 obj, p, code = _prep(U[k][n])
-                C.check(C.cncpd_set_factors(self._h, k, n, p, code))
+                if code0 is None:
+                    code0 = code
+                elif code != code0:
+                    obj, p, code = _prep(U[k][n], np.float64 if code0 == C.CNCPD_F64 else np.float32)
+                keep.append(obj)
+                ptrs.append(p.value)
+        arr = (ctypes.c_void_p * len(ptrs))(*ptrs)
+        C.check(C.cncpd_set_factors_all(self._h, arr, code0))
 
     def set_cores(self, lams):
         for k, lam in enumerate(lams):

@@ -1331,10 +1331,17 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
     const void* src = X[k];
     cudaPointerAttributes pa;
     bool on_dev = false;
-    if (cudaPointerGetAttributes(&pa, src) == cudaSuccess)
+    if (cudaPointerGetAttributes(&pa, src) == cudaSuccess) {
       on_dev = (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
-    else
+      // page-locked host memory is mapped into the device's address space:
+      // the quantising kernel reads it in place (no staging copy)
+      if (pa.type == cudaMemoryTypeHost && pa.devicePointer) {
+        src = pa.devicePointer;
+        on_dev = true;
+      }
+    } else {
       cudaGetLastError();
+    }
     if (!on_dev) {
       if (!stage) CTRY(dalloc(c, &stage, maxel * ses));
       CCU(cudaMemcpyAsync(stage, src, ne * ses, cudaMemcpyHostToDevice, c->stream));
@@ -1544,6 +1551,16 @@ extern "C" {
 int cncpd_set_factors(cncpd_t h, int k, int n, const void* U, cncpd_dtype dtype) {
   TRY(check_handle(h));
   TRY(write_factor(h, k, n, U, dtype));
+  TRY(sync(h));
+  h->dirty = true;
+  return CNCPD_OK;
+}
+
+int cncpd_set_factors_all(cncpd_t h, const void* const* U, cncpd_dtype dtype) {
+  TRY(check_handle(h));
+  if (!U) return set_err(CNCPD_EINVAL, "U is NULL");
+  for (int k = 0; k < h->K; ++k)
+    for (int n = 0; n < h->N; ++n) TRY(write_factor(h, k, n, U[(size_t)k * h->N + n], dtype));
   TRY(sync(h));
   h->dirty = true;
   return CNCPD_OK;

@@ -1817,35 +1817,71 @@ cudaError_t launch_grad(const LaunchCfg& c, const DevDesc* dd, const DevDesc& hd
 // Data preparation: quantise X into the storage type and take ||X_stored||^2
 // in FP64 (per-CTA partial sums, then a fixed-order sum).
 // ---------------------------------------------------------------------------
+// One element: stored at o in the storage type; returns the stored value.
+__device__ __forceinline__ double quantize_one(double x, void* dst, void* dst_lo, int st, int64_t o) {
+  if (st == ST_F64) {
+    reinterpret_cast<double*>(dst)[o] = x;
+    return x;
+  }
+  if (st == ST_F32) {
+    const float f = (float)x;
+    reinterpret_cast<float*>(dst)[o] = f;
+    return f;
+  }
+  if (st == ST_BF16) {
+    const __nv_bfloat16 b = __double2bfloat16(x);
+    reinterpret_cast<__nv_bfloat16*>(dst)[o] = b;
+    return (double)__bfloat162float(b);
+  }
+  const float f = (float)x;
+  const __nv_bfloat16 hi = __float2bfloat16_rn(f);
+  const __nv_bfloat16 lo = __float2bfloat16_rn(f - __bfloat162float(hi));
+  reinterpret_cast<__nv_bfloat16*>(dst)[o] = hi;
+  reinterpret_cast<__nv_bfloat16*>(dst_lo)[o] = lo;
+  return (double)(__bfloat162float(hi) + __bfloat162float(lo));
+}
+
+// The source may be page-locked host memory read in place, so it is read in
+// 16-byte vectors, four per thread in flight, when its address allows; each
+// element then goes to (row, col) of the pitched store.
 template <typename S>
 __global__ void k_quantize(const S* __restrict__ src, void* dst, void* dst_lo, int st, int64_t rows, int64_t cols,
                            int64_t pitch, double* part) {
+  constexpr int V = 16 / sizeof(S);  // elements per 16-byte vector
   double acc = 0.0;
   const int64_t n = rows * cols;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = i / cols;
-    const int64_t o = row * pitch + (i - row * cols);
-    const double x = (double)src[i];
-    double q;
-    if (st == ST_F64) {
-      reinterpret_cast<double*>(dst)[o] = x;
-      q = x;
-    } else if (st == ST_F32) {
-      const float f = (float)x;
-      reinterpret_cast<float*>(dst)[o] = f;
-      q = f;
-    } else if (st == ST_BF16) {
-      const __nv_bfloat16 b = __double2bfloat16(x);
-      reinterpret_cast<__nv_bfloat16*>(dst)[o] = b;
-      q = (double)__bfloat162float(b);
-    } else {
-      const float f = (float)x;
-      const __nv_bfloat16 hi = __float2bfloat16_rn(f);
-      const __nv_bfloat16 lo = __float2bfloat16_rn(f - __bfloat162float(hi));
-      reinterpret_cast<__nv_bfloat16*>(dst)[o] = hi;
-      reinterpret_cast<__nv_bfloat16*>(dst_lo)[o] = lo;
-      q = (double)(__bfloat162float(hi) + __bfloat162float(lo));
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t done = 0;
+  if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+    const int64_t nv = n / V;  // whole vectors
+    const uint4* sv = reinterpret_cast<const uint4*>(src);
+    for (int64_t v0 = t; v0 < nv; v0 += 4 * nthreads) {
+      uint4 buf[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t v = v0 + u * nthreads;
+        buf[u] = v < nv ? sv[v] : make_uint4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t v = v0 + u * nthreads;
+        if (v >= nv) break;
+        const S* e = reinterpret_cast<const S*>(&buf[u]);
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+          const int64_t i = v * V + j;
+          const int64_t row = i / cols;
+          const double q = quantize_one((double)e[j], dst, dst_lo, st, row * pitch + (i - row * cols));
+          acc = fma(q, q, acc);
+        }
+      }
     }
+    done = nv * V;
+  }
+  for (int64_t i = done + t; i < n; i += nthreads) {
+    const int64_t row = i / cols;
+    const double q = quantize_one((double)src[i], dst, dst_lo, st, row * pitch + (i - row * cols));
     acc = fma(q, q, acc);
   }
   __shared__ double red[256];
