@@ -91,7 +91,16 @@ typedef struct {
                         MTTKRP within 3e-7 of FP64 on uniform data).  Off by default: on
                         GB300 it is slower than the CUDA-core pass (96 against 63 us on
                         5 x 256^3, R = 10) */
-  int reserved[3];
+  int stream_x;      /* 1: keep only one block's stored values on the device (a window
+                        the size of the largest block); cncpd_create takes ||X^(k)||^2
+                        block by block, cncpd_lra runs each block's ALS with its tensor
+                        in the window, and cncpd_global_fit streams the blocks again.
+                        The caller's tensors must stay valid for the handle's lifetime
+                        (device or page-locked host memory is read in place).  Only the
+                        lraCoNCPD-APG iterations run without X: cncpd_step, cncpd_fit,
+                        cncpd_mttkrp and cncpd_objective_grad(_at) return CNCPD_ESTATE
+                        before cncpd_lra */
+  int reserved[2];
 } cncpd_opts;
 
 /* Results of a solver call. */

@@ -21,7 +21,7 @@ class cncpd_opts(ctypes.Structure):
                 ("reupdate", ctypes.c_int), ("storage", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("profile", ctypes.c_int),
                 ("tensor_cores", ctypes.c_int), ("autotune", ctypes.c_int), ("tf32", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("stream_x", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 class cncpd_stats(ctypes.Structure):

@@ -75,7 +75,8 @@ class CoupledNCP:
 
     def __init__(self, tensors, R, L, nonneg=None, storage=None, use_core=False, reupdate=True,
                  eps=1e-8, max_it=1000, lra_eps=1e-4, lra_max_it=200, delta_w=0.9999,
-                 use_graph=True, profile=False, tensor_cores=True, autotune=True, tf32=False, stream=None):
+                 use_graph=True, profile=False, tensor_cores=True, autotune=True, tf32=False, stream_x=False,
+                 stream=None):
         self.K = len(tensors)
         self.N = len(tensors[0].shape)
         self.R = [int(r) for r in (R if np.ndim(R) else [R] * self.K)]
@@ -89,6 +90,7 @@ class CoupledNCP:
         o.tensor_cores = int(tensor_cores)
         o.autotune = int(autotune)
         o.tf32 = int(tf32)
+        o.stream_x = int(stream_x)
         self.opts = o
         code0 = None
         keep, ptrs = [], []
@@ -113,6 +115,8 @@ class CoupledNCP:
                                ctypes.byref(o), ctypes.c_void_p(st) if st else None))
         self._h = h
         self.Rt = None
+        # with stream_x the library reads the tensors again (LRA, global fit)
+        self._x_keep = keep if stream_x else None
 
     # -------------------------------------------------------------- state --
     def close(self):

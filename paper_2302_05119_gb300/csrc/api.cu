@@ -123,6 +123,19 @@ struct cncpd_ctx {
   cudaStream_t side = nullptr;                // branch for work independent of a tensor pass
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
+  // opts.stream_x: one device window holds the stored values of one block at
+  // a time; the caller's tensors (xsrc, in x_dtype) are quantised into it on
+  // demand (load_block)
+  std::vector<const void*> xsrc;
+  int x_src_f64 = 0;
+  void* window = nullptr;
+  void* window_lo = nullptr;
+  void* xstage = nullptr;        // staging buffer for pageable sources
+  size_t window_bytes = 0;
+  int window_block = -1;
+  double* wscratch = nullptr;    // norm partials of a window load
+  double* wnorm = nullptr;
+
   // lead-pass split plan: units per SM in use, whether it was measured, and
   // the partial-sum capacity (elements) every candidate plan fits in
   int lead_mult = 0;
@@ -134,6 +147,7 @@ struct cncpd_ctx {
   std::vector<int> Rt;
   DevDesc hd_als{};
   DevDesc* dd_als = nullptr;
+  DevDesc* dd_tmp = nullptr;     // a restricted copy of hd (streamed X: one block's passes)
   int RPt = 0;
   int64_t* d_red_prefix_als = nullptr;
   int* d_active = nullptr;
@@ -1031,7 +1045,15 @@ int tune_lead(cncpd_ctx* c) {
   return CNCPD_OK;
 }
 
+int need_resident_x(const cncpd_ctx* c) {
+  if (c->opts.stream_x && !c->lra)
+    return set_err(CNCPD_ESTATE, "opts.stream_x keeps one block of X on the device: run cncpd_lra first "
+                                 "(only the lraCoNCPD-APG iterations run without X)");
+  return CNCPD_OK;
+}
+
 int run_iterations(cncpd_ctx* c, int n_iters, bool use_eps, cncpd_stats* out) {
+  TRY(need_resident_x(c));
   cncpd_stats st{};
   const double t0 = now_s();
   if (!c->lead_tuned) TRY(tune_lead(c));
@@ -1113,6 +1135,63 @@ int all_modes_m(cncpd_ctx* c) {
     if (gsize > 1) CU(launch_level2(lc, c->dd, c->hd, c->fp64, c->RP, n));
   }
   return CNCPD_OK;
+}
+
+// opts.stream_x: make the window hold block k's stored values (quantised
+// from the caller's tensor: in place when it is device or page-locked
+// memory, else through the staging buffer).
+int load_block(cncpd_ctx* c, int k) {
+  if (c->window_block == k) return CNCPD_OK;
+  const DevDesc& d = c->hd;
+  const size_t xes = (c->st == ST_F64) ? 8 : (c->st == ST_F32) ? 4 : 2;
+  const int64_t ne = d.lead_rows[k] * d.trail_cols[k];
+  const int64_t nstore = d.lead_rows[k] * d.pitch[k];
+  if (d.pitch[k] != d.trail_cols[k]) {
+    CU(cudaMemsetAsync(c->window, 0, nstore * xes, c->stream));
+    if (c->window_lo) CU(cudaMemsetAsync(c->window_lo, 0, nstore * xes, c->stream));
+  }
+  const void* src = c->xsrc[k];
+  const size_t ses = c->x_src_f64 ? 8 : 4;
+  cudaPointerAttributes pa;
+  bool on_dev = false;
+  if (cudaPointerGetAttributes(&pa, src) == cudaSuccess) {
+    on_dev = (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
+    if (pa.type == cudaMemoryTypeHost && pa.devicePointer) {
+      src = pa.devicePointer;
+      on_dev = true;
+    }
+  } else {
+    cudaGetLastError();
+  }
+  if (!on_dev) {
+    if (!c->xstage) {
+      int64_t maxel = 0;
+      for (int b = 0; b < c->K; ++b) maxel = std::max(maxel, d.lead_rows[b] * d.trail_cols[b]);
+      TRY(dalloc(c, &c->xstage, maxel * ses));
+    }
+    CU(cudaMemcpyAsync(c->xstage, src, ne * ses, cudaMemcpyHostToDevice, c->stream));
+    src = c->xstage;
+  }
+  CU(launch_quantize(c->stream, src, c->x_src_f64, c->window, c->window_lo, c->st, d.lead_rows[k], d.trail_cols[k],
+                     d.pitch[k], c->wnorm, c->wscratch, 1024));
+  c->window_block = k;
+  return CNCPD_OK;
+}
+
+// A copy of `full` whose tensor-pass unit lists cover only the blocks with
+// active[k] set (the balanced per-CTA lists number every block's units, so
+// they are dropped unless every block is active).
+DevDesc restrict_units(const DevDesc& full, const int* active) {
+  DevDesc aa = full;
+  int nact = 0;
+  aa.lt_prefix[0] = aa.tt_prefix[0] = 0;
+  for (int k = 0; k < full.K; ++k) {
+    nact += active[k] ? 1 : 0;
+    aa.lt_prefix[k + 1] = aa.lt_prefix[k] + (active[k] ? full.lt_prefix[k + 1] - full.lt_prefix[k] : 0);
+    aa.tt_prefix[k + 1] = aa.tt_prefix[k] + (active[k] ? full.tt_prefix[k + 1] - full.tt_prefix[k] : 0);
+  }
+  if (nact < full.K) aa.lt_sched = aa.tt_sched = nullptr;
+  return aa;
 }
 
 int check_handle(cncpd_t h) {
@@ -1315,6 +1394,22 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
   const int nblk = 1024;
   CTRY(dalloc(c, (void**)&nscratch, nblk * sizeof(double)));
   CTRY(dalloc(c, (void**)&nout, CNCPD_KMAX * sizeof(double)));
+  const bool streamed = c->opts.stream_x != 0;
+  if (streamed) {
+    // one window for the largest stored block (and its lo plane)
+    size_t wmax = 0;
+    for (int k = 0; k < K; ++k) {
+      d.pitch[k] = (d.trail_cols[k] + 15) / 16 * 16;
+      wmax = std::max(wmax, (size_t)(d.lead_rows[k] * d.pitch[k]) * xes);
+    }
+    c->window_bytes = wmax;
+    CTRY(dalloc(c, &c->window, wmax));
+    if (st == ST_BF16X2) CTRY(dalloc(c, &c->window_lo, wmax));
+    c->xsrc.assign(X, X + K);
+    c->x_src_f64 = src_f64;
+    CTRY(dalloc(c, (void**)&c->wscratch, nblk * sizeof(double)));
+    CTRY(dalloc(c, (void**)&c->wnorm, sizeof(double)));
+  }
   for (int k = 0; k < K; ++k) {
     const int64_t ne = d.lead_rows[k] * d.trail_cols[k];
     const int64_t pitch = (d.trail_cols[k] + 15) / 16 * 16;  // rows start on 64-byte (FP32) boundaries
@@ -1322,11 +1417,21 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
     const int64_t nstore = d.lead_rows[k] * pitch;
     void* xb = nullptr;
     void* xlo = nullptr;
-    CTRY(dalloc(c, &xb, nstore * xes));
-    if (pitch != d.trail_cols[k]) CCU(cudaMemsetAsync(xb, 0, nstore * xes, c->stream));
-    if (st == ST_BF16X2) {
-      CTRY(dalloc(c, &xlo, nstore * xes));
-      if (pitch != d.trail_cols[k]) CCU(cudaMemsetAsync(xlo, 0, nstore * xes, c->stream));
+    if (streamed) {
+      // every block's stored values go through the window (here for ||X||^2)
+      xb = c->window;
+      xlo = c->window_lo;
+      if (pitch != d.trail_cols[k]) {
+        CCU(cudaMemsetAsync(xb, 0, nstore * xes, c->stream));
+        if (xlo) CCU(cudaMemsetAsync(xlo, 0, nstore * xes, c->stream));
+      }
+    } else {
+      CTRY(dalloc(c, &xb, nstore * xes));
+      if (pitch != d.trail_cols[k]) CCU(cudaMemsetAsync(xb, 0, nstore * xes, c->stream));
+      if (st == ST_BF16X2) {
+        CTRY(dalloc(c, &xlo, nstore * xes));
+        if (pitch != d.trail_cols[k]) CCU(cudaMemsetAsync(xlo, 0, nstore * xes, c->stream));
+      }
     }
     const void* src = X[k];
     cudaPointerAttributes pa;
@@ -1351,7 +1456,9 @@ int cncpd_create(cncpd_t* out, int K, int N, const int64_t* dims, const void* co
                         nscratch, nblk));
     d.X[k] = xb;
     d.Xlo[k] = xlo;
+    if (streamed) c->window_block = k;
   }
+  if (streamed && stage) c->xstage = stage;
   CCU(cudaMemcpyAsync(c->xnorm2.data(), nout, K * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
 
   // --- factor arenas
@@ -1609,6 +1716,7 @@ int cncpd_core(cncpd_t h, int k, double* lambda) {
 int cncpd_mttkrp(cncpd_t h, int k, int n, void* dst, cncpd_dtype dtype) {
   TRY(check_handle(h));
   if (k < 0 || k >= h->K || n < 0 || n >= h->N || !dst) return set_err(CNCPD_EINVAL, "bad block/mode or NULL dst");
+  TRY(need_resident_x(h));
   if (h->lra) {
     LaunchCfg lc{h->stream, h->num_sms};
     CU(launch_cross_gram(lc, h->dd, h->hd, h->fp64, 0, h->N));
@@ -1621,6 +1729,7 @@ int cncpd_mttkrp(cncpd_t h, int k, int n, void* dst, cncpd_dtype dtype) {
 
 int cncpd_objective_grad(cncpd_t h, double* F, void* const* gradU, void* const* gradC, cncpd_dtype dtype) {
   TRY(check_handle(h));
+  TRY(need_resident_x(h));
   if (dtype != CNCPD_F64 && dtype != CNCPD_F32) return set_err(CNCPD_EINVAL, "dtype must be F64 or F32");
   if (h->dirty) TRY(initialise(h));
   return eval_objective_grad(h, F, gradU, gradC, dtype);
@@ -1629,6 +1738,7 @@ int cncpd_objective_grad(cncpd_t h, double* F, void* const* gradU, void* const* 
 int cncpd_objective_grad_at(cncpd_t h, const void* const* U, cncpd_dtype udtype, double* F, void* const* gradU,
                             void* const* gradC, cncpd_dtype dtype) {
   TRY(check_handle(h));
+  TRY(need_resident_x(h));
   if (!U) return set_err(CNCPD_EINVAL, "U is NULL");
   if (dtype != CNCPD_F64 && dtype != CNCPD_F32) return set_err(CNCPD_EINVAL, "dtype must be F64 or F32");
   if (h->dirty) TRY(initialise(h));
@@ -1661,7 +1771,27 @@ int cncpd_global_fit(cncpd_t h, double* fit) {
   const bool was_lra = h->lra;
   h->lra = false;
   CU(launch_gram(lc, h->dd, h->hd, h->fp64, 0, h->N, 0));
-  int r = enqueue_lead(h, h->dd, h->hd, h->RP, h->d_red_prefix);
+  int r = CNCPD_OK;
+  if (h->opts.stream_x) {
+    // one block at a time through the window: its lead pass alone (the
+    // split-K sums of the other blocks are formed from their own partials)
+    if (!h->dd_tmp) r = dalloc(h, (void**)&h->dd_tmp, sizeof(DevDesc));
+    std::vector<int> one(CNCPD_KMAX, 0);
+    for (int k = 0; k < h->K && r == CNCPD_OK; ++k) {
+      r = load_block(h, k);
+      if (r != CNCPD_OK) break;
+      std::fill(one.begin(), one.end(), 0);
+      one[k] = 1;
+      const DevDesc t = restrict_units(h->hd, one.data());
+      cudaError_t e = cudaMemcpyAsync(h->dd_tmp, &t, sizeof(DevDesc), cudaMemcpyHostToDevice, h->stream);
+      if (e != cudaSuccess) r = set_err(CNCPD_ECUDA, "%s", cudaGetErrorString(e));
+      if (r == CNCPD_OK) r = enqueue_lead(h, h->dd_tmp, t, h->RP, h->d_red_prefix);
+      // the descriptor copy must not change before the kernels have read it
+      if (r == CNCPD_OK) r = sync(h);
+    }
+  } else {
+    r = enqueue_lead(h, h->dd, h->hd, h->RP, h->d_red_prefix);
+  }
   if (r == CNCPD_OK) r = enqueue_mode_m(h, h->N - 1);
   h->lra = was_lra;
   TRY(r);
@@ -1808,53 +1938,58 @@ int cncpd_lra(cncpd_t h, const int* R_tilde, const void* const* Ut0, cncpd_dtype
   LaunchCfg lc{h->stream, h->num_sms};
   CU(launch_gram(lc, h->dd_als, h->hd_als, h->fp64, 0, N, 0));
   std::vector<int> active(CNCPD_KMAX, 0), sweeps(K, 0);
-  for (int k = 0; k < K; ++k) active[k] = 1;
   std::vector<double> rel_prev(K, -1.0), rel(K, 0.0);
-  // relative error of the initial factors
-  {
-    // M^(N-1) at the initial factors for the ALS relative error
+  const DevDesc full = h->hd_als;
+  // The blocks' ALS runs are independent.  With X resident they run together;
+  // with opts.stream_x one block at a time, each with its tensor in the window.
+  const bool streamed = h->opts.stream_x != 0;
+  for (int g0 = 0; g0 < K; g0 = streamed ? g0 + 1 : K) {
+    const int g1 = streamed ? g0 + 1 : K;
+    if (streamed) TRY(load_block(h, g0));
+    std::fill(active.begin(), active.end(), 0);
+    for (int k = g0; k < g1; ++k) active[k] = 1;
+    // relative error of the initial factors, from M^(N-1) at those factors
+    h->hd_als = restrict_units(full, active.data());
+    CU(cudaMemcpyAsync(h->dd_als, &h->hd_als, sizeof(DevDesc), cudaMemcpyHostToDevice, h->stream));
     TRY(enqueue_lead(h, h->dd_als, h->hd_als, h->RPt, h->d_red_prefix_als));
     if (N - h->h > 1) CU(launch_level2(lc, h->dd_als, h->hd_als, h->fp64, h->RPt, N - 1));
     CU(launch_als_relerr(lc, h->dd_als, h->hd_als, h->fp64, h->d_relk));
-    CU(cudaMemcpyAsync(rel_prev.data(), h->d_relk, K * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    TRY(sync(h));
-  }
-  const DevDesc full = h->hd_als;
-  for (int s = 1; s <= h->opts.lra_max_it; ++s) {
-    int nact = 0;
-    for (int k = 0; k < K; ++k) nact += active[k];
-    if (nact == 0) break;
-    // only active blocks stream X
-    DevDesc& aa = h->hd_als;
-    aa.lt_prefix[0] = aa.tt_prefix[0] = 0;
-    for (int k = 0; k < K; ++k) {
-      aa.lt_prefix[k + 1] = aa.lt_prefix[k] + (active[k] ? full.lt_prefix[k + 1] - full.lt_prefix[k] : 0);
-      aa.tt_prefix[k + 1] = aa.tt_prefix[k] + (active[k] ? full.tt_prefix[k + 1] - full.tt_prefix[k] : 0);
+    {
+      std::vector<double> r0(K, 0.0);
+      CU(cudaMemcpyAsync(r0.data(), h->d_relk, K * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      TRY(sync(h));
+      for (int k = g0; k < g1; ++k) rel_prev[k] = r0[k];
     }
-    if (nact < K) aa.lt_sched = aa.tt_sched = nullptr;  // the lists number the units of all blocks
-    CU(cudaMemcpyAsync(h->dd_als, &aa, sizeof(DevDesc), cudaMemcpyHostToDevice, h->stream));
-    CU(cudaMemcpyAsync(h->d_active, active.data(), CNCPD_KMAX * sizeof(int), cudaMemcpyHostToDevice, h->stream));
-    CU(cudaMemsetAsync(h->d_status, 0, CNCPD_KMAX * sizeof(int), h->stream));
-    for (int n = 0; n < N; ++n) {
-      if (n == 0) TRY(enqueue_trailing(h, h->dd_als, h->hd_als, h->RPt));
-      if (n == h->h) TRY(enqueue_lead(h, h->dd_als, h->hd_als, h->RPt, h->d_red_prefix_als));
-      const int gsize = (n < h->h) ? h->h : N - h->h;
-      if (gsize > 1) CU(launch_level2(lc, h->dd_als, h->hd_als, h->fp64, h->RPt, n));
-      CU(launch_als_solve(lc, h->dd_als, h->hd_als, h->fp64, n, h->d_active, h->d_status));
-      CU(launch_als_apply(lc, h->dd_als, h->hd_als, h->fp64, n, h->d_active));
-      CU(launch_gram(lc, h->dd_als, h->hd_als, h->fp64, n, n + 1, 0));
-    }
-    CU(launch_als_relerr(lc, h->dd_als, h->hd_als, h->fp64, h->d_relk));
-    std::vector<int> status(K, 0);
-    CU(cudaMemcpyAsync(rel.data(), h->d_relk, K * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    CU(cudaMemcpyAsync(status.data(), h->d_status, K * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    TRY(sync(h));
-    for (int k = 0; k < K; ++k) {
-      if (!active[k]) continue;
-      if (status[k]) return set_err(CNCPD_ESINGULAR, "ALS normal matrix of block %d not positive definite", k);
-      sweeps[k] = s;
-      if (std::fabs(rel[k] - rel_prev[k]) < h->opts.lra_eps) active[k] = 0;
-      rel_prev[k] = rel[k];
+    for (int s = 1; s <= h->opts.lra_max_it; ++s) {
+      int nact = 0;
+      for (int k = 0; k < K; ++k) nact += active[k];
+      if (nact == 0) break;
+      // only active blocks stream X
+      h->hd_als = restrict_units(full, active.data());
+      CU(cudaMemcpyAsync(h->dd_als, &h->hd_als, sizeof(DevDesc), cudaMemcpyHostToDevice, h->stream));
+      CU(cudaMemcpyAsync(h->d_active, active.data(), CNCPD_KMAX * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+      CU(cudaMemsetAsync(h->d_status, 0, CNCPD_KMAX * sizeof(int), h->stream));
+      for (int n = 0; n < N; ++n) {
+        if (n == 0) TRY(enqueue_trailing(h, h->dd_als, h->hd_als, h->RPt));
+        if (n == h->h) TRY(enqueue_lead(h, h->dd_als, h->hd_als, h->RPt, h->d_red_prefix_als));
+        const int gsize = (n < h->h) ? h->h : N - h->h;
+        if (gsize > 1) CU(launch_level2(lc, h->dd_als, h->hd_als, h->fp64, h->RPt, n));
+        CU(launch_als_solve(lc, h->dd_als, h->hd_als, h->fp64, n, h->d_active, h->d_status));
+        CU(launch_als_apply(lc, h->dd_als, h->hd_als, h->fp64, n, h->d_active));
+        CU(launch_gram(lc, h->dd_als, h->hd_als, h->fp64, n, n + 1, 0));
+      }
+      CU(launch_als_relerr(lc, h->dd_als, h->hd_als, h->fp64, h->d_relk));
+      std::vector<int> status(K, 0);
+      CU(cudaMemcpyAsync(rel.data(), h->d_relk, K * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      CU(cudaMemcpyAsync(status.data(), h->d_status, K * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+      TRY(sync(h));
+      for (int k = 0; k < K; ++k) {
+        if (!active[k]) continue;
+        if (status[k]) return set_err(CNCPD_ESINGULAR, "ALS normal matrix of block %d not positive definite", k);
+        sweeps[k] = s;
+        if (std::fabs(rel[k] - rel_prev[k]) < h->opts.lra_eps) active[k] = 0;
+        rel_prev[k] = rel[k];
+      }
     }
   }
   h->hd_als = full;

@@ -1,0 +1,86 @@
+"""Streamed X (cncpd_opts.stream_x): only one block's stored values are on
+the device at a time.  The LRA step of lraCoNCPD-APG runs each block's ALS
+with its tensor in the window, the collapsed iterations need no X, and the
+global fit streams the blocks once more.  Since every kernel computes a
+block's results independently of the other blocks, the streamed handle must
+reproduce the resident one bit for bit: ALS sweeps, relative errors, the
+LRA factors, the iterates and the global fit.  Plain iterations, which need
+every block each sweep, are refused before the LRA step."""
+
+import numpy as np
+import pytest
+
+from tests.gpu_common import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def _face_small(seed=36):
+    import synth
+    w = synth.Workload("face_small_stream", [(120, 120, 48), (120, 120, 48), (120, 120, 48)], 20, [8, 0, 0], 20.0,
+                       seed, sparse_mode=0, density=0.1, R_lra=30)
+    Xs, _ = synth.make_tensors(w, dtype=np.float32)
+    return w, Xs, synth.init_factors(w.dims, w.R, w.seed), synth.init_lra_factors(w.dims, 30, w.seed)
+
+
+def _run(Xs, w, U0, Ut0, storage, stream_x):
+    import paper_2302_05119_gb300 as P
+    m = P.CoupledNCP(Xs, w.R, w.L, storage=storage, stream_x=stream_x)
+    m.set_factors(U0)
+    st = m.lra(30, Ut0)
+    Ut = [[m.lra_factor(k, n) for n in range(3)] for k in range(w.K)]
+    fit0 = m.global_fit()
+    s = m.step(10)
+    out = (st["lra_sweeps"], st["lra_relerr"], Ut, fit0, s["F"], m.factors(), m.global_fit())
+    m.close()
+    return out
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16", "bf16x2"])
+@pytest.mark.parametrize("source", ["pageable", "pinned"])
+def test_streamed_lra_reproduces_resident(storage, source):
+    import torch
+    w, Xs, U0, Ut0 = _face_small()
+    src = Xs if source == "pageable" else [torch.from_numpy(X).pin_memory() for X in Xs]
+    a = _run(Xs, w, U0, Ut0, storage, False)
+    b = _run(src, w, U0, Ut0, storage, True)
+    assert a[0] == b[0] and a[1] == b[1], (a[:2], b[:2])
+    for k in range(w.K):
+        for n in range(3):
+            assert np.array_equal(a[2][k][n], b[2][k][n]), ("lra factor", k, n)
+            assert np.array_equal(a[5][k][n], b[5][k][n]), ("factor", k, n)
+    assert a[3] == b[3] and a[4] == b[4] and a[6] == b[6]
+    assert 0.0 < b[6] < 1.0  # ten collapsed iterations from the initial factors: far from converged
+
+
+def test_streamed_handle_refuses_plain_iterations_and_holds_one_block():
+    import torch
+
+    import paper_2302_05119_gb300 as P
+    w, Xs, U0, Ut0 = _face_small(seed=37)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    r = P.CoupledNCP(Xs, w.R, w.L, storage="f32")
+    used_resident = free0 - torch.cuda.mem_get_info()[0]
+    r.close()
+    free0 = torch.cuda.mem_get_info()[0]
+    m = P.CoupledNCP(Xs, w.R, w.L, storage="f32", stream_x=True)
+    used_streamed = free0 - torch.cuda.mem_get_info()[0]
+    block = int(np.prod(w.dims[0])) * 4
+    # two of the three stored blocks are not held (allocation granularity aside)
+    assert used_streamed <= used_resident - block, (used_resident, used_streamed, block)
+    m.set_factors(U0)
+    for call in (lambda: m.step(1), lambda: m.fit(), lambda: m.mttkrp(0, 0)):
+        with pytest.raises(P.CncpdError) as e:
+            call()
+        assert e.value.code == -6 and "stream_x" in str(e.value)
+    st = m.lra(30, Ut0)
+    assert st["lra_sweeps"] >= 1
+    s = m.step(3)
+    assert np.isfinite(s["F"])
+    m.close()
