@@ -369,11 +369,17 @@ def run_ours(args):
     w = _workload(args.workload)
     Xs, _ = synth.make_tensors(w, dtype=np.float32)
     U0 = synth.init_factors(w.dims, w.R, w.seed)
-    Xd = [torch.from_numpy(X).cuda() for X in Xs]
+    # streamed X reads the tensors from page-locked host memory block by block
+    # (device copies would defeat the point)
+    Xd = ([torch.from_numpy(X).pin_memory() for X in Xs] if args.stream_x
+          else [torch.from_numpy(X).cuda() for X in Xs])
     torch.cuda.synchronize()
 
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
     m = P.CoupledNCP(Xd, w.R, w.L, profile=True, storage=args.storage, tf32=args.tf32,
-                     autotune=not args.no_autotune)
+                     autotune=not args.no_autotune, stream_x=args.stream_x)
+    handle_bytes = free0 - torch.cuda.mem_get_info()[0]
     m.set_factors(U0)
     lra = None
     if args.lra:
@@ -381,7 +387,8 @@ def run_ours(args):
         t0 = time.perf_counter()
         sl = m.lra(Rt, synth.init_lra_factors(w.dims, Rt, w.seed))
         lra = {"R_tilde": Rt, "seconds": time.perf_counter() - t0, "als_sweeps": sl["lra_sweeps"],
-               "als_relerr": sl["lra_relerr"]}
+               "als_relerr": sl["lra_relerr"], "stream_x": args.stream_x,
+               "handle_device_bytes": handle_bytes}
     m.step(args.warmup)
     t0 = time.perf_counter()
     m.step(10)
@@ -449,7 +456,8 @@ def run_ours(args):
     Xh = [torch.from_numpy(X).pin_memory() for X in Xs]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    m2 = P.CoupledNCP(Xh, w.R, w.L, storage=args.storage, tf32=args.tf32, autotune=not args.no_autotune)
+    m2 = P.CoupledNCP(Xh, w.R, w.L, storage=args.storage, tf32=args.tf32, autotune=not args.no_autotune,
+                      stream_x=args.stream_x)
     m2.set_factors(U0)
     if args.lra:
         m2.lra(lra["R_tilde"], synth.init_lra_factors(w.dims, lra["R_tilde"], w.seed))
@@ -547,9 +555,13 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="lead-pass plan from the cost model instead of the measuring tuner (for profiler "
                          "runs, whose serialised launches would bias the tuner's choice)")
+    ap.add_argument("--stream-x", action="store_true",
+                    help="with --lra: keep one block of X on the device at a time (cncpd_opts.stream_x)")
     ap.add_argument("--tf32", action="store_true",
                     help="FP32 third-order data: trailing pass on the TF32 tensor cores (opt-in, slower)")
     args = ap.parse_args()
+    if args.stream_x and not args.lra:
+        ap.error("--stream-x needs --lra: only the lraCoNCPD-APG iterations run without X on the device")
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
