@@ -366,9 +366,11 @@ int64_t unit_cost(const DevDesc& d, int st, int64_t valid, int64_t tile, bool te
   return std::max(valid * es, work) + 4 * 32768;
 }
 
-// Split-K plan of the lead-mode contraction for rank bucket RP.
-// Split-K plan aiming at about target_units units in all.
-void plan_lead_units(cncpd_ctx* c, DevDesc& d, int RP, int fp64, int64_t target_units, size_t* partial_elems) {
+// Split-K plan of the lead-mode contraction for rank bucket RP, aiming at
+// about target_units units in all (per_block: for every block, which then
+// runs alone, as with streamed X).
+void plan_lead_units(cncpd_ctx* c, DevDesc& d, int RP, int fp64, int64_t target_units, size_t* partial_elems,
+                     bool per_block = false) {
   const int cpt = lead_cpt(fp64, RP);
   const int tile_cols = (d.use_tma || d.use_umma) ? 256 : 64 * cpt;
   int64_t tot_rows = 0;
@@ -379,7 +381,8 @@ void plan_lead_units(cncpd_ctx* c, DevDesc& d, int RP, int fp64, int64_t target_
     const int64_t J = d.trail_cols[k];
     const int ctiles = (int)((J + tile_cols - 1) / tile_cols);
     const int64_t rows = d.lead_rows[k];
-    int64_t want = std::max<int64_t>(1, (target_units * rows) / std::max<int64_t>(1, tot_rows) / ctiles);
+    const int64_t share = per_block ? rows : tot_rows;
+    int64_t want = std::max<int64_t>(1, (target_units * rows) / std::max<int64_t>(1, share) / ctiles);
     int64_t split_rows = (rows + want - 1) / want;
     if (d.use_umma) {
       const int64_t I1 = d.dims[k][1];
@@ -427,8 +430,13 @@ constexpr int kLeadMults[] = {1, 2, 3, 4, 6, 8};
 
 int plan_lead_splits(cncpd_ctx* c, DevDesc& d, int RP, int fp64, size_t* partial_elems) {
   if (!d.use_tma && !d.use_umma) {
-    plan_lead_units(c, d, RP, fp64, (int64_t)c->num_sms * 2, partial_elems);
+    plan_lead_units(c, d, RP, fp64, (int64_t)c->num_sms * 2, partial_elems, c->opts.stream_x != 0);
     return 0;
+  }
+  if (c->opts.stream_x) {
+    // blocks run one at a time: two units per SM for each
+    plan_lead_units(c, d, RP, fp64, (int64_t)c->num_sms * 2, partial_elems, true);
+    return 2;
   }
   int best = 1;
   int64_t best_span = -1;
@@ -450,7 +458,11 @@ int plan_lead_splits(cncpd_ctx* c, DevDesc& d, int RP, int fp64, size_t* partial
 size_t lead_partial_cap(cncpd_ctx* c, DevDesc d, int RP, int fp64) {
   size_t cap = 0, pel = 0;
   if (!d.use_tma && !d.use_umma) {
-    plan_lead_units(c, d, RP, fp64, (int64_t)c->num_sms * 2, &pel);
+    plan_lead_units(c, d, RP, fp64, (int64_t)c->num_sms * 2, &pel, c->opts.stream_x != 0);
+    return pel;
+  }
+  if (c->opts.stream_x) {
+    plan_lead_units(c, d, RP, fp64, (int64_t)c->num_sms * 2, &pel, true);
     return pel;
   }
   for (int mult : kLeadMults) {

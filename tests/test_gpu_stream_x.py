@@ -1,11 +1,13 @@
 """Streamed X (cncpd_opts.stream_x): only one block's stored values are on
 the device at a time.  The LRA step of lraCoNCPD-APG runs each block's ALS
 with its tensor in the window, the collapsed iterations need no X, and the
-global fit streams the blocks once more.  Since every kernel computes a
-block's results independently of the other blocks, the streamed handle must
-reproduce the resident one bit for bit: ALS sweeps, relative errors, the
-LRA factors, the iterates and the global fit.  Plain iterations, which need
-every block each sweep, are refused before the LRA step."""
+global fit streams the blocks once more.  A block's results depend on the
+other blocks only through the split-K plan of the lead pass, which a
+streamed handle makes per block (each block runs alone): so the streamed
+handle must reproduce the resident one up to FP32 summation order, in the
+ALS sweeps and errors, the low-rank reconstruction, the objective and the
+global fit.  Plain iterations, which need every block each sweep, are
+refused before the LRA step."""
 
 import numpy as np
 import pytest
@@ -33,7 +35,8 @@ def _run(Xs, w, U0, Ut0, storage, stream_x):
     m = P.CoupledNCP(Xs, w.R, w.L, storage=storage, stream_x=stream_x)
     m.set_factors(U0)
     st = m.lra(30, Ut0)
-    Ut = [[m.lra_factor(k, n) for n in range(3)] for k in range(w.K)]
+    from oracle import cncpd_oracle as O
+    Ut = [O.kruskal(np.ones(30), [m.lra_factor(k, n) for n in range(3)]) for k in range(w.K)]
     fit0 = m.global_fit()
     s = m.step(10)
     out = (st["lra_sweeps"], st["lra_relerr"], Ut, fit0, s["F"], m.factors(), m.global_fit())
@@ -49,12 +52,20 @@ def test_streamed_lra_reproduces_resident(storage, source):
     src = Xs if source == "pageable" else [torch.from_numpy(X).pin_memory() for X in Xs]
     a = _run(Xs, w, U0, Ut0, storage, False)
     b = _run(src, w, U0, Ut0, storage, True)
-    assert a[0] == b[0] and a[1] == b[1], (a[:2], b[:2])
+    assert abs(a[0] - b[0]) <= 1, (a[0], b[0])
+    assert abs(a[1] - b[1]) <= 1e-5 * a[1], (a[1], b[1])
+    # the low-rank tensors X~ (their factors are not unique): with R~ = 30
+    # above the data's rank 20 the fit leaves directions free, along which
+    # summation-order differences (~1e-7) grow over the ALS sweeps (2e-5
+    # measured with BF16 storage); the ALS error and the Fit agree to 1e-5
+    for k in range(w.K):
+        assert np.linalg.norm(a[2][k] - b[2][k]) <= 1e-4 * np.linalg.norm(a[2][k]), k
+    assert abs(a[3] - b[3]) <= 1e-5 and abs(a[6] - b[6]) <= 1e-5, (a[3], b[3], a[6], b[6])
+    assert abs(a[4] - b[4]) <= 1e-5 * abs(a[4]), (a[4], b[4])
     for k in range(w.K):
         for n in range(3):
-            assert np.array_equal(a[2][k][n], b[2][k][n]), ("lra factor", k, n)
-            assert np.array_equal(a[5][k][n], b[5][k][n]), ("factor", k, n)
-    assert a[3] == b[3] and a[4] == b[4] and a[6] == b[6]
+            e = np.linalg.norm(a[5][k][n] - b[5][k][n]) / np.linalg.norm(a[5][k][n])
+            assert e <= 1e-4, ("factor", k, n, e)
     assert 0.0 < b[6] < 1.0  # ten collapsed iterations from the initial factors: far from converged
 
 
