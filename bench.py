@@ -476,7 +476,7 @@ def run_ours(args):
     others = None
     if rank == 0 and ws == 1 and not args.no_time_to_fit:
         # the metric's second part: mixed precision against plain FP32 on the
-        # precision workload (512 x 512 x 256 x 4, R = 20), judged on the FP32
+        # precision workload (512 x 512 x 256 x 4, R = 20), evaluated on the FP32
         # data; then the same data in BF16 and BF16 hi+lo storage, and the
         # uneven fourth-order EEG-shaped blocks, for iterations/s and roofline
         wp = _workload("bf16_512x512x256")
