@@ -373,6 +373,9 @@ __global__ void __launch_bounds__(256) k_level2(const DevDesc* __restrict__ d, i
   const int m0 = (n < h) ? 0 : h, m1 = (n < h) ? h : N;
   const int64_t In = d->dims[k][n];
   if (in >= In) return;
+  // a block whose tensor pass had no units (inactive in a restricted
+  // descriptor) has no new level-1 product
+  if ((n < h) ? d->lt_prefix[k + 1] == d->lt_prefix[k] : d->tt_prefix[k + 1] == d->tt_prefix[k]) return;
   const int R = d->R[k];
   const T* P = reinterpret_cast<const T*>((n < h) ? d->Pl[k] : d->Pt[k]);
   int A = 1, B = 1;

@@ -626,7 +626,10 @@ static PairArgs<T> pair_args(const DevDesc& hd, int n, int num_sms, int* ctas) {
     a.Io[k] = (int)hd.dims[k][other];
     a.R[k] = hd.R[k];
     a.cta0[k] = tot;
-    tot += (int)((hd.dims[k][n] + ni - 1) / ni);
+    // no CTAs for a block whose tensor pass had no units (inactive in a
+    // restricted descriptor): its level-1 product is not new
+    const bool act = (n < h) ? hd.lt_prefix[k + 1] > hd.lt_prefix[k] : hd.tt_prefix[k + 1] > hd.tt_prefix[k];
+    if (act) tot += (int)((hd.dims[k][n] + ni - 1) / ni);
     a.P[k] = reinterpret_cast<const T*>((n < h) ? hd.Pl[k] : hd.Pt[k]);
     a.W[k] = reinterpret_cast<const T*>(hd.U1[k][other]);
     a.M[k] = reinterpret_cast<T*>(hd.M[k][n]);
