@@ -44,11 +44,14 @@ def _run(Xs, w, U0, Ut0, storage, stream_x):
     return out
 
 
-@pytest.mark.parametrize("storage", ["f32", "bf16", "bf16x2"])
-@pytest.mark.parametrize("source", ["pageable", "pinned"])
+@pytest.mark.parametrize("storage,source", [
+    ("f32", "pageable"), ("f32", "pinned"), ("bf16", "pageable"), ("bf16", "pinned"),
+    ("bf16x2", "pageable"), ("bf16x2", "pinned"), ("f64", "pageable"), ("f64", "pinned")])
 def test_streamed_lra_reproduces_resident(storage, source):
     import torch
     w, Xs, U0, Ut0 = _face_small()
+    if storage == "f64":  # FP64 storage from FP64 tensors (the generic contraction kernels)
+        Xs = [X.astype(np.float64) for X in Xs]
     src = Xs if source == "pageable" else [torch.from_numpy(X).pin_memory() for X in Xs]
     a = _run(Xs, w, U0, Ut0, storage, False)
     b = _run(src, w, U0, Ut0, storage, True)
