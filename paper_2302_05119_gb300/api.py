@@ -71,6 +71,11 @@ class CoupledNCP:
 
     tensors: K arrays of shape (I_1, ..., I_N); R: rank (int or K ints);
     L: coupled columns per mode; nonneg: per-mode projection flags.
+    The keyword options mirror cncpd_opts (include/cncpd.h): storage (None,
+    "f64", "f32", "bf16", "bf16x2"), tensor_cores, autotune, tf32 (FP32
+    data: trailing pass on the TF32 tensor cores, opt-in) and stream_x (one
+    block of X on the device at a time; lraCoNCPD-APG only, the tensors are
+    kept referenced by this object).
     """
 
     def __init__(self, tensors, R, L, nonneg=None, storage=None, use_core=False, reupdate=True,
